@@ -1,0 +1,230 @@
+"""Plain FP64 CPU oracle of the sky cross-match -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The CUDA
+library never calls it and shares no code with it.
+
+The membership test itself lives in ``xm_oracle.c`` (paper §2.1, Sky
+functional case, written out pair by pair in FP64). This module loads it and
+adds the two steps of paper §2.2 in plain numpy:
+
+* match selection: *all* the matches, or only the *best* pair of each source
+  of the first catalogue (smallest angular separation; equal separations go to
+  the lowest row of the second catalogue);
+* the join types i)-v): 1 and 2, 1 or 2, all from 1 / all from 2,
+  1 not 2 / 2 not 1, 1 xor 2. A row counts as matched when it appears in the
+  selected pairs. Rows come as (a_row, b_row, sep_arcsec) with -1 / NaN for
+  the missing side, first every row carrying an A source in ascending
+  (a_row, b_row), then the rows of unmatched B sources in ascending b_row.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xm_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+EQ, GAL = 0, 1
+CIRCLE, ELLIPSE, RECT = 0, 1, 2
+JOINS = ("and", "or", "all1", "all2", "not1_2", "not2_1", "xor")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (plain C, no GPU)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    pd = ctypes.POINTER(ctypes.c_double)
+    pi64 = ctypes.POINTER(ctypes.c_int64)
+    lib.or_match.restype = ctypes.c_void_p
+    lib.or_match.argtypes = [i64, pd, pd, i32, i32, pd, pd, pd, d, d, d, d, d, d, i32, i64, pd, pd,
+                             i32, pi64, i64, i32, i32, d, ctypes.POINTER(ctypes.c_int)]
+    lib.or_result_npairs.restype = i64
+    lib.or_result_npairs.argtypes = [ctypes.c_void_p]
+    lib.or_result_nborder.restype = i64
+    lib.or_result_nborder.argtypes = [ctypes.c_void_p]
+    lib.or_result_copy.argtypes = [ctypes.c_void_p, pi64, pi64, pd]
+    lib.or_result_copy_border.argtypes = [ctypes.c_void_p, pi64, pi64, pd]
+    lib.or_result_free.argtypes = [ctypes.c_void_p]
+    lib.or_to_equatorial.restype = i32
+    lib.or_to_equatorial.argtypes = [i64, pd, pd, i32, pd, pd]
+    lib.or_from_equatorial.restype = i32
+    lib.or_from_equatorial.argtypes = [i64, pd, pd, i32, pd, pd]
+    lib.or_gal_to_eq_matrix.argtypes = [pd]
+    lib.or_separation.restype = d
+    lib.or_separation.argtypes = [d, d, i32, d, d, i32]
+    _lib = lib
+    return lib
+
+
+class OracleError(ValueError):
+    """Invalid input, rejected as the library rejects it (XM_EINVAL)."""
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _ptr(x, ctype=ctypes.c_double):
+    return None if x is None else x.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def gal_to_eq_matrix() -> np.ndarray:
+    m = np.zeros(9)
+    _load().or_gal_to_eq_matrix(_ptr(m))
+    return m.reshape(3, 3)
+
+
+def to_equatorial(lon, lat, frame):
+    lon, lat = _f64(lon), _f64(lat)
+    ra, dec = np.empty_like(lon), np.empty_like(lat)
+    if _load().or_to_equatorial(lon.size, _ptr(lon), _ptr(lat), frame, _ptr(ra), _ptr(dec)):
+        raise OracleError("invalid coordinates")
+    return ra, dec
+
+
+def from_equatorial(ra, dec, frame):
+    ra, dec = _f64(ra), _f64(dec)
+    lon, lat = np.empty_like(ra), np.empty_like(dec)
+    if _load().or_from_equatorial(ra.size, _ptr(ra), _ptr(dec), frame, _ptr(lon), _ptr(lat)):
+        raise OracleError("invalid coordinates")
+    return lon, lat
+
+
+def separation(lon1, lat1, frame1, lon2, lat2, frame2) -> float:
+    return _load().or_separation(lon1, lat1, frame1, lon2, lat2, frame2)
+
+
+def match(a_lon, a_lat, b_lon, b_lat, *, shape=CIRCLE, a=1.0, b=None, pa=0.0,
+          a_col=None, b_col=None, pa_col=None, size_scale=1.0, size_unit_arcsec=1.0,
+          pa_zero_deg=0.0, pa_dir=1, a_frame=EQ, b_frame=EQ, subset=None, mode="grid",
+          nthreads=None, tau=1e-9):
+    """All members of each A source (paper §2.1). Returns a dict with int64
+    ``a_row``, ``b_row``, float64 ``sep`` (arcsec) in ascending (a_row, b_row)
+    and the borderline candidates ``border_a``, ``border_b``, ``border_margin``
+    (decision margin below ``tau``)."""
+    lib = _load()
+    a_lon, a_lat, b_lon, b_lat = _f64(a_lon), _f64(a_lat), _f64(b_lon), _f64(b_lat)
+    a_col = None if a_col is None else _f64(a_col)
+    b_col = None if b_col is None else _f64(b_col)
+    pa_col = None if pa_col is None else _f64(pa_col)
+    if b is None:
+        b = a
+    sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int64)
+    nthreads = nthreads or os.cpu_count() or 1
+    st = ctypes.c_int(0)
+    res = lib.or_match(a_lon.size, _ptr(a_lon), _ptr(a_lat), a_frame, shape, _ptr(a_col),
+                       _ptr(b_col), _ptr(pa_col), float(a), float(b), float(pa),
+                       float(size_scale), float(size_unit_arcsec), float(pa_zero_deg),
+                       int(pa_dir), b_lon.size, _ptr(b_lon), _ptr(b_lat), b_frame,
+                       _ptr(sub, ctypes.c_int64), 0 if sub is None else sub.size,
+                       {"brute": 0, "grid": 1}[mode], nthreads, float(tau), ctypes.byref(st))
+    if not res:
+        if st.value == 1:
+            raise OracleError("invalid input")
+        raise MemoryError("oracle out of memory")
+    try:
+        n = lib.or_result_npairs(res)
+        nb = lib.or_result_nborder(res)
+        out = {"a_row": np.empty(n, np.int64), "b_row": np.empty(n, np.int64),
+               "sep": np.empty(n, np.float64), "border_a": np.empty(nb, np.int64),
+               "border_b": np.empty(nb, np.int64), "border_margin": np.empty(nb, np.float64)}
+        lib.or_result_copy(res, _ptr(out["a_row"], ctypes.c_int64),
+                           _ptr(out["b_row"], ctypes.c_int64), _ptr(out["sep"]))
+        lib.or_result_copy_border(res, _ptr(out["border_a"], ctypes.c_int64),
+                                  _ptr(out["border_b"], ctypes.c_int64),
+                                  _ptr(out["border_margin"]))
+    finally:
+        lib.or_result_free(res)
+    return out
+
+
+def best(pairs, n_a, tau=1e-9):
+    """Best pair of every A source (paper §2.2 "best"): the member with the
+    smallest separation, ties to the lowest B row. Returns ``best_b`` (int64,
+    -1 when A has no member), ``best_sep`` (NaN when none) and ``near_tie``, the
+    A rows whose two smallest separations differ by less than tau times the
+    smallest (their order may depend on the last ulp)."""
+    a, b, sep = pairs["a_row"], pairs["b_row"], pairs["sep"]
+    best_b = np.full(n_a, -1, np.int64)
+    best_sep = np.full(n_a, np.nan)
+    near = []
+    if a.size:
+        order = np.lexsort((b, sep, a))  # by a, then sep, then b
+        a_s, b_s, s_s = a[order], b[order], sep[order]
+        first = np.ones(a_s.size, bool)
+        first[1:] = a_s[1:] != a_s[:-1]
+        idx = np.nonzero(first)[0]
+        best_b[a_s[idx]] = b_s[idx]
+        best_sep[a_s[idx]] = s_s[idx]
+        second = idx + 1
+        ok = second < a_s.size
+        second, idx2 = second[ok], idx[ok]
+        same_a = a_s[second] == a_s[idx2]
+        second, idx2 = second[same_a], idx2[same_a]
+        gap = s_s[second] - s_s[idx2]
+        near = a_s[idx2[gap < tau * s_s[idx2]]]
+    return {"best_b": best_b, "best_sep": best_sep, "near_tie": np.asarray(near, np.int64)}
+
+
+def selected_pairs(pairs, n_a, selection, tau=1e-9):
+    """The pair set after match selection ("all" or "best")."""
+    if selection == "all":
+        return {k: pairs[k] for k in ("a_row", "b_row", "sep")}
+    bb = best(pairs, n_a, tau)
+    rows = np.nonzero(bb["best_b"] >= 0)[0].astype(np.int64)
+    return {"a_row": rows, "b_row": bb["best_b"][rows], "sep": bb["best_sep"][rows]}
+
+
+def join(sel, n_a, n_b, join_type):
+    """Join types of paper §2.2 over a selected pair set. Returns int64
+    ``a_row``, ``b_row`` and float64 ``sep`` (-1 / NaN for a missing side)."""
+    if join_type not in JOINS:
+        raise OracleError(join_type)
+    a, b, sep = sel["a_row"], sel["b_row"], sel["sep"]
+    matched_a = np.zeros(n_a, bool)
+    matched_a[a] = True
+    matched_b = np.zeros(n_b, bool)
+    matched_b[b] = True
+    un_a = np.nonzero(~matched_a)[0].astype(np.int64)
+    un_b = np.nonzero(~matched_b)[0].astype(np.int64)
+    with_pairs = join_type in ("and", "or", "all1", "all2")
+    with_un_a = join_type in ("or", "all1", "not1_2", "xor")
+    with_un_b = join_type in ("or", "all2", "not2_1", "xor")
+    parts_a, parts_b, parts_s = [], [], []
+    if with_pairs:
+        parts_a.append(a); parts_b.append(b); parts_s.append(sep)
+    if with_un_a:
+        parts_a.append(un_a); parts_b.append(np.full(un_a.size, -1, np.int64))
+        parts_s.append(np.full(un_a.size, np.nan))
+    if parts_a:
+        ra, rb, rs = np.concatenate(parts_a), np.concatenate(parts_b), np.concatenate(parts_s)
+        order = np.lexsort((rb, ra))
+        ra, rb, rs = ra[order], rb[order], rs[order]
+    else:
+        ra, rb, rs = (np.empty(0, np.int64), np.empty(0, np.int64), np.empty(0))
+    if with_un_b:
+        ra = np.concatenate([ra, np.full(un_b.size, -1, np.int64)])
+        rb = np.concatenate([rb, un_b])
+        rs = np.concatenate([rs, np.full(un_b.size, np.nan)])
+    return {"a_row": ra, "b_row": rb, "sep": rs}

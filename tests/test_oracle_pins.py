@@ -1,0 +1,415 @@
+"""Pins of the FP64 oracle to facts outside itself (no GPU).
+
+Each test checks the oracle against something it does not compute itself:
+brute force, planted truths drawn by the generator, closed forms, published
+frame constants, symmetries and set identities of paper §2.2.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_08494_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ARCSEC_DEG = 1.0 / 3600.0
+
+
+def _pairs(r):
+    return set(zip(r["a_row"].tolist(), r["b_row"].tolist()))
+
+
+# ------------------------------------------------------------- pruning --
+
+def _random_mixed(seed, n_a=300, n_b=600):
+    """Tiny catalogues crowded around hard places: both poles, the RA 0/360
+    seam and an ordinary field, so a few arcsec regions catch members."""
+    g = synth.rng(seed)
+    parts_a, parts_b = [], []
+    for lon0, lat0 in ((0.0, 90.0), (0.0, -90.0), (0.0, 10.0), (200.0, -45.0)):
+        parts_a.append(synth.cap(g, n_a // 4, lon0, lat0, 0.01))
+        parts_b.append(synth.cap(g, n_b // 4, lon0, lat0, 0.01))
+    a_lon = np.concatenate([p[0] for p in parts_a]); a_lat = np.concatenate([p[1] for p in parts_a])
+    b_lon = np.concatenate([p[0] for p in parts_b]); b_lat = np.concatenate([p[1] for p in parts_b])
+    n = a_lon.size
+    cols = dict(a_col=np.exp(g.uniform(np.log(2.0), np.log(40.0), n)),
+                pa_col=g.uniform(-200.0, 400.0, n))
+    cols["b_col"] = cols["a_col"] * g.uniform(0.2, 1.0, n)
+    return a_lon, a_lat, b_lon, b_lat, cols
+
+
+@pytest.mark.parametrize("shape", [oracle.CIRCLE, oracle.ELLIPSE, oracle.RECT])
+@pytest.mark.parametrize("frames", [(0, 0), (1, 1), (1, 0), (0, 1)])
+def test_grid_equals_brute_force(shape, frames):
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(7 + shape)
+    # the catalogues are drawn in one frame; a galactic one is re-expressed so
+    # both still cover the same sky
+    if frames[0] == oracle.GAL:
+        a_lon, a_lat = oracle.from_equatorial(a_lon, a_lat, oracle.GAL)
+    if frames[1] == oracle.GAL:
+        b_lon, b_lat = oracle.from_equatorial(b_lon, b_lat, oracle.GAL)
+    kw = dict(shape=shape, a_frame=frames[0], b_frame=frames[1], pa_zero_deg=12.5, pa_dir=-1,
+              size_scale=0.5, **cols)
+    g = oracle.match(a_lon, a_lat, b_lon, b_lat, mode="grid", **kw)
+    b = oracle.match(a_lon, a_lat, b_lon, b_lat, mode="brute", **kw)
+    assert g["a_row"].size > 20  # the case is not vacuous
+    np.testing.assert_array_equal(g["a_row"], b["a_row"])
+    np.testing.assert_array_equal(g["b_row"], b["b_row"])
+    np.testing.assert_array_equal(g["sep"], b["sep"])
+    # canonical order
+    key = g["a_row"] * (b_lon.size + 1) + g["b_row"]
+    assert np.all(np.diff(key) > 0)
+
+
+def test_grid_finds_rectangle_corners():
+    # a rectangle reaches sqrt(a^2 + b^2) from its centre; members sitting
+    # just inside the corners must survive the pruning at any orientation
+    g = synth.rng(21)
+    n = 400
+    a_lon, a_lat = synth.uniform_box(g, n, 0.0, 360.0, -89.0, 89.0)
+    pa = g.uniform(0.0, 180.0, n)
+    a, b = 10.0, 10.0
+    corners = np.array([[a, b], [-a, b], [a, -b], [-a, -b]]) * 0.9999
+    b_lon, b_lat = [], []
+    for i in range(n):
+        lo, la = _region_points(a_lon[i], a_lat[i], pa[i], corners)
+        b_lon.append(lo); b_lat.append(la)
+    b_lon, b_lat = np.concatenate(b_lon), np.concatenate(b_lat)
+    kw = dict(shape=oracle.RECT, a=a, b=b, pa_col=pa)
+    gr = oracle.match(a_lon, a_lat, b_lon, b_lat, **kw)
+    br = oracle.match(a_lon, a_lat, b_lon, b_lat, mode="brute", **kw)
+    assert _pairs(gr) == _pairs(br)
+    assert {(i, 4 * i + k) for i in range(n) for k in range(4)} <= _pairs(gr)
+
+
+def test_subset_equals_full():
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(3)
+    full = oracle.match(a_lon, a_lat, b_lon, b_lat, shape=oracle.ELLIPSE, **cols)
+    sub = np.arange(0, a_lon.size, 7)
+    part = oracle.match(a_lon, a_lat, b_lon, b_lat, shape=oracle.ELLIPSE, subset=sub, **cols)
+    keep = np.isin(full["a_row"], sub)
+    np.testing.assert_array_equal(full["a_row"][keep], part["a_row"])
+    np.testing.assert_array_equal(full["b_row"][keep], part["b_row"])
+
+
+# -------------------------------------------------------- planted truth --
+
+def test_planted_truth_c1():
+    d = synth.c1()
+    r = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], **d["region"])
+    t = d["truth"]
+    got = _pairs(r)
+    found = np.array([(a, b) in got for a, b in zip(t["a_row"].tolist(), t["b_row"].tolist())])
+    # every planted pair is a member exactly when its true offset is <= r
+    # (no generated offset lies within 1e-6 of the radius)
+    assert np.min(np.abs(t["rho_arcsec"] - 1.0)) > 1e-6
+    np.testing.assert_array_equal(found, t["rho_arcsec"] <= 1.0)
+    # recall of a 2-D Gaussian offset inside r: 1 - exp(-r^2 / 2 sigma^2)
+    p = 1.0 - np.exp(-1.0 / (2 * 0.3 ** 2))
+    n = found.size
+    assert abs(found.sum() - n * p) < 5 * np.sqrt(n * p * (1 - p))
+    # separations of planted pairs equal the drawn offsets
+    sep = {k: s for k, s in zip(zip(r["a_row"].tolist(), r["b_row"].tolist()), r["sep"].tolist())}
+    err = [abs(sep[(a, b)] - rho) for a, b, rho in
+           zip(t["a_row"].tolist(), t["b_row"].tolist(), t["rho_arcsec"].tolist()) if (a, b) in sep]
+    assert max(err) < 1e-8
+    # chance matches: B surface density x circle area, per A (Poisson, 5 sigma)
+    area_deg2 = np.degrees(1.0) * (np.sin(np.radians(3.0)) - np.sin(np.radians(2.0)))
+    dens_b = d["b_lon"].size / area_deg2
+    expect = d["a_lon"].size * dens_b * np.pi * (1.0 * ARCSEC_DEG) ** 2
+    extra = r["a_row"].size - found.sum()
+    assert abs(extra - expect) < 5 * np.sqrt(expect) + 3
+    assert r["border_a"].size == 0
+
+
+# ----------------------------------------------------------- symmetries --
+
+def test_circle_symmetry():
+    d = synth.c1()
+    ab = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], a=1.0)
+    ba = oracle.match(d["b_lon"], d["b_lat"], d["a_lon"], d["a_lat"], a=1.0)
+    assert _pairs(ab) == {(b, a) for a, b in _pairs(ba)}
+
+
+def _rotate(lon, lat, rot):
+    l, b = np.radians(lon), np.radians(lat)
+    p = np.stack([np.cos(b) * np.cos(l), np.cos(b) * np.sin(l), np.sin(b)])
+    q = rot @ p
+    return np.degrees(np.arctan2(q[1], q[0])) % 360.0, np.degrees(np.arctan2(q[2], np.hypot(q[0], q[1])))
+
+
+def test_rotation_invariance_circles():
+    a_lon, a_lat, b_lon, b_lat, _ = _random_mixed(11)
+    g = synth.rng(99)
+    qm, _ = np.linalg.qr(g.normal(size=(3, 3)))
+    if np.linalg.det(qm) < 0:
+        qm[:, 0] = -qm[:, 0]
+    r0 = oracle.match(a_lon, a_lat, b_lon, b_lat, a=25.0)
+    ra_lon, ra_lat = _rotate(a_lon, a_lat, qm)
+    rb_lon, rb_lat = _rotate(b_lon, b_lat, qm)
+    r1 = oracle.match(ra_lon, ra_lat, rb_lon, rb_lat, a=25.0)
+    assert r0["a_row"].size > 50
+    assert r0["border_a"].size == 0
+    np.testing.assert_array_equal(r0["a_row"], r1["a_row"])
+    np.testing.assert_array_equal(r0["b_row"], r1["b_row"])
+    np.testing.assert_allclose(r0["sep"], r1["sep"], atol=1e-9)
+
+
+# ---------------------------------------------------------- closed forms --
+
+def test_golden_equator_meridian():
+    rows = np.loadtxt(os.path.join(GOLDEN, "equator_meridian.txt"))
+    for a_ra, a_dec, b_ra, b_dec, sep, member in rows:
+        assert oracle.separation(a_ra, a_dec, 0, b_ra, b_dec, 0) == pytest.approx(sep, abs=1e-6)
+        r = oracle.match([a_ra], [a_dec], [b_ra], [b_dec], a=1.5)
+        assert r["a_row"].size == int(member)
+        if member:
+            assert r["sep"][0] == pytest.approx(sep, abs=1e-6)
+
+
+def _region_points(lon0, lat0, theta_deg, xy_arcsec):
+    """Positions whose azimuthal-equidistant region coordinates about
+    (lon0, lat0) are (X, Y): X along the major axis at bearing theta, Y
+    towards bearing theta + 90 deg."""
+    x, y = xy_arcsec[:, 0], xy_arcsec[:, 1]
+    rho = np.hypot(x, y) * synth.ARCSEC
+    bearing = np.radians(theta_deg) + np.arctan2(y, x)
+    return synth.destination(np.full(x.size, lon0), np.full(x.size, lat0), rho, bearing)
+
+
+@pytest.mark.parametrize("lat0", [0.0, -48.0, 89.9999])
+def test_circle_boundary(lat0):
+    r = 7.0
+    eps = 1e-8  # the constructed offsets carry ~1e-11 relative error
+    bearings = np.linspace(0.0, 360.0, 13)[:-1]
+    xy = np.concatenate([np.stack([r * (1 - eps) * np.cos(np.radians(bearings)),
+                                   r * (1 - eps) * np.sin(np.radians(bearings))], 1),
+                         np.stack([r * (1 + eps) * np.cos(np.radians(bearings)),
+                                   r * (1 + eps) * np.sin(np.radians(bearings))], 1)])
+    lon, lat = _region_points(45.0, lat0, 0.0, xy)
+    res = oracle.match([45.0], [lat0], lon, lat, a=r)
+    np.testing.assert_array_equal(res["b_row"], np.arange(12))
+    np.testing.assert_allclose(res["sep"], r * (1 - eps), rtol=1e-10)
+
+
+@pytest.mark.parametrize("lat0", [0.0, 37.0, -89.99, 89.995])
+def test_ellipse_axes_and_orientation(lat0):
+    a, b, pa = 20.0, 6.0, 30.0
+    eps = 1e-8
+    xy = np.array([[a * (1 - eps), 0], [a * (1 + eps), 0], [-a * (1 - eps), 0], [-a * (1 + eps), 0],
+                   [0, b * (1 - eps)], [0, b * (1 + eps)], [0, -b * (1 - eps)], [0, -b * (1 + eps)],
+                   [b * 1.01, a * 0.5], [a * 0.6, b * 0.79], [a * 0.6, b * 0.81]])
+    # expected from the construction: inside iff (X/a)^2 + (Y/b)^2 <= 1
+    expect = (xy[:, 0] / a) ** 2 + (xy[:, 1] / b) ** 2 <= 1.0
+    lon, lat = _region_points(123.0, lat0, pa, xy)
+    r = oracle.match([123.0], [lat0], lon, lat, shape=oracle.ELLIPSE, a=a, b=b, pa=pa)
+    got = np.zeros(len(xy), bool)
+    got[r["b_row"]] = True
+    np.testing.assert_array_equal(got, expect)
+
+
+@pytest.mark.parametrize("lat0", [0.0, -60.0, 89.999])
+def test_rectangle_corners(lat0):
+    a, b, pa = 15.0, 4.0, 110.0
+    eps = 1e-8
+    xy = np.array([[a * (1 - eps), b * (1 - eps)], [a * (1 + eps), b * (1 - eps)],
+                   [a * (1 - eps), b * (1 + eps)], [-a * (1 - eps), -b * (1 - eps)],
+                   [-a * (1 - eps), b * (1 + eps)], [a * 0.99, -b * 0.99], [0.0, b * 1.001]])
+    expect = (np.abs(xy[:, 0]) <= a) & (np.abs(xy[:, 1]) <= b)
+    lon, lat = _region_points(300.0, lat0, pa, xy)
+    r = oracle.match([300.0], [lat0], lon, lat, shape=oracle.RECT, a=a, b=b, pa=pa)
+    got = np.zeros(len(xy), bool)
+    got[r["b_row"]] = True
+    np.testing.assert_array_equal(got, expect)
+
+
+def test_orientation_identities():
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(5)
+    base = dict(a_col=cols["a_col"], b_col=cols["b_col"])
+    pa = cols["pa_col"]
+    for shape in (oracle.ELLIPSE, oracle.RECT):
+        ref = _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=shape, pa_col=pa, **base))
+        assert len(ref) > 20
+        # PA + 180 deg leaves the region unchanged
+        assert ref == _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=shape,
+                                          pa_col=pa + 180.0, **base))
+        # PA + 90 deg with the axes swapped is the same region
+        assert ref == _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=shape,
+                                          pa_col=pa + 90.0, a_col=base["b_col"],
+                                          b_col=base["a_col"]))
+        # direction -1 with PA equals direction +1 with -PA
+        assert ref == _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=shape, pa_dir=-1,
+                                          pa_col=-pa, **base))
+        # a zero-point shift is a PA shift
+        assert ref == _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=shape, pa_zero_deg=40.0,
+                                          pa_col=pa - 40.0, **base))
+    # an ellipse with equal axes is the circle
+    circ = _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, a_col=cols["a_col"]))
+    ell = _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, shape=oracle.ELLIPSE, a_col=cols["a_col"],
+                              b_col=cols["a_col"], pa_col=pa))
+    assert circ == ell
+
+
+def test_size_scale_and_unit():
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(6)
+    ref = _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, a_col=cols["a_col"]))
+    # FWHM column with scale 0.5, in arcmin
+    alt = _pairs(oracle.match(a_lon, a_lat, b_lon, b_lat, a_col=cols["a_col"] * 2 / 60.0,
+                              size_scale=0.5, size_unit_arcsec=60.0))
+    assert ref == alt
+
+
+# --------------------------------------------------------------- frames --
+
+def test_frame_constants_golden():
+    with open(os.path.join(GOLDEN, "galactic_frame.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    for _, lon, lat, fr, lon2, lat2, fr2, tol in rows:
+        lon, lat, lon2, lat2, tol = map(float, (lon, lat, lon2, lat2, tol))
+        if fr == "gal":
+            ra, dec = oracle.to_equatorial([lon], [lat], oracle.GAL)
+        else:
+            ra, dec = oracle.from_equatorial([lon], [lat], oracle.GAL)
+        assert ra[0] == pytest.approx(lon2, abs=tol)
+        assert dec[0] == pytest.approx(lat2, abs=tol)
+
+
+def test_frame_matrix_orthonormal():
+    m = oracle.gal_to_eq_matrix()
+    np.testing.assert_allclose(m @ m.T, np.eye(3), atol=1e-15)
+    assert np.linalg.det(m) == pytest.approx(1.0, abs=1e-15)
+
+
+def test_frame_round_trip():
+    g = synth.rng(4)
+    ra, dec = synth.uniform_box(g, 20000, 0.0, 360.0, -90.0, 90.0)
+    ra = np.concatenate([ra, [0.0, 359.9999999, 10.0, 10.0]])
+    dec = np.concatenate([dec, [0.0, 0.0, 90.0, -90.0]])
+    lon, lat = oracle.from_equatorial(ra, dec, oracle.GAL)
+    ra2, dec2 = oracle.to_equatorial(lon, lat, oracle.GAL)
+    seps = np.array([oracle.separation(a, b, 0, c, d, 0) for a, b, c, d in zip(ra, dec, ra2, dec2)])
+    assert seps.max() * synth.ARCSEC < 1e-12
+
+
+def test_galactic_position_angle_counts_from_galactic_north():
+    # an ellipse given in galactic coordinates with PA 0 has its major axis
+    # towards galactic north, wherever it sits
+    l0, b0 = 33.0, 20.0
+    xy = np.array([[9.99, 0.0], [10.01, 0.0], [0.0, 2.5], [0.0, 1.9]])
+    lon, lat = _region_points(l0, b0, 0.0, xy)  # built in the galactic frame
+    r = oracle.match([l0], [b0], lon, lat, shape=oracle.ELLIPSE, a=10.0, b=2.0, pa=0.0,
+                     a_frame=oracle.GAL, b_frame=oracle.GAL)
+    np.testing.assert_array_equal(r["b_row"], [0, 3])
+    # B given in equatorial coordinates: same members
+    ra, dec = oracle.to_equatorial(lon, lat, oracle.GAL)
+    r2 = oracle.match([l0], [b0], ra, dec, shape=oracle.ELLIPSE, a=10.0, b=2.0, pa=0.0,
+                      a_frame=oracle.GAL, b_frame=oracle.EQ)
+    np.testing.assert_array_equal(r2["b_row"], [0, 3])
+    np.testing.assert_allclose(r2["sep"], r["sep"], atol=1e-8)
+
+
+# ------------------------------------------------------- validity rules --
+
+@pytest.mark.parametrize("bad", [dict(a_lat=[91.0]), dict(a_lat=[np.nan]), dict(a_lon=[np.inf]),
+                                 dict(b_lat=[-90.5]), dict(a_col=[-1.0])])
+def test_invalid_input_rejected(bad):
+    kw = dict(a_lon=[10.0], a_lat=[0.0], b_lon=[10.0], b_lat=[0.0])
+    cols = {k: v for k, v in bad.items() if k == "a_col"}
+    kw.update({k: v for k, v in bad.items() if k != "a_col"})
+    with pytest.raises(oracle.OracleError):
+        oracle.match(kw["a_lon"], kw["a_lat"], kw["b_lon"], kw["b_lat"], **cols)
+
+
+def test_zero_size_matches_nothing():
+    r = oracle.match([10.0, 10.0], [0.0, 0.0], [10.0], [0.0], a_col=[0.0, 1.0])
+    np.testing.assert_array_equal(r["a_row"], [1])
+
+
+def test_ra_normalisation():
+    r1 = oracle.match([-0.0001], [5.0], [359.9999, 0.0002], [5.0], a=1.5)
+    r2 = oracle.match([359.9999], [5.0], [-0.0001, 360.0002], [5.0], a=1.5)
+    np.testing.assert_array_equal(r1["b_row"], [0])
+    np.testing.assert_array_equal(r2["b_row"], [0])
+
+
+# ------------------------------------------------- selection and joins --
+
+@pytest.fixture(scope="module")
+def c1_result():
+    d = synth.c1()
+    r = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], a=3.0)  # crowded enough for ties
+    return d, r
+
+
+def test_best_is_argmin_of_all(c1_result):
+    d, r = c1_result
+    n_a = d["a_lon"].size
+    bb = oracle.best(r, n_a)
+    sel = oracle.selected_pairs(r, n_a, "best")
+    assert _pairs(sel) <= _pairs(r)
+    for i in np.unique(r["a_row"])[:2000]:
+        m = r["a_row"] == i
+        j = np.lexsort((r["b_row"][m], r["sep"][m]))[0]
+        assert bb["best_b"][i] == r["b_row"][m][j]
+    assert np.all(bb["best_b"][np.setdiff1d(np.arange(n_a), r["a_row"])] == -1)
+    assert bb["near_tie"].size == 0
+
+
+def test_best_tie_goes_to_lowest_b_row():
+    # two identical B positions: the lower row wins
+    r = oracle.match([10.0], [0.0], [10.0001, 10.0001, 10.0002], [0.0, 0.0, 0.0], a=2.0)
+    bb = oracle.best(r, 1)
+    assert bb["best_b"][0] == 0
+
+
+@pytest.mark.parametrize("selection", ["all", "best"])
+def test_join_identities(c1_result, selection):
+    d, r = c1_result
+    n_a, n_b = d["a_lon"].size, d["b_lon"].size
+    sel = oracle.selected_pairs(r, n_a, selection)
+    J = {t: oracle.join(sel, n_a, n_b, t) for t in oracle.JOINS}
+    un_a = np.setdiff1d(np.arange(n_a), sel["a_row"])
+    un_b = np.setdiff1d(np.arange(n_b), sel["b_row"])
+    assert J["and"]["a_row"].size == sel["a_row"].size
+    assert J["or"]["a_row"].size == sel["a_row"].size + un_a.size + un_b.size
+    np.testing.assert_array_equal(J["not1_2"]["a_row"], un_a)
+    np.testing.assert_array_equal(J["not2_1"]["b_row"], un_b)
+    np.testing.assert_array_equal(J["xor"]["a_row"][: un_a.size], un_a)
+    np.testing.assert_array_equal(J["xor"]["b_row"][un_a.size:], un_b)
+    rows = lambda x: set(zip(x["a_row"].tolist(), x["b_row"].tolist()))  # noqa: E731
+    assert rows(J["all1"]) == rows(J["and"]) | rows(J["not1_2"])
+    assert rows(J["all2"]) == rows(J["and"]) | rows(J["not2_1"])
+    assert rows(J["or"]) == rows(J["and"]) | rows(J["xor"])
+    # A-side rows ascending, then B-only rows ascending
+    o = J["or"]
+    has_a = o["a_row"] >= 0
+    k = np.nonzero(~has_a)[0]
+    assert np.all(has_a[: k[0]]) and not np.any(has_a[k[0]:])
+    key = o["a_row"][has_a] * (n_b + 2) + o["b_row"][has_a] + 1
+    assert np.all(np.diff(key) > 0)
+    assert np.all(np.diff(o["b_row"][~has_a]) > 0)
+    assert np.all(np.isnan(o["sep"][o["b_row"] < 0]))
+
+
+def test_all_selection_unmatched_are_complements(c1_result):
+    d, r = c1_result
+    n_a, n_b = d["a_lon"].size, d["b_lon"].size
+    j = oracle.join(r, n_a, n_b, "xor")
+    in_m_a = np.zeros(n_a, bool); in_m_a[r["a_row"]] = True
+    in_m_b = np.zeros(n_b, bool); in_m_b[r["b_row"]] = True
+    np.testing.assert_array_equal(j["a_row"][j["a_row"] >= 0], np.nonzero(~in_m_a)[0])
+    np.testing.assert_array_equal(j["b_row"][j["a_row"] < 0], np.nonzero(~in_m_b)[0])
+
+
+# --------------------------------------------------------- fixed seeds --
+
+def test_c2_small_grid_equals_brute_and_no_borderline():
+    d = synth.c2(scale=0.002)
+    kw = dict(a_frame=d["a_frame"], b_frame=d["b_frame"], **d["region"])
+    g = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], **kw)
+    b = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], mode="brute", **kw)
+    assert g["a_row"].size > 500
+    assert _pairs(g) == _pairs(b)
+    assert g["border_a"].size == 0
