@@ -1,0 +1,269 @@
+/*
+ * xm.h -- C ABI of the GB300-native sky cross-match library (libxm.so).
+ *
+ * The library implements the "Sky" functional case of the paper (§2.1): for
+ * every source of catalogue A (the paper's first catalogue) a region -- circle,
+ * ellipse or rectangle -- is centred on its position, sized by fixed values or
+ * by per-source columns and oriented by a position angle with a zero-point and
+ * a direction of rotation; the sources of catalogue B (the second catalogue)
+ * inside that region are its members. Catalogue B is held in a sky-partitioned
+ * index (§2.3), the members of each A source are then selected ("all" or
+ * "best", §2.2) and joined (the five join types of §2.2).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an xm_status. No exception, abort or exit crosses the
+ *    ABI. xm_last_error() gives a one-line reason for the last failure on the
+ *    calling thread.
+ *  - Arrays are passed as plain pointers plus sizes. A pointer argument is
+ *    host memory or device memory as the accompanying `on_device` flag says;
+ *    inputs are borrowed for the duration of the call (the library copies what
+ *    it keeps) and never modified.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). All device
+ *    work of a call is ordered on it. Calls that must learn a data-dependent
+ *    size (xm_build_index, xm_match, xm_join) synchronise `stream` once to read
+ *    it; their outputs are written by work queued on `stream`, so use them on
+ *    that stream or after synchronising it.
+ *  - Outputs are opaque handles owned by the library and released with the
+ *    matching xm_*_free. Their device arrays stay valid until then.
+ *  - Device memory comes from the allocator installed with xm_set_allocator,
+ *    else from cudaMallocAsync on the call's stream.
+ *  - Angles: longitudes/latitudes and position angles in degrees; region sizes
+ *    in `size_unit_arcsec` arcseconds times `size_scale`; separations are
+ *    returned in arcseconds (float64).
+ *  - Rows are 0-based indices into the caller's catalogue arrays; -1 marks a
+ *    missing side in join output. Catalogues hold at most 2^31 - 1 rows.
+ */
+#ifndef XM_H
+#define XM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define XM_API __attribute__((visibility("default")))
+#else
+#define XM_API
+#endif
+
+typedef enum {
+    XM_OK = 0,
+    XM_EINVAL = 1,      /* invalid argument or invalid catalogue value */
+    XM_ENOMEM = 2,      /* a device or host allocation failed */
+    XM_ECUDA = 3,       /* a CUDA runtime call failed */
+    XM_ETIMEOUT = 4,    /* a bounded wait in a kernel or on the host ran out */
+    XM_EOVERFLOW = 5,   /* a result does not fit the caller's buffer or limit */
+    XM_EBUSY = 6,       /* admission refused: not enough free device memory */
+    XM_EUNSUPPORTED = 7 /* valid request the library does not implement */
+} xm_status;
+
+/* Coordinate systems of paper §2 (equatorial ICRS/J2000; IAU galactic). */
+typedef enum { XM_FRAME_EQ = 0, XM_FRAME_GAL = 1 } xm_frame;
+
+/* Region shapes of paper §2.1. CIRCLE uses `a` as its radius; ELLIPSE uses
+ * semi-axes a (along the position angle) and b; RECT uses half-sides a (along
+ * the position angle) and b. The region is the set of points whose
+ * azimuthal-equidistant coordinates about the A source satisfy the shape's
+ * inequality (closed boundary). */
+typedef enum { XM_CIRCLE = 0, XM_ELLIPSE = 1, XM_RECT = 2 } xm_shape;
+
+/* Match selection of paper §2.2 (a bit mask: both may be requested). */
+typedef enum { XM_SEL_ALL = 1, XM_SEL_BEST = 2 } xm_selection;
+
+/* Arithmetic of the membership test. FP64 evaluates every candidate in
+ * float64. FP32_RECHECK evaluates candidates in float32 on tangent-plane
+ * offsets from float64 cell centres and re-evaluates in float64 every
+ * candidate whose float32 value lies inside a proven guard band around the
+ * region boundary; both give the same member sets. */
+typedef enum { XM_PREC_FP64 = 0, XM_PREC_FP32_RECHECK = 1 } xm_precision;
+
+/* Join types of paper §2.2: i) 1 and 2, ii) 1 or 2, iii) all from 1 / all
+ * from 2, iv) 1 not 2 / 2 not 1, v) 1 xor 2. */
+typedef enum {
+    XM_JOIN_AND = 0,
+    XM_JOIN_OR = 1,
+    XM_JOIN_ALL1 = 2,
+    XM_JOIN_ALL2 = 3,
+    XM_JOIN_NOT1_2 = 4,
+    XM_JOIN_NOT2_1 = 5,
+    XM_JOIN_XOR = 6
+} xm_join_type;
+
+/* A catalogue as columns: n positions (lon_deg[i], lat_deg[i]) in `frame`.
+ * Longitudes are taken modulo 360; |lat| > 90, NaN or infinite values make the
+ * call fail with XM_EINVAL. `id` (nullable) is an int64 id column kept with
+ * the index. on_device: 1 if the pointers are device memory, 0 if host. */
+typedef struct {
+    const double* lon_deg;
+    const double* lat_deg;
+    const int64_t* id;
+    int64_t n;
+    int32_t frame;
+    int32_t on_device;
+} xm_columns;
+
+/* Region of each A source (paper §2.1). A size or angle comes from its column
+ * when the column pointer is non-NULL (one value per A source, same placement
+ * as the A columns), else from the fixed value. Effective sizes are
+ * value * size_scale * size_unit_arcsec arcsec (e.g. size_scale 0.5 turns an
+ * FWHM column into a radius). The effective position angle is
+ * pa_zero_deg + pa_dir * PA, counted east of north of the A catalogue's own
+ * frame; pa_dir is +1 or -1. A size of zero gives an empty region (that A
+ * source matches nothing); a negative or non-finite value is XM_EINVAL. */
+typedef struct {
+    int32_t shape;
+    int32_t pa_dir;
+    double a, b, pa_deg;
+    const double* a_col;
+    const double* b_col;
+    const double* pa_col;
+    double size_scale;
+    double size_unit_arcsec;
+    double pa_zero_deg;
+} xm_region;
+
+/* Options of the B index (the sky partition of paper §2.3). The index cuts
+ * the sphere into declination zones of height zone_height_arcsec, each zone
+ * into RA cells about as wide as they are high; B sources are sorted by
+ * (zone, RA). 0 selects 20 arcsec. build_fp64 also stores float64 unit
+ * vectors, which the FP64 path reads (it falls back to computing them). */
+typedef struct {
+    double zone_height_arcsec;
+    int32_t build_fp64;
+    int32_t reserved;
+} xm_index_opts;
+
+typedef struct {
+    int32_t selection; /* XM_SEL_ALL and/or XM_SEL_BEST */
+    int32_t precision; /* xm_precision */
+    int32_t block;     /* threads per block of the scan kernel, 0 = default */
+    int32_t reserved;
+} xm_match_opts;
+
+typedef struct xm_index xm_index;
+typedef struct xm_result xm_result;
+typedef struct xm_rows xm_rows;
+
+/* Per-call counters (cumulative over calls on the handle's device). */
+typedef struct {
+    uint64_t candidates;   /* B sources tested against a region */
+    uint64_t rechecked;    /* FP32 tests that fell in the guard band */
+    uint64_t flipped;      /* rechecks whose FP64 decision differed from q<=1 in FP32 */
+    uint64_t members;      /* (A, B) memberships found */
+    uint64_t tie_resolved; /* A sources whose best pair was decided in FP64 */
+    uint64_t kernel_launches;
+} xm_stats;
+
+/* ---- status and configuration ------------------------------------------ */
+
+XM_API const char* xm_status_str(xm_status s);
+/* One-line description of the last failure on this host thread ("" if none). */
+XM_API const char* xm_last_error(void);
+/* Library version string. */
+XM_API const char* xm_version(void);
+
+/* Installs the device allocator used by every later call (NULL restores
+ * cudaMallocAsync/cudaFreeAsync). alloc returns NULL on failure; both get the
+ * call's stream and ctx. */
+XM_API xm_status xm_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
+                                  void (*release)(void* ptr, void* stream, void* ctx), void* ctx);
+
+/* Counters accumulated since the last reset. */
+XM_API xm_status xm_get_stats(xm_stats* out);
+XM_API xm_status xm_reset_stats(void);
+
+/* Kernel timing: while enabled, the library brackets every kernel launch
+ * with CUDA events on the launching stream. xm_prof_read synchronises those
+ * events and returns, for the kernel whose name is given, the summed device
+ * time and launch count since the last enable. */
+XM_API xm_status xm_prof_enable(int32_t on);
+XM_API xm_status xm_prof_read(const char* kernel, double* total_ms, int64_t* launches);
+/* Name and totals of the i-th timed kernel (XM_EOVERFLOW past the end). */
+XM_API xm_status xm_prof_entry(int32_t i, const char** kernel, double* total_ms,
+                               int64_t* launches);
+
+/* ---- the B index (paper §2.3, sky partitioning) ------------------------ */
+
+/* Builds the resident, immutable index of catalogue B: ingest (longitude
+ * normalisation, validity), zone and RA key per source, a stable radix sort
+ * on (zone, RA key), per-zone offsets, and per-source float32 tangent-plane
+ * offsets from float64 cell centres. The index keeps B's frame; an A
+ * catalogue in another frame is rotated into it at match time. Synchronises
+ * `stream` once. Errors: XM_EINVAL (bad opts or coordinates), XM_ENOMEM,
+ * XM_ECUDA. */
+XM_API xm_status xm_build_index(const xm_columns* B, const xm_index_opts* opts, void* stream,
+                                xm_index** out);
+XM_API xm_status xm_index_free(xm_index* index);
+/* n sources, zones, zone height (arcsec) and device bytes held. */
+XM_API xm_status xm_index_info(const xm_index* index, int64_t* n, int64_t* zones,
+                               double* zone_height_arcsec, int64_t* device_bytes);
+
+/* ---- matching (paper §2.1 Sky case, §2.2 selection) -------------------- */
+
+/* Finds the members of every A source among the indexed B sources and keeps
+ * the selections asked for in opts->selection:
+ *   ALL:  every member pair, ordered by A row then B row;
+ *   BEST: per A row, the member of smallest angular separation, ties to the
+ *         lowest B row (-1 / NaN when the A source has no member).
+ * Synchronises `stream` once (to size the pair list).
+ * Errors: XM_EINVAL (bad region/opts/coordinates), XM_ENOMEM, XM_ECUDA. */
+XM_API xm_status xm_match(const xm_index* index, const xm_columns* A, const xm_region* region,
+                          const xm_match_opts* opts, void* stream, xm_result** out);
+XM_API xm_status xm_result_free(xm_result* result);
+
+/* Device arrays of a result (valid until xm_result_free):
+ *  n_pairs, a_row[n_pairs], b_row[n_pairs], sep_arcsec[n_pairs]   (ALL)
+ *  n_a, count[n_a] (int32 members per A row),
+ *  best_b_row[n_a] (int64, -1 = none), best_sep_arcsec[n_a] (NaN = none) (BEST)
+ * Arrays of a selection that was not requested come back NULL. */
+typedef struct {
+    int64_t n_pairs, n_a, n_b;
+    const int64_t* a_row;
+    const int64_t* b_row;
+    const double* sep_arcsec;
+    const int32_t* count;
+    const int64_t* best_b_row;
+    const double* best_sep_arcsec;
+} xm_result_view;
+XM_API xm_status xm_result_get(const xm_result* result, xm_result_view* view);
+
+/* ---- joins (paper §2.2) ------------------------------------------------ */
+
+/* Builds the rows of one join type over one selection of a result. A row is
+ * (a_row, b_row, sep_arcsec); a missing side is -1 / NaN. A source counts as
+ * matched when it appears in the selected pairs. Row order: every row that
+ * carries an A source in ascending (a_row, b_row), then the rows of unmatched
+ * B sources in ascending b_row. Synchronises `stream` once.
+ * Errors: XM_EINVAL (selection not in the result, bad join type), XM_ENOMEM,
+ * XM_ECUDA. */
+XM_API xm_status xm_join(const xm_result* result, int32_t selection, int32_t join_type,
+                         void* stream, xm_rows** out);
+XM_API xm_status xm_rows_free(xm_rows* rows);
+
+typedef struct {
+    int64_t n;
+    const int64_t* a_row;
+    const int64_t* b_row;
+    const double* sep_arcsec;
+    int64_t n_unmatched_a, n_unmatched_b;
+} xm_rows_view;
+XM_API xm_status xm_rows_get(const xm_rows* rows, xm_rows_view* view);
+
+/* Copies a device array of `bytes` bytes to host memory on `stream` and
+ * waits for it (convenience for callers without their own CUDA runtime). */
+XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);
+
+/* Host only, no device work: the library's galactic -> equatorial rotation
+ * (row major, v_eq = m v_gal) built from the IAU frame angles of paper §2's
+ * galactic coordinate system (north galactic pole at RA 192.85948 deg,
+ * Dec 27.12825 deg; galactic longitude of the north celestial pole
+ * 122.93192 deg). */
+XM_API xm_status xm_frame_matrix(double m[9]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XM_H */

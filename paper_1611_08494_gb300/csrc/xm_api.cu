@@ -1,0 +1,274 @@
+// xm_api.cu -- runtime of the C ABI: status strings, last-error text,
+// allocator hook, counters, kernel timing, and the galactic frame rotation.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+struct AllocHook {
+    void* (*alloc)(size_t, void*, void*) = nullptr;
+    void (*release)(void*, void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+AllocHook g_hook;
+std::mutex g_hook_mu;
+
+std::atomic<unsigned long long> g_stats[6];
+
+struct ProfPending {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfPending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+std::map<std::string, std::pair<double, int64_t>> g_prof_tot;
+thread_local cudaEvent_t t_begin = nullptr;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void drain_locked() {
+    for (auto& p : g_pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto& t = g_prof_tot[p.name];
+            t.first += ms;
+            t.second += 1;
+        }
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace
+
+xm_status set_error(xm_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+xm_status cuda_fail(cudaError_t e, const char* what) {
+    return set_error(XM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 1;
+    AllocHook h;
+    {
+        std::lock_guard<std::mutex> g(g_hook_mu);
+        h = g_hook;
+    }
+    if (h.alloc) return h.alloc(bytes, (void*)s, h.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error state of a failed allocation
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (!p) return;
+    AllocHook h;
+    {
+        std::lock_guard<std::mutex> g(g_hook_mu);
+        h = g_hook;
+    }
+    if (h.release) {
+        h.release(p, (void*)s, h.ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+void launch_begin(const char* name, cudaStream_t s) {
+    (void)name;
+    g_stats[5].fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on) {
+        t_begin = nullptr;
+        return;
+    }
+    t_begin = take_event();
+    if (t_begin) cudaEventRecord(t_begin, s);
+}
+
+cudaError_t launch_end(const char* name, cudaStream_t s) {
+    cudaError_t e = cudaGetLastError();
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (g_prof_on && t_begin) {
+        cudaEvent_t b = take_event();
+        if (b) {
+            cudaEventRecord(b, s);
+            g_pending.push_back({name, t_begin, b});
+        } else {
+            g_event_pool.push_back(t_begin);
+        }
+    }
+    t_begin = nullptr;
+    return e;
+}
+
+void stats_add(const unsigned long long* c) {
+    for (int k = 0; k < 5; k++) g_stats[k].fetch_add(c[k], std::memory_order_relaxed);
+}
+
+// Galactic -> equatorial rotation from the IAU frame angles (north galactic
+// pole at RA 192.85948 deg, Dec 27.12825 deg; galactic longitude of the north
+// celestial pole 122.93192 deg), as the product of three axis rotations:
+// turn the equatorial x axis onto the ascending node of the galactic plane
+// (RA_NGP + 90 deg), tilt the pole by 90 deg - Dec_NGP about that node, then
+// turn within the galactic plane so the node sits at longitude l_NCP - 90 deg.
+void gal_to_eq(double m[9]) {
+    const double ra_ngp = 192.85948 * kDeg, dec_ngp = 27.12825 * kDeg;
+    const double l_node = (122.93192 - 90.0) * kDeg;
+    auto rz = [](double ang, double r[9]) {
+        double c = cos(ang), s = sin(ang);
+        double t[9] = {c, s, 0, -s, c, 0, 0, 0, 1};
+        memcpy(r, t, sizeof(t));
+    };
+    auto rx = [](double ang, double r[9]) {
+        double c = cos(ang), s = sin(ang);
+        double t[9] = {1, 0, 0, 0, c, s, 0, -s, c};
+        memcpy(r, t, sizeof(t));
+    };
+    auto mul = [](const double* a, const double* b, double* c) {
+        double t[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                t[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+        memcpy(c, t, sizeof(t));
+    };
+    double r1[9], r2[9], r3[9], tmp[9], e2g[9];
+    rz(ra_ngp + 0.5 * kPi, r1);
+    rx(0.5 * kPi - dec_ngp, r2);
+    rz(-l_node, r3);
+    mul(r2, r1, tmp);
+    mul(r3, tmp, e2g);  // v_gal = e2g v_eq
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) m[3 * i + j] = e2g[3 * j + i];
+}
+
+}  // namespace xm
+
+using namespace xm;
+
+extern "C" const char* xm_status_str(xm_status s) {
+    switch (s) {
+        case XM_OK: return "ok";
+        case XM_EINVAL: return "invalid argument";
+        case XM_ENOMEM: return "out of memory";
+        case XM_ECUDA: return "CUDA error";
+        case XM_ETIMEOUT: return "timed out";
+        case XM_EOVERFLOW: return "overflow";
+        case XM_EBUSY: return "busy (admission refused)";
+        case XM_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* xm_last_error(void) { return g_err; }
+
+extern "C" const char* xm_version(void) { return "xm 0.1 (sm_103a)"; }
+
+extern "C" xm_status xm_set_allocator(void* (*alloc)(size_t, void*, void*),
+                                      void (*release)(void*, void*, void*), void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return set_error(XM_EINVAL, "xm_set_allocator: give both functions or neither");
+    std::lock_guard<std::mutex> g(g_hook_mu);
+    g_hook.alloc = alloc;
+    g_hook.release = release;
+    g_hook.ctx = ctx;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_get_stats(xm_stats* out) {
+    if (!out) return set_error(XM_EINVAL, "xm_get_stats: NULL");
+    out->candidates = g_stats[0].load();
+    out->rechecked = g_stats[1].load();
+    out->flipped = g_stats[2].load();
+    out->members = g_stats[3].load();
+    out->tie_resolved = g_stats[4].load();
+    out->kernel_launches = g_stats[5].load();
+    return XM_OK;
+}
+
+extern "C" xm_status xm_reset_stats(void) {
+    for (auto& c : g_stats) c.store(0);
+    return XM_OK;
+}
+
+extern "C" xm_status xm_prof_enable(int32_t on) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    drain_locked();
+    g_prof_tot.clear();
+    g_prof_on = on != 0;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_prof_read(const char* kernel, double* total_ms, int64_t* launches) {
+    if (!kernel) return set_error(XM_EINVAL, "xm_prof_read: NULL name");
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    drain_locked();
+    auto it = g_prof_tot.find(kernel);
+    if (total_ms) *total_ms = it == g_prof_tot.end() ? 0.0 : it->second.first;
+    if (launches) *launches = it == g_prof_tot.end() ? 0 : it->second.second;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_prof_entry(int32_t i, const char** kernel, double* total_ms,
+                                   int64_t* launches) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    drain_locked();
+    if (i < 0 || i >= (int32_t)g_prof_tot.size()) return XM_EOVERFLOW;
+    auto it = g_prof_tot.begin();
+    std::advance(it, i);
+    if (kernel) *kernel = it->first.c_str();
+    if (total_ms) *total_ms = it->second.first;
+    if (launches) *launches = it->second.second;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream) {
+    if (bytes == 0) return XM_OK;
+    if (!dst || !src) return set_error(XM_EINVAL, "xm_copy_to_host: NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "xm_copy_to_host");
+    return XM_OK;
+}
+
+// Host-only: the library's galactic -> equatorial rotation (row major).
+extern "C" xm_status xm_frame_matrix(double m[9]) {
+    if (!m) return set_error(XM_EINVAL, "xm_frame_matrix: NULL");
+    gal_to_eq(m);
+    return XM_OK;
+}

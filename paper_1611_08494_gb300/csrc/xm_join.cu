@@ -1,0 +1,222 @@
+// xm_join.cu -- the join types of paper §2.2 over a selected pair set.
+//
+// i) 1 and 2: the selected pairs; ii) 1 or 2: pairs, unmatched A rows and
+// unmatched B rows; iii) all from 1 (2): pairs plus unmatched A (B) rows;
+// iv) 1 not 2 (2 not 1): unmatched A (B) rows; v) 1 xor 2: unmatched A and
+// unmatched B rows. A source is matched when it appears in the selected
+// pairs. Row order: rows carrying an A source in ascending (a_row, b_row),
+// then unmatched B rows in ascending b_row.
+//
+// Device steps: a bitset of matched B rows (idempotent atomicOr, so the
+// result is deterministic), rows per A source and their prefix sum, unmatched
+// B counts per 32-row word and their prefix sum, then two writers.
+#include <math.h>
+
+#include <new>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+namespace {
+
+constexpr int kBlock = 256;
+
+unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+__global__ void k_mark_b(const int64_t* __restrict__ b_row, int64_t n, uint32_t* __restrict__ bits) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t b = b_row[i];
+    if (b >= 0) atomicOr(&bits[b >> 5], 1u << (b & 31));
+}
+
+// Rows each A source contributes, and the number of unmatched A sources.
+__global__ void k_rows_a(const int32_t* __restrict__ count, int64_t nA, int sel_all,
+                         int with_pairs, int with_un_a, int32_t* __restrict__ rows,
+                         unsigned long long* __restrict__ n_un_a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nA) return;
+    int32_t c = count[i];
+    int32_t sel = sel_all ? c : (c > 0 ? 1 : 0);
+    int32_t r = with_pairs ? sel : 0;
+    if (sel == 0 && with_un_a) r = 1;
+    rows[i] = r;
+    uint32_t mask = __activemask();
+    uint32_t un = __popc(__ballot_sync(mask, c == 0));
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && un) atomicAdd(n_un_a, (unsigned long long)un);
+}
+
+__device__ __forceinline__ uint32_t word_valid(int64_t w, int64_t nB) {
+    int64_t rem = nB - (w << 5);
+    return rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+}
+
+__global__ void k_word_unmatched(const uint32_t* __restrict__ bits, int64_t nwords, int64_t nB,
+                                 int32_t* __restrict__ wcount) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    wcount[w] = __popc(~bits[w] & word_valid(w, nB));
+}
+
+__global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off,
+                          const int64_t* __restrict__ pb, const double* __restrict__ ps,
+                          const int64_t* __restrict__ best_b, const double* __restrict__ best_s,
+                          const int64_t* __restrict__ row_off, int64_t nA, int sel_all,
+                          int with_pairs, int with_un_a, int64_t* __restrict__ oa,
+                          int64_t* __restrict__ ob, double* __restrict__ os) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nA) return;
+    int32_t c = count[i];
+    int64_t o = row_off[i];
+    if (c > 0) {
+        if (!with_pairs) return;
+        if (sel_all) {
+            int64_t p = pair_off[i];
+            for (int32_t k = 0; k < c; k++) {
+                oa[o + k] = i;
+                ob[o + k] = pb[p + k];
+                os[o + k] = ps[p + k];
+            }
+        } else {
+            oa[o] = i;
+            ob[o] = best_b[i];
+            os[o] = best_s[i];
+        }
+    } else if (with_un_a) {
+        oa[o] = i;
+        ob[o] = -1;
+        os[o] = NAN;
+    }
+}
+
+__global__ void k_write_b(const uint32_t* __restrict__ bits, const int64_t* __restrict__ word_off,
+                          int64_t nB, int64_t base, int64_t* __restrict__ oa,
+                          int64_t* __restrict__ ob, double* __restrict__ os) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nB) return;
+    int64_t w = j >> 5;
+    uint32_t un = ~bits[w] & word_valid(w, nB);
+    uint32_t bit = 1u << (j & 31);
+    if (!(un & bit)) return;
+    int64_t o = base + word_off[w] + __popc(un & (bit - 1u));
+    oa[o] = -1;
+    ob[o] = j;
+    os[o] = NAN;
+}
+
+}  // namespace
+}  // namespace xm
+
+using namespace xm;
+
+static void free_rows(xm_rows* J) {
+    if (!J) return;
+    dev_free(J->a_row, nullptr);
+    delete J;
+}
+
+extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join_type,
+                             void* stream, xm_rows** out) {
+    if (!out) return set_error(XM_EINVAL, "xm_join: out is NULL");
+    *out = nullptr;
+    if (!R) return set_error(XM_EINVAL, "xm_join: NULL result");
+    if (selection != XM_SEL_ALL && selection != XM_SEL_BEST)
+        return set_error(XM_EINVAL, "xm_join: selection must be ALL or BEST");
+    if (!(R->selection & selection))
+        return set_error(XM_EINVAL, "xm_join: selection not computed by xm_match");
+    if (join_type < XM_JOIN_AND || join_type > XM_JOIN_XOR)
+        return set_error(XM_EINVAL, "xm_join: bad join type %d", join_type);
+    const bool with_pairs = join_type == XM_JOIN_AND || join_type == XM_JOIN_OR ||
+                            join_type == XM_JOIN_ALL1 || join_type == XM_JOIN_ALL2;
+    const bool with_un_a = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL1 ||
+                           join_type == XM_JOIN_NOT1_2 || join_type == XM_JOIN_XOR;
+    const bool with_un_b = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL2 ||
+                           join_type == XM_JOIN_NOT2_1 || join_type == XM_JOIN_XOR;
+    const int sel_all = selection == XM_SEL_ALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nA = R->n_a, nB = R->n_b;
+    const int64_t nwords = (nB + 31) / 32;
+    xm_rows* J = new (std::nothrow) xm_rows();
+    if (!J) return set_error(XM_ENOMEM, "xm_join: host allocation");
+
+    uint32_t* bits = (uint32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
+    int32_t* rows = (int32_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int32_t), s);
+    int64_t* row_off = (int64_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int64_t), s);
+    int32_t* wcount = (int32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int32_t), s);
+    int64_t* word_off = (int64_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int64_t), s);
+    int64_t* small = (int64_t*)dev_alloc(4 * sizeof(int64_t), s);
+    auto body = [&]() -> xm_status {
+        if (!bits || !rows || !row_off || !wcount || !word_off || !small)
+            return set_error(XM_ENOMEM, "xm_join: work buffers");
+        cudaError_t e = cudaMemsetAsync(bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 4 * sizeof(int64_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+        if (sel_all) {
+            if (R->n_pairs > 0)
+                XM_LAUNCH("k_mark_b", grid_for(R->n_pairs), kBlock, 0, s, k_mark_b, R->b_row,
+                          R->n_pairs, bits);
+        } else if (nA > 0) {
+            XM_LAUNCH("k_mark_b", grid_for(nA), kBlock, 0, s, k_mark_b, R->best_b, nA, bits);
+        }
+        if (nA > 0)
+            XM_LAUNCH("k_rows_a", grid_for(nA), kBlock, 0, s, k_rows_a, R->count, nA, sel_all,
+                      (int)with_pairs, (int)with_un_a, rows, (unsigned long long*)small + 2);
+        xm_status r = exclusive_scan_i32(rows, row_off, nA, small + 0, s);
+        if (r != XM_OK) return r;
+        if (nwords > 0)
+            XM_LAUNCH("k_word_unmatched", grid_for(nwords), kBlock, 0, s, k_word_unmatched, bits,
+                      nwords, nB, wcount);
+        r = exclusive_scan_i32(wcount, word_off, nwords, small + 1, s);
+        if (r != XM_OK) return r;
+        int64_t h[4];
+        e = cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_join sync");
+        const int64_t total_a = h[0], un_b = h[1];
+        J->n_unmatched_a = h[2];
+        J->n_unmatched_b = un_b;
+        J->n = total_a + (with_un_b ? un_b : 0);
+        int64_t nr = J->n > 0 ? J->n : 1;
+        J->a_row = (int64_t*)dev_alloc(nr * (2 * sizeof(int64_t) + sizeof(double)), s);
+        if (!J->a_row) return set_error(XM_ENOMEM, "xm_join: %lld rows", (long long)J->n);
+        J->b_row = J->a_row + nr;
+        J->sep = (double*)(J->b_row + nr);
+        if (nA > 0)
+            XM_LAUNCH("k_write_a", grid_for(nA), kBlock, 0, s, k_write_a, R->count, R->pair_off,
+                      R->b_row, R->sep, R->best_b, R->best_sep, row_off, nA, sel_all,
+                      (int)with_pairs, (int)with_un_a, J->a_row, J->b_row, J->sep);
+        if (with_un_b && nB > 0)
+            XM_LAUNCH("k_write_b", grid_for(nB), kBlock, 0, s, k_write_b, bits, word_off, nB,
+                      total_a, J->a_row, J->b_row, J->sep);
+        return XM_OK;
+    };
+    xm_status st = body();
+    dev_free(bits, s);
+    dev_free(rows, s);
+    dev_free(row_off, s);
+    dev_free(wcount, s);
+    dev_free(word_off, s);
+    dev_free(small, s);
+    if (st != XM_OK) {
+        free_rows(J);
+        return st;
+    }
+    *out = J;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_rows_free(xm_rows* J) {
+    free_rows(J);
+    return XM_OK;
+}
+
+extern "C" xm_status xm_rows_get(const xm_rows* J, xm_rows_view* v) {
+    if (!J || !v) return set_error(XM_EINVAL, "xm_rows_get: NULL argument");
+    v->n = J->n;
+    v->a_row = J->a_row;
+    v->b_row = J->b_row;
+    v->sep_arcsec = J->sep;
+    v->n_unmatched_a = J->n_unmatched_a;
+    v->n_unmatched_b = J->n_unmatched_b;
+    return XM_OK;
+}

@@ -1,0 +1,345 @@
+"""Thin ctypes binding of the C ABI in ``include/xm.h`` (same names).
+
+Argument marshalling only: every step of the cross-match runs in the CUDA
+library ``_lib/libxm.so``. PyTorch provides device memory and streams; inputs
+may be CUDA tensors (used in place), CPU tensors or numpy arrays (copied by
+the library). Outputs are zero-copy CUDA tensors that keep their result
+handle alive. Importing this module without the built library raises: there
+is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libxm.so")
+
+EQ, GAL = 0, 1
+CIRCLE, ELLIPSE, RECT = 0, 1, 2
+SEL_ALL, SEL_BEST = 1, 2
+PREC_FP64, PREC_FP32 = 0, 1
+JOINS = {"and": 0, "or": 1, "all1": 2, "all2": 3, "not1_2": 4, "not2_1": 5, "xor": 6}
+STATUS = {0: "XM_OK", 1: "XM_EINVAL", 2: "XM_ENOMEM", 3: "XM_ECUDA", 4: "XM_ETIMEOUT",
+          5: "XM_EOVERFLOW", 6: "XM_EBUSY", 7: "XM_EUNSUPPORTED"}
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; "
+                      "g.build()'` (the cross-match has no CPU fallback)")
+lib = ctypes.CDLL(_LIB_PATH)
+
+_p = ctypes.c_void_p
+_i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class Columns(ctypes.Structure):
+    _fields_ = [("lon_deg", _p), ("lat_deg", _p), ("id", _p), ("n", _i64), ("frame", _i32),
+                ("on_device", _i32)]
+
+
+class Region(ctypes.Structure):
+    _fields_ = [("shape", _i32), ("pa_dir", _i32), ("a", _f64), ("b", _f64), ("pa_deg", _f64),
+                ("a_col", _p), ("b_col", _p), ("pa_col", _p), ("size_scale", _f64),
+                ("size_unit_arcsec", _f64), ("pa_zero_deg", _f64)]
+
+
+class IndexOpts(ctypes.Structure):
+    _fields_ = [("zone_height_arcsec", _f64), ("build_fp64", _i32), ("reserved", _i32)]
+
+
+class MatchOpts(ctypes.Structure):
+    _fields_ = [("selection", _i32), ("precision", _i32), ("block", _i32), ("reserved", _i32)]
+
+
+class ResultView(ctypes.Structure):
+    _fields_ = [("n_pairs", _i64), ("n_a", _i64), ("n_b", _i64), ("a_row", _p), ("b_row", _p),
+                ("sep_arcsec", _p), ("count", _p), ("best_b_row", _p), ("best_sep_arcsec", _p)]
+
+
+class RowsView(ctypes.Structure):
+    _fields_ = [("n", _i64), ("a_row", _p), ("b_row", _p), ("sep_arcsec", _p),
+                ("n_unmatched_a", _i64), ("n_unmatched_b", _i64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_uint64), ("rechecked", ctypes.c_uint64),
+                ("flipped", ctypes.c_uint64), ("members", ctypes.c_uint64),
+                ("tie_resolved", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+def _sig(name, res, *args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+xm_status_str = _sig("xm_status_str", ctypes.c_char_p, _i32)
+xm_last_error = _sig("xm_last_error", ctypes.c_char_p)
+xm_version = _sig("xm_version", ctypes.c_char_p)
+xm_set_allocator = _sig("xm_set_allocator", _i32, _p, _p, _p)
+xm_get_stats = _sig("xm_get_stats", _i32, ctypes.POINTER(Stats))
+xm_reset_stats = _sig("xm_reset_stats", _i32)
+xm_prof_enable = _sig("xm_prof_enable", _i32, _i32)
+xm_prof_read = _sig("xm_prof_read", _i32, ctypes.c_char_p, ctypes.POINTER(_f64),
+                    ctypes.POINTER(_i64))
+xm_prof_entry = _sig("xm_prof_entry", _i32, _i32, ctypes.POINTER(ctypes.c_char_p),
+                     ctypes.POINTER(_f64), ctypes.POINTER(_i64))
+xm_build_index = _sig("xm_build_index", _i32, ctypes.POINTER(Columns), ctypes.POINTER(IndexOpts),
+                      _p, ctypes.POINTER(_p))
+xm_index_free = _sig("xm_index_free", _i32, _p)
+xm_index_info = _sig("xm_index_info", _i32, _p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                     ctypes.POINTER(_f64), ctypes.POINTER(_i64))
+xm_match = _sig("xm_match", _i32, _p, ctypes.POINTER(Columns), ctypes.POINTER(Region),
+                ctypes.POINTER(MatchOpts), _p, ctypes.POINTER(_p))
+xm_result_free = _sig("xm_result_free", _i32, _p)
+xm_result_get = _sig("xm_result_get", _i32, _p, ctypes.POINTER(ResultView))
+xm_join = _sig("xm_join", _i32, _p, _i32, _i32, _p, ctypes.POINTER(_p))
+xm_rows_free = _sig("xm_rows_free", _i32, _p)
+xm_rows_get = _sig("xm_rows_get", _i32, _p, ctypes.POINTER(RowsView))
+xm_copy_to_host = _sig("xm_copy_to_host", _i32, _p, _p, ctypes.c_size_t, _p)
+xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
+
+
+class XMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = STATUS.get(status, str(status))
+        msg = xm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {self.status}: {msg}")
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        raise XMError(status, where)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _f64_buffer(x, keep: list, on_device: Optional[bool]):
+    """Pointer to a contiguous float64 buffer; returns (ptr, is_device)."""
+    if x is None:
+        return None, on_device
+    if isinstance(x, torch.Tensor):
+        t = x.detach()
+        if t.dtype != torch.float64:
+            t = t.to(torch.float64)
+        t = t.contiguous()
+        keep.append(t)
+        return t.data_ptr(), t.is_cuda
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data, False
+
+
+def _i64_buffer(x, keep: list):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        t = x.detach().to(torch.int64).contiguous()
+        keep.append(t)
+        return t.data_ptr()
+    a = np.ascontiguousarray(x, dtype=np.int64)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def columns(lon, lat, frame=EQ, ids=None, keep=None):
+    keep = [] if keep is None else keep
+    lp, dev = _f64_buffer(lon, keep, None)
+    bp, dev2 = _f64_buffer(lat, keep, None)
+    if dev != dev2:
+        raise ValueError("lon and lat must both be on the device or both on the host")
+    n = len(lon)
+    if len(lat) != n:
+        raise ValueError("lon and lat differ in length")
+    return Columns(lp, bp, _i64_buffer(ids, keep), n, frame, int(bool(dev))), keep
+
+
+class _DevArray:
+    """__cuda_array_interface__ holder that keeps its owner alive."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self.owner = owner
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr or 0), True), "version": 3,
+                                         "strides": None}
+
+
+def _tensor(ptr, n, typestr, owner):
+    if n == 0 or not ptr:
+        dt = {"<i8": torch.int64, "<f8": torch.float64, "<i4": torch.int32}[typestr]
+        return torch.empty(0, dtype=dt, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n, typestr, owner), device="cuda")
+
+
+class Index:
+    """Resident B index (paper §2.3). ``xm_build_index``."""
+
+    def __init__(self, lon, lat, frame=EQ, ids=None, zone_height_arcsec=0.0, build_fp64=False,
+                 stream=None):
+        cols, keep = columns(lon, lat, frame, ids)
+        opts = IndexOpts(float(zone_height_arcsec), int(bool(build_fp64)), 0)
+        h = _p()
+        check(xm_build_index(ctypes.byref(cols), ctypes.byref(opts), _stream_handle(stream),
+                             ctypes.byref(h)), "xm_build_index")
+        self.handle = h.value
+        self.n = cols.n
+        self.frame = frame
+
+    def info(self):
+        n, z, hb = _i64(), _i64(), _i64()
+        h = _f64()
+        check(xm_index_info(self.handle, ctypes.byref(n), ctypes.byref(z), ctypes.byref(h),
+                            ctypes.byref(hb)), "xm_index_info")
+        return {"n": n.value, "zones": z.value, "zone_height_arcsec": h.value,
+                "device_bytes": hb.value}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            xm_index_free(h)
+            self.handle = None
+
+
+def region(shape=CIRCLE, a=1.0, b=None, pa=0.0, a_col=None, b_col=None, pa_col=None,
+           size_scale=1.0, size_unit_arcsec=1.0, pa_zero_deg=0.0, pa_dir=1, keep=None):
+    keep = [] if keep is None else keep
+    ap, _ = _f64_buffer(a_col, keep, None)
+    bp, _ = _f64_buffer(b_col, keep, None)
+    pp, _ = _f64_buffer(pa_col, keep, None)
+    return Region(int(shape), int(pa_dir), float(a), float(a if b is None else b), float(pa),
+                  ap, bp, pp, float(size_scale), float(size_unit_arcsec), float(pa_zero_deg)), keep
+
+
+class Result:
+    """Members of every A source. ``xm_match``."""
+
+    def __init__(self, index: Index, lon, lat, frame=EQ, selection=SEL_ALL | SEL_BEST,
+                 precision=PREC_FP32, block=0, stream=None, **region_kw):
+        cols, keep = columns(lon, lat, frame)
+        reg, keep = region(keep=keep, **region_kw)
+        opts = MatchOpts(int(selection), int(precision), int(block), 0)
+        h = _p()
+        check(xm_match(index.handle, ctypes.byref(cols), ctypes.byref(reg), ctypes.byref(opts),
+                       _stream_handle(stream), ctypes.byref(h)), "xm_match")
+        self.handle = h.value
+        self.index = index
+        v = ResultView()
+        check(xm_result_get(self.handle, ctypes.byref(v)), "xm_result_get")
+        self.view = v
+        self.n_pairs, self.n_a, self.n_b = v.n_pairs, v.n_a, v.n_b
+
+    # zero-copy device tensors
+    @property
+    def a_row(self):
+        return _tensor(self.view.a_row, self.n_pairs, "<i8", self)
+
+    @property
+    def b_row(self):
+        return _tensor(self.view.b_row, self.n_pairs, "<i8", self)
+
+    @property
+    def sep(self):
+        return _tensor(self.view.sep_arcsec, self.n_pairs, "<f8", self)
+
+    @property
+    def count(self):
+        return _tensor(self.view.count, self.n_a, "<i4", self)
+
+    @property
+    def best_b(self):
+        return _tensor(self.view.best_b_row, self.n_a if self.view.best_b_row else 0, "<i8", self)
+
+    @property
+    def best_sep(self):
+        return _tensor(self.view.best_sep_arcsec, self.n_a if self.view.best_sep_arcsec else 0,
+                       "<f8", self)
+
+    def join(self, join_type: str, selection=SEL_ALL, stream=None) -> "Rows":
+        return Rows(self, join_type, selection, stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            xm_result_free(h)
+            self.handle = None
+
+
+class Rows:
+    """Rows of one join type (paper §2.2). ``xm_join``."""
+
+    def __init__(self, result: Result, join_type: str, selection=SEL_ALL, stream=None):
+        h = _p()
+        check(xm_join(result.handle, int(selection), JOINS[join_type], _stream_handle(stream),
+                      ctypes.byref(h)), "xm_join")
+        self.handle = h.value
+        self.result = result
+        v = RowsView()
+        check(xm_rows_get(self.handle, ctypes.byref(v)), "xm_rows_get")
+        self.view = v
+        self.n = v.n
+        self.n_unmatched_a, self.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
+
+    @property
+    def a_row(self):
+        return _tensor(self.view.a_row, self.n, "<i8", self)
+
+    @property
+    def b_row(self):
+        return _tensor(self.view.b_row, self.n, "<i8", self)
+
+    @property
+    def sep(self):
+        return _tensor(self.view.sep_arcsec, self.n, "<f8", self)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            xm_rows_free(h)
+            self.handle = None
+
+
+def stats() -> dict:
+    s = Stats()
+    check(xm_get_stats(ctypes.byref(s)), "xm_get_stats")
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def reset_stats() -> None:
+    check(xm_reset_stats(), "xm_reset_stats")
+
+
+def prof_enable(on: bool) -> None:
+    check(xm_prof_enable(int(bool(on))), "xm_prof_enable")
+
+
+def prof_read(kernel: str):
+    ms, n = _f64(), _i64()
+    check(xm_prof_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)), "xm_prof_read")
+    return ms.value, n.value
+
+
+def prof_all() -> dict:
+    out, i = {}, 0
+    while True:
+        name, ms, n = ctypes.c_char_p(), _f64(), _i64()
+        if xm_prof_entry(i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(n)) != 0:
+            return out
+        out[name.value.decode()] = (ms.value, n.value)
+        i += 1
+
+
+def frame_matrix() -> np.ndarray:
+    m = (_f64 * 9)()
+    check(xm_frame_matrix(m), "xm_frame_matrix")
+    return np.array(m[:]).reshape(3, 3)
