@@ -1,0 +1,383 @@
+"""Benchmark of the sky cross-match hot path (one JSON line on stdout).
+
+A step is one pass of the whole path over one synthetic workload: build the
+index of catalogue B (ingest, radix sort on (zone, RA), bucket tables, cell
+offsets), match catalogue A against it with both selections (all pairs and
+best pair), and build the "1 or 2" join rows. Default workload: the
+clump-vs-compact-source case of the paper's §3 use, A = 200,000 per-source
+ellipses against B = 5,000,000 point sources in galactic coordinates.
+
+value      A sources per second over K timed steps, inputs resident in HBM,
+           float32 path with float64 recheck; L2 flushed before every step.
+e2e        the same step through the C ABI with pinned host buffers, the
+           host->device copies of the catalogues and the device->host copy of
+           the join rows and best pairs inside the timed region.
+fp64_path  the same step on the all-float64 path.
+roofline   the dominant kernel, timed with CUDA events on its stream during
+           the timed steps, against the measured HBM copy bandwidth.
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+
+--impl reference times that oracle as the reference arm. Under torchrun
+(N > 1) each rank runs its own copy of the workload (weak scaling, no
+data-path collective); rank 0 prints the line with the max time over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A-sources cross-matched/sec, FP32+FP64-recheck vs FP64 path; serving p99 ms"
+UNIT = "A-sources/s"
+KERNELS_FOR_ROOFLINE = ("k_scan_fp32_count", "k_digit_scatter", "k_scan_fp32_emit", "k_gather_b")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--zone-height", type=float, default=0.0, help="arcsec; 0 = tuned default")
+    p.add_argument("--cpu-sample", type=int, default=0, help="A sources in the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(seed_offset=0):
+    from paper_1611_08494_gb300 import synth
+
+    d = synth.c2(seed=1002 + seed_offset)
+    d["desc"] = ("c2 clump-vs-compact-source: A=200000 per-source ellipses (a 5-60 arcsec "
+                 "log-uniform, b/a 0.3-1, PA 0-180), B=5000000, galactic l 0-60 |b|<=1 "
+                 "density exp(-|b|/0.3deg)")
+    return d
+
+
+# ------------------------------------------------------------------- oracle
+
+def oracle_sample(d, n_sample, nthreads):
+    """Times the oracle (as it stands) on the first n_sample A sources against
+    all of B: its voxel indexing of B, the pair tests and best selection."""
+    import oracle
+
+    sub = np.arange(n_sample, dtype=np.int64)
+    t = time.perf_counter()
+    r = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], a_frame=d["a_frame"],
+                     b_frame=d["b_frame"], subset=sub, nthreads=nthreads, **d["region"])
+    oracle.best(r, d["a_lon"].size)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(d, n_sample=0):
+    nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if not n_sample:
+        # size the sample so the run takes ~10-20 s of CPU work
+        dt = oracle_sample(d, 2000, nthreads)
+        n_sample = int(min(d["a_lon"].size, max(2000, 2000 * 12.0 / max(dt, 1e-3))))
+    dt = oracle_sample(d, n_sample, nthreads)
+    return {"value": n_sample / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"first {n_sample} of {d['a_lon'].size} A sources against all "
+                      f"{d['b_lon'].size} B (voxel grid over B, pair tests, best), "
+                      f"{dt:.2f} s on {nthreads} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    d = workload()
+    cb = cpu_baseline(d, args.cpu_sample)
+    n_s = int(cb["sample"].split()[1])
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(d, min(n_s, 2000), cb["cores"])
+    for _ in range(args.steps):
+        times.append(oracle_sample(d, n_s, cb["cores"]))
+    tot = sum(times)
+    v = n_s * len(times) / tot
+    cb = dict(cb, value=v)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": d["desc"], "sample_a": n_s},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in (self.out or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1611_08494_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(cs, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1611_08494_gb300 import xm
+
+    d = workload(seed_offset=rank)
+    n_a, n_b = d["a_lon"].size, d["b_lon"].size
+    cu = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")  # noqa: E731
+    dev = {k: cu(d[k]) for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
+    reg_dev = {k: (cu(v) if isinstance(v, np.ndarray) else v) for k, v in d["region"].items()}
+    zone_h = args.zone_height or 12.0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(prec, fp64_index, cols=None, reg=None, copy_out=False):
+        cols = cols or dev
+        reg = reg or reg_dev
+        idx = xm.Index(cols["b_lon"], cols["b_lat"], frame=d["b_frame"],
+                       zone_height_arcsec=zone_h, build_fp64=fp64_index)
+        res = xm.Result(idx, cols["a_lon"], cols["a_lat"], frame=d["a_frame"], precision=prec,
+                        selection=xm.SEL_ALL | xm.SEL_BEST, **reg)
+        rows = res.join("or")
+        out = None
+        if copy_out:
+            out = [rows.a_row.to("cpu", non_blocking=True), rows.b_row.to("cpu", non_blocking=True),
+                   rows.sep.to("cpu", non_blocking=True), res.best_b.to("cpu", non_blocking=True),
+                   res.best_sep.to("cpu", non_blocking=True)]
+        return idx, res, rows, out
+
+    def timed(prec, fp64_index, steps, warmup, cols=None, reg=None, copy_out=False,
+              profile=False):
+        for _ in range(warmup):
+            step(prec, fp64_index, cols, reg, copy_out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        xm.reset_stats()
+        if profile:
+            xm.prof_enable(True)
+        ms, bytes_out = [], 0
+        for _ in range(steps):
+            flush.zero_()  # evict the inputs from L2 between steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, res, rows, out = step(prec, fp64_index, cols, reg, copy_out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if out is not None:
+                bytes_out = sum(t.numel() * t.element_size() for t in out)
+        torch.cuda.synchronize()
+        prof = xm.prof_all() if profile else {}
+        if profile:
+            xm.prof_enable(False)
+        st = xm.stats()
+        if world > 1:
+            dist.barrier()
+        return ms, st, prof, res, rows, bytes_out
+
+    # float32 + float64 recheck (the product path)
+    with Clocks(local) as clk:
+        ms, st, prof, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup,
+                                           profile=True)
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * n_a * args.steps / (total_ms / 1e3)
+    launches = st["kernel_launches"]
+
+    # all-float64 path
+    ms64, _, _, _, _, _ = timed(xm.PREC_FP64, True, max(3, args.steps // 2), 1)
+    v64 = n_a * len(ms64) / (sum(ms64) / 1e3)
+
+    # end to end through the C ABI from pinned host memory
+    host = {k: torch.as_tensor(d[k]).pin_memory() for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
+    reg_host = {k: (torch.as_tensor(v).pin_memory() if isinstance(v, np.ndarray) else v)
+                for k, v in d["region"].items()}
+    ms_e2e, _, _, _, _, d2h = timed(xm.PREC_FP32, False, max(3, args.steps // 2), 1, cols=host,
+                                    reg=reg_host, copy_out=True)
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + \
+        sum(t.numel() * t.element_size() for t in reg_host.values() if hasattr(t, "numel"))
+    v_e2e = n_a * len(ms_e2e) / (sum(ms_e2e) / 1e3)
+
+    # roofline of the dominant kernel
+    roof = roofline(prof, st, args.steps, n_a, n_b, zone_h)
+
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": d["desc"], "n_a": n_a, "n_b": n_b,
+                   "step": "build B index + match (all and best pairs) + join '1 or 2'",
+                   "precision": "float32 tests, float64 recheck in the guard band",
+                   "zone_height_arcsec": zone_h, "l2": "flushed (256 MiB write) before each step",
+                   "pairs": int(res.n_pairs), "join_rows": int(rows.n)},
+        "e2e": {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": statistics.mean(ms64)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in
+                                sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]},
+        "stats_per_step": {k: v // args.steps for k, v in st.items()},
+        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peaks.get("_source")},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(d, args.cpu_sample)
+    print(json.dumps(line), flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "_source": "fallback"}
+
+
+def sort_passes(zone_height_arcsec):
+    """Digit passes of the (zone, RA) sort: bits 8 .. 32 + bits(nz - 1)."""
+    nz = int(np.ceil(648000.0 / zone_height_arcsec - 1e-9))
+    return (32 + int(nz - 1).bit_length() - 8 + 7) // 8
+
+
+def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, zone_h):
+    """Bytes the method must move per launch of a kernel:
+    k_onesweep   per key and pass 8 B key + 4 B row, read and written (B and A
+                 sorts, the same number of passes each);
+    k_scan_fp32_count  per A 16 B position + 24 B region columns + 16 B best
+                 row, per candidate 12 B (offsets + RA key);
+    k_gather_b   per B 16 B position read + 16 B record + 16 B position
+                 written."""
+    if kernel == "k_onesweep":
+        return steps * sort_passes(zone_h) * 24 * (n_b + n_a) / launches
+    if kernel == "k_scan_fp32_count":
+        return n_a * (16 + 24 + 16) + st["candidates"] / steps * 12
+    if kernel == "k_gather_b":
+        return n_b * (16 + 16 + 16)
+    return None
+
+
+def roofline(prof, st, steps, n_a, n_b, zone_h):
+    if not prof:
+        return None
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    name, (tot_ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = tot_ms / launches
+    alg = algorithmic_bytes(name, st, steps, launches, n_a, n_b, zone_h)
+    out = {"kernel": name, "bound": "hbm", "peak": peak, "unit": "GB/s", "ms_per_launch": per_launch_ms,
+           "share_of_step": tot_ms / steps, "achieved": None, "frac": None, "traffic": None,
+           "peak_source": "of measured" if peaks.get("_source") == "measured" else "of fallback"}
+    if alg is None:
+        return out
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    out.update(achieved=achieved, frac=achieved / peak, algorithmic_bytes=alg,
+               traffic=traffic_record(name))
+    return out
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec or rec.get("source_hash") != source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,21 @@ xm_status cuda_fail(cudaError_t e, const char* what) {
     return set_error(XM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// The default stream-ordered pool keeps freed memory cached instead of
+// returning it to the driver at every synchronisation (release threshold
+// raised once per device), so per-call temporaries cost no driver call.
+static void keep_pool_cached() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 1;
     AllocHook h;
@@ -86,6 +101,7 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
         h = g_hook;
     }
     if (h.alloc) return h.alloc(bytes, (void*)s, h.ctx);
+    keep_pool_cached();
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
         cudaGetLastError();  // clear the sticky-free error state of a failed allocation
@@ -138,6 +154,51 @@ cudaError_t launch_end(const char* name, cudaStream_t s) {
 
 void stats_add(const unsigned long long* c) {
     for (int k = 0; k < 5; k++) g_stats[k].fetch_add(c[k], std::memory_order_relaxed);
+}
+
+// Per-device counters the kernels add to directly (candidates, rechecked,
+// flipped, members, tie_resolved), so no call waits just to read them.
+static unsigned long long* g_dev_stats[64] = {};
+static std::mutex g_dev_stats_mu;
+
+unsigned long long* device_stats() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(g_dev_stats_mu);
+    if (!g_dev_stats[dev]) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, 8 * sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, 8 * sizeof(unsigned long long));
+        g_dev_stats[dev] = (unsigned long long*)p;
+    }
+    return g_dev_stats[dev];
+}
+
+static void device_stats_read(unsigned long long out[5]) {
+    for (int k = 0; k < 5; k++) out[k] = 0;
+    std::lock_guard<std::mutex> g(g_dev_stats_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; d++) {
+        if (!g_dev_stats[d]) continue;
+        unsigned long long h[8];
+        cudaSetDevice(d);
+        if (cudaMemcpy(h, g_dev_stats[d], sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
+            for (int k = 0; k < 5; k++) out[k] += h[k];
+    }
+    cudaSetDevice(cur);
+}
+
+static void device_stats_reset() {
+    std::lock_guard<std::mutex> g(g_dev_stats_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; d++) {
+        if (!g_dev_stats[d]) continue;
+        cudaSetDevice(d);
+        cudaMemset(g_dev_stats[d], 0, 8 * sizeof(unsigned long long));
+    }
+    cudaSetDevice(cur);
 }
 
 // Galactic -> equatorial rotation from the IAU frame angles (north galactic
@@ -211,17 +272,20 @@ extern "C" xm_status xm_set_allocator(void* (*alloc)(size_t, void*, void*),
 
 extern "C" xm_status xm_get_stats(xm_stats* out) {
     if (!out) return set_error(XM_EINVAL, "xm_get_stats: NULL");
-    out->candidates = g_stats[0].load();
-    out->rechecked = g_stats[1].load();
-    out->flipped = g_stats[2].load();
-    out->members = g_stats[3].load();
-    out->tie_resolved = g_stats[4].load();
+    unsigned long long d[5];
+    device_stats_read(d);  // waits for the kernels that add to them
+    out->candidates = g_stats[0].load() + d[0];
+    out->rechecked = g_stats[1].load() + d[1];
+    out->flipped = g_stats[2].load() + d[2];
+    out->members = g_stats[3].load() + d[3];
+    out->tie_resolved = g_stats[4].load() + d[4];
     out->kernel_launches = g_stats[5].load();
     return XM_OK;
 }
 
 extern "C" xm_status xm_reset_stats(void) {
     for (auto& c : g_stats) c.store(0);
+    device_stats_reset();
     return XM_OK;
 }
 

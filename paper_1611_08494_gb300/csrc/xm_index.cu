@@ -1,16 +1,20 @@
 // xm_index.cu -- the resident index of the second catalogue (paper §2.3).
 //
-// The paper assigns every source of the second catalogue to a sky cell so a
+// The paper files every source of the second catalogue under a sky cell so a
 // source of the first catalogue need only look at nearby cells. Here the
-// partition is a set of declination zones cut into RA cells, realised by a
-// stable radix sort of the sources on (zone, RA key):
-//   k_ingest_b    longitude normalisation, validity, (zone, ra_key) sort key
+// partition is a set of equal-height declination zones cut into RA cells,
+// realised by a stable radix sort of the sources on (zone, RA key):
+//   k_zone_geom   per zone: centre, its sin/cos, number and width of RA cells
+//   k_ingest_b    per source, input order: validity, fixed-point position,
+//                 the 16-byte record (float32 offsets in its cell's tangent
+//                 frame, RA key, row), sort key; exact position kept by row
 //   radix sort    (xm_sort.cu)
-//   k_zone_table  per zone: centre, its sin/cos, number and width of RA cells
 //   k_zone_start  first sorted source of each zone (binary search)
-//   k_gather_b    per sorted source: float32 offsets in its cell's tangent
-//                 frame, float64 (RA, Dec), optional float64 unit vector, id
+//   k_zone_rows   rows of each zone, size of its RA bucket table (about one
+//                 bucket per 4 sources); prefix sum; k_zone_lut the offsets
+//   k_gather_b    records into (zone, RA) order, and the bucket tables
 #include <math.h>
+#include <string.h>
 
 #include <new>
 
@@ -22,22 +26,36 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ bool coord_ok(double lon, double lat) {
-    return isfinite(lon) && isfinite(lat) && lat >= -90.0 && lat <= 90.0;
-}
-
-// Longitude modulo 360 and latitude, in radians.
-__device__ __forceinline__ void norm_radec(double lon, double lat, double* ra, double* dec) {
-    double l = fmod(lon, 360.0);
-    if (l < 0) l += 360.0;
-    *ra = l * kDeg;
-    *dec = lat * kDeg;
+__global__ void k_zone_geom(int32_t nz, ZoneInfo* __restrict__ zones) {
+    const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= nz) return;
+    const double h = kPi / nz;
+    const double lo = -kHalfPi + z * h;
+    const double hi = lo + h;
+    ZoneInfo Z;
+    memset(&Z, 0, sizeof(Z));
+    Z.dec_c = -kHalfPi + (z + 0.5) * h;
+    sincos(Z.dec_c, &Z.sin_c, &Z.cos_c);
+    Z.sin_cf = (float)Z.sin_c;
+    Z.cos_cf = (float)Z.cos_c;
+    // widest edge of the zone: its cells are at most h wide there
+    const double cos_edge = (lo <= 0.0 && hi >= 0.0) ? 1.0 : cos(fmin(fabs(lo), fabs(hi)));
+    double nb = ceil(kTwoPi * cos_edge / h);
+    if (nb < 1) nb = 1;
+    if (nb > 1073741824.0) nb = 1073741824.0;
+    Z.nbins = (uint32_t)nb;
+    Z.binw = kTwoPi / nb;
+    Z.binw_f = (float)Z.binw;
+    zones[z] = Z;
 }
 
 __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restrict__ lat,
-                           int64_t n, double h, int32_t nz, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ vals, int32_t* err) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                           int64_t n, double zscale, int32_t nz, float h_f,
+                           const ZoneInfo* __restrict__ zones, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals, BRec* __restrict__ rec_in,
+                           double2* __restrict__ pos, double* __restrict__ px,
+                           double* __restrict__ py, double* __restrict__ pz, int32_t* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double lo = lon[i], la = lat[i];
     if (!coord_ok(lo, la)) {
@@ -45,75 +63,92 @@ __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restr
         lo = 0.0;
         la = 0.0;
     }
-    double ra, dec;
-    norm_radec(lo, la, &ra, &dec);
-    keys[i] = ((uint64_t)zone_of(dec, h, nz) << 32) | ra_key_of(ra);
+    lo = lon_mod360(lo);
+    const PosKey k = pos_key(lo, la, zscale, nz);
+    const uint32_t ra_key = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
+    const ZoneInfo& Z = zones[k.z];
+    const uint32_t bin = bin_of(ra_key, Z.nbins);
+    const LatTerms L = lat_terms(h_f * k.zfrac, Z.sin_cf, Z.cos_cf);
+    float sa, hav_a;
+    sin_hav(Z.binw_f * cells_from_centre(k.key64, Z.nbins, bin), &sa, &hav_a);
+    BRec r;
+    r.xi = L.cd * sa;
+    r.eta = fmaf(L.cd * Z.sin_cf, hav_a, L.sdd);
+    r.ra_key = ra_key;
+    r.row = (int32_t)i;
+    rec_in[i] = r;
+    keys[i] = ((uint64_t)k.z << 32) | ra_key;
     vals[i] = (uint32_t)i;
-}
-
-__global__ void k_zone_table(int32_t nz, double h, ZoneInfo* __restrict__ zones) {
-    int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= nz) return;
-    double lo = -kHalfPi + z * h;
-    double hi = fmin(lo + h, kHalfPi);
-    ZoneInfo Z;
-    Z.dec_c = 0.5 * (lo + hi);
-    sincos(Z.dec_c, &Z.sin_c, &Z.cos_c);
-    Z.sin_cf = (float)Z.sin_c;
-    Z.cos_cf = (float)Z.cos_c;
-    // widest edge of the zone: its cells are at most h wide there
-    double cos_edge = (lo <= 0.0 && hi >= 0.0) ? 1.0 : cos(fmin(fabs(lo), fabs(hi)));
-    double nb = ceil(kTwoPi * cos_edge / h);
-    if (nb < 1) nb = 1;
-    if (nb > 1073741824.0) nb = 1073741824.0;
-    Z.nbins = (uint32_t)nb;
-    Z.binw = kTwoPi / nb;
-    Z.pad = 0;
-    zones[z] = Z;
+    pos[i] = make_double2(lo, la);
+    if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
 }
 
 __global__ void k_zone_start(const uint64_t* __restrict__ keys, int64_t n, int32_t nz,
                              int64_t* __restrict__ zone_start) {
-    int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z > nz) return;
-    uint64_t target = (uint64_t)z << 32;
+    const uint64_t target = (uint64_t)z << 32;
     int64_t lo = 0, hi = n;
     while (lo < hi) {
-        int64_t mid = lo + ((hi - lo) >> 1);
+        const int64_t mid = lo + ((hi - lo) >> 1);
         if (keys[mid] < target) lo = mid + 1;
         else hi = mid;
     }
     zone_start[z] = lo;
 }
 
-__global__ void k_gather_b(const double* __restrict__ lon, const double* __restrict__ lat,
-                           const int64_t* __restrict__ id, const uint64_t* __restrict__ keys,
-                           const uint32_t* __restrict__ vals, int64_t n,
-                           const ZoneInfo* __restrict__ zones, BRec* __restrict__ rec,
-                           double2* __restrict__ pos, double* __restrict__ px,
-                           double* __restrict__ py, double* __restrict__ pz,
-                           int64_t* __restrict__ id_out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start,
+                            ZoneInfo* __restrict__ zones, int32_t* __restrict__ lut_cnt) {
+    const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= nz) return;
+    ZoneInfo& Z = zones[z];
+    Z.start = zone_start[z];
+    Z.end = zone_start[z + 1];
+    // RA buckets: a power of two, about one per 4 sources, at most 2^20
+    const int64_t m = Z.end - Z.start;
+    int lg = 0;
+    while (lg < 20 && ((int64_t)1 << lg) * 4 < m) lg++;
+    Z.lut_shift = 32u - (uint32_t)lg;
+    lut_cnt[z] = (1 << lg) + 1;
+}
+
+__global__ void k_zone_lut(int32_t nz, const int64_t* __restrict__ lut_off,
+                           ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut) {
+    const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= nz) return;
+    const int64_t base = lut_off[z];
+    zones[z].lut_base = base;
+    if (zones[z].end == zones[z].start) {  // empty zone: one empty bucket
+        lut[base] = 0;
+        lut[base + 1] = 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, uint32_t shift) {
+    return (uint32_t)((uint64_t)(uint32_t)key >> shift);
+}
+
+// Records into index order, and each zone's RA bucket table: bucket k holds
+// the first row (relative to the zone) whose key reaches it.
+__global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                           int64_t n, const BRec* __restrict__ rec_in,
+                           const ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut,
+                           BRec* __restrict__ rec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t row = vals[i];
-    uint64_t key = keys[i];
-    int32_t z = (int32_t)(key >> 32);
-    uint32_t ra_key = (uint32_t)key;
-    double lo = lon[row], la = lat[row];
-    if (!coord_ok(lo, la)) { lo = 0.0; la = 0.0; }  // the call fails anyway
-    double ra, dec;
-    norm_radec(lo, la, &ra, &dec);
-    const ZoneInfo Z = zones[z];
-    CellOff o = cell_offsets(ra, dec, Z, bin_of(ra_key, Z.nbins));
-    BRec r;
-    r.xi = o.xi;
-    r.eta = o.eta;
-    r.ra_key = ra_key;
-    r.row = (int32_t)row;
-    rec[i] = r;
-    pos[i] = make_double2(ra, dec);
-    if (px) unit64(ra, dec, &px[i], &py[i], &pz[i]);
-    if (id_out) id_out[i] = id[row];
+    rec[i] = rec_in[vals[i]];
+    const uint64_t key = keys[i];
+    const ZoneInfo& Z = zones[key >> 32];
+    const int64_t start = Z.start, rows = Z.end - Z.start, rel = i - start;
+    const uint32_t shift = Z.lut_shift;
+    const uint32_t b = bucket_of(key, shift);
+    const int64_t prev = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], shift);
+    uint32_t* L = lut + Z.lut_base;
+    for (int64_t k = prev + 1; k <= b; k++) L[k] = (uint32_t)rel;
+    if (rel == rows - 1) {
+        const int64_t nb = (int64_t)1 << (32 - shift);
+        for (int64_t k = (int64_t)b + 1; k <= nb; k++) L[k] = (uint32_t)rows;
+    }
 }
 
 int bits_for(int64_t v) {
@@ -151,19 +186,21 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     X->device = dev;
     X->frame = B->frame;
     X->n = n;
-    X->h_arcsec = h_as;
-    X->h = h_as * kArcsec;
-    X->nz = (int32_t)ceil(648000.0 / h_as - 1e-9);
+    X->nz = (int32_t)ceil(648000.0 / h_as - 1e-9);  // equal zones of height <= requested
+    X->h_arcsec = 648000.0 / X->nz;
+    X->h = kPi / X->nz;
     const bool fp64 = opts && opts->build_fp64;
     const int64_t nn = n > 0 ? n : 1;
 
     xm_status st = XM_OK;
     // temporaries
     double *d_lon = nullptr, *d_lat = nullptr;
-    int64_t* d_id = nullptr;
     uint64_t *keys = nullptr, *tk = nullptr;
     uint32_t *vals = nullptr, *tv = nullptr;
+    BRec* rec_in = nullptr;
     int32_t* err = nullptr;
+    int32_t* lut_cnt = nullptr;
+    int64_t* lut_off = nullptr;
     int32_t h_err = 0;
 
     auto fail = [&](xm_status code) { st = code; };
@@ -186,10 +223,14 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             X->id = (int64_t*)dev_alloc(nn * sizeof(int64_t), s);
             if (!X->id) { fail(set_error(XM_ENOMEM, "index ids")); break; }
             X->bytes += nn * sizeof(int64_t);
+            if (n > 0) {
+                e = cudaMemcpyAsync(X->id, B->id, n * sizeof(int64_t),
+                                    B->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) { fail(cuda_fail(e, "id copy")); break; }
+            }
         }
         const double* lon = B->lon_deg;
         const double* lat = B->lat_deg;
-        const int64_t* idp = B->id;
         if (!B->on_device && n > 0) {
             d_lon = (double*)dev_alloc(2 * n * sizeof(double), s);
             if (!d_lon) { fail(set_error(XM_ENOMEM, "input copy")); break; }
@@ -197,41 +238,52 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             e = cudaMemcpyAsync(d_lon, B->lon_deg, n * sizeof(double), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_lat, B->lat_deg, n * sizeof(double), cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess && B->id) {
-                d_id = (int64_t*)dev_alloc(n * sizeof(int64_t), s);
-                if (!d_id) { fail(set_error(XM_ENOMEM, "input copy")); break; }
-                e = cudaMemcpyAsync(d_id, B->id, n * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-            }
             if (e != cudaSuccess) { fail(cuda_fail(e, "input copy")); break; }
             lon = d_lon;
             lat = d_lat;
-            idp = d_id;
         }
         keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
         vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
+        rec_in = (BRec*)dev_alloc(nn * sizeof(BRec), s);
         err = (int32_t*)dev_alloc(sizeof(int32_t), s);
-        if (!keys || !vals || !err) { fail(set_error(XM_ENOMEM, "sort buffers")); break; }
+        lut_cnt = (int32_t*)dev_alloc(X->nz * sizeof(int32_t), s);
+        lut_off = (int64_t*)dev_alloc(X->nz * sizeof(int64_t), s);
+        // bucket tables: a zone of m rows has at most max(1, m/2) + 1 entries
+        X->lut_n = n / 2 + 2 * (int64_t)X->nz + 16;
+        X->lut = (uint32_t*)dev_alloc(X->lut_n * sizeof(uint32_t), s);
+        if (!keys || !vals || !rec_in || !err || !lut_cnt || !lut_off || !X->lut) {
+            fail(set_error(XM_ENOMEM, "index build buffers"));
+            break;
+        }
+        X->bytes += X->lut_n * sizeof(uint32_t);
         tk = keys + nn;
         tv = vals + nn;
         e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) { fail(cuda_fail(e, "memset")); break; }
 
         auto body = [&]() -> xm_status {
-            unsigned gz = (unsigned)((X->nz + kBlock) / kBlock);
-            XM_LAUNCH("k_zone_table", gz, kBlock, 0, s, k_zone_table, X->nz, X->h, X->zones);
+            const IndexGeom G = X->geom();
+            const unsigned gz = (unsigned)((X->nz + kBlock) / kBlock);
+            XM_LAUNCH("k_zone_geom", gz, kBlock, 0, s, k_zone_geom, X->nz, X->zones);
             if (n > 0) {
-                unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->h, X->nz, keys,
-                          vals, err);
-                xm_status r = radix_sort_u64(keys, vals, tk, tv, n, 32 + bits_for(X->nz - 1), s);
+                const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
+                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, G.zscale, X->nz,
+                          G.h_f, X->zones, keys, vals, rec_in, X->pos, X->px, X->py, X->pz, err);
+                xm_status r = radix_sort_u64(keys, vals, tk, tv, n, kSortBeginBit,
+                                             32 + bits_for(X->nz - 1), err, s);
                 if (r != XM_OK) return r;
             }
             XM_LAUNCH("k_zone_start", gz, kBlock, 0, s, k_zone_start, keys, n, X->nz,
                       X->zone_start);
+            XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, X->zones,
+                      lut_cnt);
+            xm_status r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, s);
+            if (r != XM_OK) return r;
+            XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->lut);
             if (n > 0) {
-                unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, lon, lat, idp, keys, vals, n,
-                          X->zones, X->rec, X->pos, X->px, X->py, X->pz, X->id);
+                const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
+                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, keys, vals, n, rec_in,
+                          X->zones, X->lut, X->rec);
             }
             return XM_OK;
         };
@@ -241,13 +293,16 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { fail(cuda_fail(e, "xm_build_index sync")); break; }
         if (h_err & kErrCoord) { fail(set_error(XM_EINVAL, "B: NaN/inf or |lat| > 90")); break; }
+        if (h_err & kErrTimeout) { fail(set_error(XM_ETIMEOUT, "index sort: look-back timed out")); break; }
     } while (0);
 
     dev_free(d_lon, s);
-    dev_free(d_id, s);
+    dev_free(rec_in, s);
     dev_free(keys, s);
     dev_free(vals, s);
     dev_free(err, s);
+    dev_free(lut_cnt, s);
+    dev_free(lut_off, s);
     if (st != XM_OK) {
         xm_index_free(X);
         return st;
@@ -265,6 +320,7 @@ extern "C" xm_status xm_index_free(xm_index* X) {
     dev_free(X->id, s);
     dev_free(X->zone_start, s);
     dev_free(X->zones, s);
+    dev_free(X->lut, s);
     delete X;
     return XM_OK;
 }

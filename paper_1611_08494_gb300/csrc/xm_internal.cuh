@@ -10,21 +10,25 @@
 //   ellipse:   (X/a)^2 + (Y/b)^2 <= 1,  X = k (x sin t + y cos t),
 //   rectangle: max(|X|/a, |Y|/b) <= 1,  Y = k (x cos t - y sin t), k = rho/s.
 //
-// Sky partition (paper §2.3). Index frame latitudes are cut into zones of
-// height h; zone z spans [-90 deg + z h, -90 deg + (z+1) h). Each zone is cut
-// into `nbins` RA cells of equal width, nbins chosen so a cell is at most h
-// wide on the zone's equator-side edge. B sources are sorted by
-// (zone, ra_key) with ra_key = floor(RA / 2pi * 2^32). The cell of a source is
-// bin = (ra_key * nbins) >> 32; its centre is ((bin + 1/2) 2pi/nbins, zone
-// centre).
+// Sky partition (paper §2.3). Index-frame latitudes are cut into nz zones of
+// equal height h = 180 deg / nz. A position's zone coordinate is
+// t = (lat_deg + 90) * nz / 180: zone z = floor(t), and its offset from the
+// zone centre line is t - z - 1/2 zones. Longitudes become 64-bit fixed-point
+// keys key64 = floor(lon_deg / 360 * 2^64); the sort key of the index uses
+// ra_key = key64 >> 32. Each zone is cut into `nbins` RA cells of equal width,
+// nbins chosen so a cell is at most h wide on the zone's equator-side edge;
+// the cell of a source is bin = (ra_key * nbins) >> 32 and its centre is at
+// RA (bin + 1/2) 2pi/nbins on the zone's centre line.
 //
 // Precision pattern. Each B source stores float32 orthographic offsets
 // (xi, eta) = (p_B.e_c, p_B.n_c) in the tangent frame of its cell centre c.
-// They are computed from float64 differences (RA - RA_c, Dec - Dec_c) followed
-// by float32 trigonometry of those small angles, so they carry absolute
-// errors of a few float32 ulps of the cell size. An A source re-expresses
-// itself in the same cell frame once per (A, cell) and tests candidates with
-// ~20 float32 operations; results within a guard band of the boundary are
+// The angles from the cell centre are formed exactly in fixed point (integer
+// products of key64 and nbins, and the zone coordinate) and only then rounded
+// to float32, so the offsets carry absolute errors of a few float32 ulps of
+// the cell size and the float32 path needs no float64 operation per source or
+// per candidate (GB300's float64 pipe runs at 1/64 of its float32 rate). An A
+// source re-expresses itself in the same cell frame and tests candidates with
+// ~60 float32 operations; results within a guard band of the boundary are
 // re-tested in float64.
 #pragma once
 
@@ -41,8 +45,10 @@ constexpr double kHalfPi = 1.570796326794896619231321691639751442;
 constexpr double kDeg = kPi / 180.0;
 constexpr double kArcsec = kPi / 648000.0;
 constexpr double kRadToArcsec = 648000.0 / kPi;
-constexpr double kKeyScale = 4294967296.0 / kTwoPi;  // ra_key per radian
-constexpr float kEps32 = 5.9604645e-08f;              // 2^-24
+constexpr double kKey64PerDeg = 18446744073709551616.0 / 360.0;  // 2^64 / 360
+constexpr double kKey64PerRad = 18446744073709551616.0 / kTwoPi;
+constexpr float kKey32PerRadF = 683565275.57643158f;            // 2^32 / 2pi
+constexpr float kEps32 = 5.9604645e-08f;                         // 2^-24
 
 // error bits set by kernels (device status word)
 enum : int32_t {
@@ -52,132 +58,139 @@ enum : int32_t {
     kErrOverflow = 8,   // a fixed-capacity buffer would overflow
 };
 
-// Slots of the member list kept inline per A source during the count pass.
-constexpr int kInlineSlots = 8;
-
-struct ZoneInfo {
+// One declination zone. Its B sources are rows [start, end) of the index,
+// sorted by ra_key. The RA bucket table lut[lut_base + k], k = ra_key >>
+// lut_shift, holds the first row (relative to start) whose key reaches bucket
+// k, so a window bound is found with two table reads and a short search.
+struct __align__(16) ZoneInfo {
     double dec_c;          // zone centre latitude (rad)
     double sin_c, cos_c;   // of dec_c, float64
     double binw;           // RA cell width (rad)
+    int64_t start, end;    // index rows of the zone
+    int64_t lut_base;      // first bucket entry of the zone
     float sin_cf, cos_cf;  // of dec_c, float32
-    uint32_t nbins;
+    float binw_f;          // RA cell width (rad), float32
+    uint32_t nbins;        // RA cells
+    uint32_t lut_shift;    // 32 - log2(buckets)
     uint32_t pad;
 };
 
 // One B source in index order (16 bytes: one vector load per candidate).
 struct __align__(16) BRec {
     float xi, eta;    // offsets in the tangent frame of the source's cell
-    uint32_t ra_key;  // floor(RA / 2pi * 2^32)
+    uint32_t ra_key;  // key64 >> 32
     int32_t row;      // row in the caller's B catalogue
 };
 
 // One A source, prepared in (zone, RA) order.
-struct APrep {
-    double alpha, delta;  // index-frame RA / Dec (rad)
+struct __align__(16) APrep {
+    double alpha, delta;  // index-frame RA / Dec (rad), for float64 tests
     double theta;         // position angle in the index frame (rad)
     double a, b;          // region sizes (rad); circle: a = b = radius
+    uint64_t key64;       // fixed-point RA
+    int32_t z;            // zone
+    float zfrac;          // t - z - 1/2 (zones)
     float R;              // bounding radius (rad); 0 = empty region
     int32_t row;          // row in the caller's A catalogue
     float m00, m01, m10, m11;  // float32 map (x, y) -> (X/a, Y/b)
 };
 
-// A member kept inline during the count pass: B row and the separation
-// (arcsec) that will be reported for the pair.
-struct Slot {
-    int32_t b_row;
-    int32_t pad;
-    double sep;
-};
-
 // Geometry of a built index, passed by value to kernels.
 struct IndexGeom {
     const BRec* rec;
-    const double2* pos;  // (RA, Dec) rad, float64, index order
-    const double* px;    // float64 unit vectors, index order (nullable)
+    const double2* pos;  // (lon, lat) in degrees, index frame, by B row
+    const double* px;    // float64 unit vectors by B row (nullable)
     const double* py;
     const double* pz;
-    const int64_t* zone_start;  // [nz + 1]
-    const ZoneInfo* zones;      // [nz]
+    const ZoneInfo* zones;  // [nz]
+    const uint32_t* lut;    // RA bucket tables of all zones
     int32_t nz;
-    double h;  // zone height (rad)
+    double h;        // zone height (rad)
+    double zscale;   // zones per degree of latitude (nz / 180)
+    float h_f;       // zone height (rad), float32
 };
 
-__host__ __device__ inline int32_t zone_of(double dec, double h, int32_t nz) {
-    double t = floor((dec + kHalfPi) / h);
-    int32_t z = t < 0 ? 0 : (t >= nz ? nz - 1 : (int32_t)t);
-    return z;
+// ------------------------------------------------------ fixed-point position
+
+// Longitude (deg) reduced to [0, 360); the in-range case costs two compares.
+__host__ __device__ inline double lon_mod360(double lon) {
+    if (lon >= 0.0 && lon < 360.0) return lon;
+    double l = lon - 360.0 * floor(lon * (1.0 / 360.0));
+    if (l >= 360.0) l -= 360.0;
+    if (l < 0.0) l += 360.0;
+    return l;
 }
 
-__host__ __device__ inline uint32_t ra_key_of(double ra) {
-    double k = floor(ra * kKeyScale);
-    if (k < 0) k = 0;
-    if (k > 4294967295.0) k = 4294967295.0;
-    return (uint32_t)k;
+// Finite longitude and |lat| <= 90 (NaN fails), decided on the bit patterns.
+__device__ __forceinline__ bool coord_ok(double lon, double lat) {
+    const uint64_t bl = (uint64_t)__double_as_longlong(lon) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t bb = (uint64_t)__double_as_longlong(lat) & 0x7FFFFFFFFFFFFFFFull;
+    return bl < 0x7FF0000000000000ull && bb <= 0x4056800000000000ull;  // bits of 90.0
+}
+
+struct PosKey {
+    uint64_t key64;  // floor(lon / 360 * 2^64)
+    int32_t z;       // zone
+    float zfrac;     // zone coordinate minus zone centre line, in zones
+};
+
+// The single place positions (degrees, lon already in [0, 360)) become zone
+// and key: every caller uses it, so zone spans and key windows computed from
+// it cover the sources filed under them.
+__device__ __forceinline__ PosKey pos_key(double lon, double lat, double zscale, int32_t nz) {
+    PosKey k;
+    const double t = (lat + 90.0) * zscale;
+    int32_t z = __double2int_rd(t);
+    z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
+    k.z = z;
+    k.zfrac = (float)(t - (double)z) - 0.5f;
+    k.key64 = __double2ull_rd(lon * kKey64PerDeg);
+    return k;
 }
 
 __device__ __forceinline__ uint32_t bin_of(uint32_t ra_key, uint32_t nbins) {
     return (uint32_t)(((uint64_t)ra_key * (uint64_t)nbins) >> 32);
 }
 
-// Offsets of a position in the tangent frame of a cell:
-//   xi   = cos(dec) sin(dRA)
-//   eta  = sin(dDec) + cos(dec) sin(dec_c) (1 - cos dRA)
-//   zeta = p.p_c - 1 = -[(1 - cos dDec) + cos(dec) cos(dec_c) (1 - cos dRA)]
-// with dRA = RA - RA_c, dDec = Dec - Dec_c taken in float64 and everything
-// after in float32; cos(dec) by angle addition from the zone centre.
-struct CellOff {
-    float xi, eta, zeta;
-    float sd, cd;   // sin / cos of dec (float32)
-    float sa, hav_a, sdd, hav_d;
-};
-
-__device__ __forceinline__ CellOff cell_offsets(double ra, double dec, const ZoneInfo& Z,
-                                                uint32_t bin) {
-    double ra_c = ((double)bin + 0.5) * Z.binw;
-    double dra = ra - ra_c;
-    if (dra > kPi) dra -= kTwoPi;
-    else if (dra <= -kPi) dra += kTwoPi;
-    double ddec = dec - Z.dec_c;
-    float fa = (float)dra, fd = (float)ddec;
-    CellOff o;
-    float ca;
-    sincosf(fa, &o.sa, &ca);
-    float sh = sinf(0.5f * fa);
-    o.hav_a = 2.0f * sh * sh;  // 1 - cos dRA without cancellation
-    float cdd;
-    sincosf(fd, &o.sdd, &cdd);
-    float shd = sinf(0.5f * fd);
-    o.hav_d = 2.0f * shd * shd;
-    o.cd = Z.cos_cf * cdd - Z.sin_cf * o.sdd;
-    o.sd = Z.sin_cf * cdd + Z.cos_cf * o.sdd;
-    o.xi = o.cd * o.sa;
-    o.eta = o.sdd + o.cd * Z.sin_cf * o.hav_a;
-    o.zeta = -(o.hav_d + o.cd * Z.cos_cf * o.hav_a);
-    return o;
+// RA of a fixed-point key relative to the centre of cell `bin` of a zone with
+// nbins cells, in cells: key64 * nbins / 2^64 - bin - 1/2, from the exact
+// 128-bit product.
+__device__ __forceinline__ float cells_from_centre(uint64_t key64, uint32_t nbins, uint32_t bin) {
+    const uint64_t hi = __umul64hi(key64, (uint64_t)nbins);
+    const uint64_t lo = key64 * (uint64_t)nbins;
+    const float frac = (float)(lo >> 40) * 5.9604644775390625e-08f;  // 2^-24
+    return (float)(int32_t)((uint32_t)hi - bin) + (frac - 0.5f);
 }
 
-// Per (A, cell) float32 transform taking B's cell offsets to (x, y) in A's
-// east/north frame: (x, y) = J (dxi, deta) + dzeta t, d* = B - A offsets.
-struct CellXf {
-    float xa, ya, za;
-    float j00, j01, j10, j11, t0, t1;
+// sin(x) and 1 - cos(x) = 2 sin^2(x/2) in float32. Below |x| = 1/16 they are
+// the Taylor series (truncation error < 3e-15 relative); above, the float32
+// library functions.
+__device__ __forceinline__ void sin_hav(float x, float* s, float* hav) {
+    float x2 = x * x;
+    if (fabsf(x) < 0.0625f) {
+        *s = fmaf(x * x2, fmaf(x2, fmaf(x2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), x);
+        *hav = x2 * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 40320.0f, 1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
+    } else {
+        *s = sinf(x);
+        float h = sinf(0.5f * x);
+        *hav = 2.0f * h * h;
+    }
+}
+
+// Latitude terms of a position relative to a zone centre, from the latitude
+// offset ddec (rad): sin/hav of ddec and cos/sin of the latitude by angle
+// addition.
+struct LatTerms {
+    float sdd, hav_d, cd, sd;
 };
 
-__device__ __forceinline__ CellXf cell_xf(double ra, double dec, const ZoneInfo& Z,
-                                          uint32_t bin) {
-    CellOff o = cell_offsets(ra, dec, Z, bin);
-    CellXf x;
-    x.xa = o.xi;
-    x.ya = o.eta;
-    x.za = o.zeta;
-    // basis products (c = cell centre, A = the source)
-    x.j00 = 1.0f - o.hav_a;            // e_c . e_A = cos dRA
-    x.j01 = Z.sin_cf * o.sa;           // n_c . e_A
-    x.t0 = -Z.cos_cf * o.sa;           // p_c . e_A
-    x.j10 = -o.sd * o.sa;              // e_c . n_A
-    x.j11 = (1.0f - o.hav_d) - o.sd * Z.sin_cf * o.hav_a;  // n_c . n_A
-    x.t1 = -o.sdd + o.sd * Z.cos_cf * o.hav_a;              // p_c . n_A
-    return x;
+__device__ __forceinline__ LatTerms lat_terms(float ddec, float sin_c, float cos_c) {
+    LatTerms t;
+    sin_hav(ddec, &t.sdd, &t.hav_d);
+    const float cdd = 1.0f - t.hav_d;
+    t.cd = cos_c * cdd - sin_c * t.sdd;
+    t.sd = sin_c * cdd + cos_c * t.sdd;
+    return t;
 }
 
 // zeta of a stored offset pair: p.p_c - 1 = -r2 / (1 + sqrt(1 - r2)).
@@ -239,19 +252,18 @@ __device__ __forceinline__ bool test64(const A64& A, int shape, double px, doubl
     return k * fmax(fabs(X) / A.a, fabs(Y) / A.b) <= 1.0;
 }
 
-__device__ __forceinline__ void unit64(double ra, double dec, double* px, double* py,
-                                       double* pz) {
+// Float64 unit vector of a position given in degrees.
+__device__ __forceinline__ void unit64_deg(double lon, double lat, double* px, double* py,
+                                           double* pz) {
     double sa, ca, sd, cd;
-    sincos(ra, &sa, &ca);
-    sincos(dec, &sd, &cd);
+    sincos(lon * kDeg, &sa, &ca);
+    sincos(lat * kDeg, &sd, &cd);
     *px = cd * ca;
     *py = cd * sa;
     *pz = sd;
 }
 
 // ---------------------------------------------------------------- host side
-
-struct Ctx;  // per-call allocator / stream / launch bookkeeping (xm_api.cu)
 
 void* dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
@@ -273,12 +285,19 @@ xm_status cuda_fail(cudaError_t e, const char* what);
 xm_status set_error(xm_status s, const char* fmt, ...);
 
 // Device primitives (xm_sort.cu).
-// Stable LSD radix sort of (keys, vals) on key bits [0, end_bit). Sorted data
-// ends in (keys, vals); (tk, tv) are scratch of the same sizes.
+// Stable LSD radix sort of (keys, vals) on key bits [begin_bit, end_bit).
+// Sorted data ends in (keys, vals); (tk, tv) are scratch of the same sizes.
+// A look-back that timed out sets kErrTimeout in *err (device), which the
+// caller reads at its next synchronisation.
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                         int end_bit, cudaStream_t s);
-// out[i] = sum of in[0..i) (int64); *total (device) = sum of all. Works in
-// place (out == in is not allowed).
+                         int begin_bit, int end_bit, int32_t* err, cudaStream_t s);
+
+// Sort keys file sources by zone, then by RA to 2^-24 of a turn (0.08
+// arcsec): the low 8 bits of the RA key are dropped, so the sort starts at
+// bit 8. Search windows are widened by one such quantum.
+constexpr uint32_t kRaKeyMask = 0xFFFFFF00u;
+constexpr int kSortBeginBit = 8;
+// out[i] = sum of in[0..i) (int64); *total (device) = sum of all.
 xm_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
                              cudaStream_t s);
 xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
@@ -286,6 +305,10 @@ xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t
 
 // Host-side galactic -> equatorial rotation (row major, v_eq = m v_gal).
 void gal_to_eq(double m[9]);
+
+void stats_add(const unsigned long long* host_counters);  // [0..4] as in xm_stats
+// Per-device cumulative counters ([0..4] as in xm_stats) kernels add to.
+unsigned long long* device_stats();
 
 }  // namespace xm
 
@@ -295,8 +318,8 @@ struct xm_index {
     int device;
     int32_t frame;
     int64_t n;
-    double h_arcsec;
-    double h;  // rad
+    double h_arcsec;  // zone height actually used (180 deg / nz)
+    double h;         // rad
     int32_t nz;
     xm::BRec* rec;
     double2* pos;
@@ -304,9 +327,11 @@ struct xm_index {
     int64_t* id;
     int64_t* zone_start;
     xm::ZoneInfo* zones;
+    uint32_t* lut;
+    int64_t lut_n;
     int64_t bytes;
     xm::IndexGeom geom() const {
-        return xm::IndexGeom{rec, pos, px, py, pz, zone_start, zones, nz, h};
+        return xm::IndexGeom{rec, pos, px, py, pz, zones, lut, nz, h, nz / 180.0, (float)h};
     }
 };
 
@@ -327,7 +352,3 @@ struct xm_rows {
     int64_t *a_row, *b_row;
     double* sep;
 };
-
-namespace xm {
-void stats_add(const unsigned long long* host_counters);  // [0..4] as in xm_stats
-}

@@ -1,0 +1,850 @@
+// xm_scan.cuh -- device side of the Sky cross-match (paper §2.1) with the
+// selections of §2.2, shared by the single-request and batched entry points.
+//
+//   k_ingest_a   validity, rotation into the index frame when the frames
+//                differ, (zone, RA key) sort key per A source
+//   k_prep_a     per A in (zone, RA) order: index-frame position (float64 and
+//                fixed point), position angle (plus the frame rotation's
+//                angle), sizes, bounding radius, float32 region map
+//   k_scan       the candidate scan (below), in three modes: count (members,
+//                best pair, member records), emit (re-scan straight into the
+//                pair list), resolve (best pair decided in float64)
+//   k_place, k_sort_small, k_seg_sort   member records into the canonical
+//                pair list (ascending A row, then B row)
+#pragma once
+
+#include <math.h>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+namespace {
+
+constexpr int kSegMax = 2048;  // largest member list sorted in shared memory
+constexpr int kSmallSort = 16;  // largest member list sorted by one thread
+
+enum { kPrecFP64 = 0, kPrecFP32 = 1 };
+enum { kModeCount = 0, kModeEmit = 1, kModeResolve = 2 };
+
+struct AIn {
+    const double* lon;
+    const double* lat;
+    int64_t n;
+    int32_t rotate;  // 1: rotate by rot (input frame -> index frame)
+    double rot[9];
+    int32_t shape, pa_dir;
+    double a, b, pa;
+    const double* a_col;
+    const double* b_col;
+    const double* pa_col;
+    double size_k;   // radians per size unit (scale * unit * arcsec)
+    double pa_zero;  // degrees
+    double zscale;   // zones per degree of latitude
+    int32_t nz;
+};
+
+// Index-frame position of A source i, in degrees (lon in [0, 360)), and the
+// angle gamma from the index frame's north to the input frame's north (east
+// positive) at that point.
+__device__ void a_position(const AIn& I, int64_t i, double* lon_o, double* lat_o, double* gamma,
+                           bool* ok) {
+    double lon = I.lon[i], lat = I.lat[i];
+    *ok = coord_ok(lon, lat);
+    if (!*ok) { lon = 0.0; lat = 0.0; }
+    lon = lon_mod360(lon);
+    if (!I.rotate) {
+        *lon_o = lon;
+        *lat_o = lat;
+        *gamma = 0.0;
+        return;
+    }
+    double sl, cl, sb, cb;
+    sincos(lon * kDeg, &sl, &cl);
+    sincos(lat * kDeg, &sb, &cb);
+    const double p[3] = {cb * cl, cb * sl, sb};
+    const double nn[3] = {-sb * cl, -sb * sl, cb};
+    double q[3], m[3];
+    for (int k = 0; k < 3; k++) {
+        q[k] = I.rot[3 * k] * p[0] + I.rot[3 * k + 1] * p[1] + I.rot[3 * k + 2] * p[2];
+        m[k] = I.rot[3 * k] * nn[0] + I.rot[3 * k + 1] * nn[1] + I.rot[3 * k + 2] * nn[2];
+    }
+    const double rxy = hypot(q[0], q[1]);
+    double r = atan2(q[1], q[0]) / kDeg;
+    if (r < 0) r += 360.0;
+    if (r >= 360.0) r -= 360.0;
+    *lon_o = r;
+    *lat_o = atan2(q[2], rxy) / kDeg;
+    const double ca = rxy > 0 ? q[0] / rxy : 1.0, sa = rxy > 0 ? q[1] / rxy : 0.0;
+    const double sd = q[2], cd = rxy;
+    // index-frame east / north at the rotated point
+    const double me = -m[0] * sa + m[1] * ca;
+    const double mn = -m[0] * sd * ca - m[1] * sd * sa + m[2] * cd;
+    *gamma = atan2(me, mn);
+}
+
+__device__ __forceinline__ bool size_ok(double a, double b, double pa) {
+    return isfinite(a) && isfinite(b) && isfinite(pa) && a >= 0.0 && b >= 0.0;
+}
+
+__global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           int32_t* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I.n) return;
+    double lon, lat, gamma;
+    bool ok;
+    a_position(I, i, &lon, &lat, &gamma, &ok);
+    if (!ok) atomicOr(err, kErrCoord);
+    const double a = I.a_col ? I.a_col[i] : I.a;
+    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
+    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
+    const PosKey k = pos_key(lon, lat, I.zscale, I.nz);
+    keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= I.n) return;
+    const int64_t i = vals[s];
+    double lon, lat, gamma;
+    bool ok;
+    a_position(I, i, &lon, &lat, &gamma, &ok);
+    double a = I.a_col ? I.a_col[i] : I.a;
+    double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
+    double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    if (!size_ok(a, b, pa)) a = b = pa = 0.0;
+    APrep P;
+    P.alpha = lon * kDeg;
+    P.delta = lat * kDeg;
+    const PosKey k = pos_key(lon, lat, I.zscale, I.nz);
+    P.key64 = k.key64;
+    P.z = k.z;
+    P.zfrac = k.zfrac;
+    P.row = (int32_t)i;
+    P.a = a * I.size_k;
+    P.b = b * I.size_k;
+    double th = (I.pa_zero + I.pa_dir * pa) * kDeg + gamma;
+    th = remainder(th, kTwoPi);
+    P.theta = th;
+    if (P.a <= 0.0 || P.b <= 0.0 || !ok) {
+        P.R = 0.0f;
+        P.m00 = P.m01 = P.m10 = P.m11 = 0.0f;
+    } else {
+        const double R = I.shape == XM_RECT ? hypot(P.a, P.b) : fmax(P.a, P.b);
+        P.R = (float)(R * (1.0 + 1e-6));
+        float st, ct;
+        sincosf((float)th, &st, &ct);
+        const float ia = (float)(1.0 / P.a), ib = (float)(1.0 / P.b);
+        P.m00 = st * ia;
+        P.m01 = ct * ia;
+        P.m10 = ct * ib;
+        P.m11 = -st * ib;
+    }
+    out[s] = P;
+}
+
+// One member found by the count pass: A row, its index among that row's
+// members (scan order), B row, and the separation to report: float64 arcsec,
+// or (flag 1) the float32 separation in radians, converted when placed.
+struct MemberRec {
+    int32_t a_row, k, b_row, f32;
+    double sep;
+};
+
+struct ScanArgs {
+    IndexGeom G;
+    const APrep* A;
+    int64_t nA;
+    int32_t shape;
+    int32_t want_best;
+    const int32_t* list;  // sorted A indices to process (overflow / ties)
+    int64_t nlist;
+    // count mode: per A row
+    int32_t* count;
+    int64_t* best_b;
+    double* best_sep;
+    MemberRec* arena;             // member records (all-pairs selection), or NULL
+    unsigned long long* arena_n;  // records claimed
+    long long arena_cap;
+    int32_t* ovf_list;  // sources with members that did not fit the arena
+    int32_t* tie_list;  // sources whose best pair is decided in float64
+    int32_t* big_list;  // rows with more than kSegMax members
+    int32_t* list_n;    // [0] overflow, [1] ties, [2] big
+    // emit mode
+    const int64_t* pair_off;
+    int64_t* out_a;
+    int64_t* out_b;
+    double* out_sep;
+    int32_t* err;               // status bits
+    unsigned long long* stats;  // candidates, rechecked, flipped, members, tie_resolved
+};
+
+// Bounds of one A source's search: zones [z0, z1] and up to two ra_key
+// segments (the RA window, split at 0/360). Float32 and integer arithmetic on
+// the fixed-point position, widened so it contains every source within the
+// bounding radius.
+struct Window {
+    int32_t z0, z1, nseg;
+    uint32_t lo[2], hi[2];
+};
+
+__device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
+    Window W;
+    const float Rm = A.R * (1.0f + 1e-5f) + 1e-9f;
+    const float dz = Rm / G.h_f * (1.0f + 1e-5f) + 1e-3f;  // zones, with margin
+    const float t = A.zfrac + 0.5f;                       // position inside zone A.z
+    const int32_t z0 = A.z + (int32_t)floorf(t - dz);
+    const int32_t z1 = A.z + (int32_t)floorf(t + dz);
+    bool full = z0 < 0 || z1 >= G.nz;  // the window reaches a pole
+    W.z0 = max(z0, 0);
+    W.z1 = min(z1, G.nz - 1);
+    int64_t dk = 0;
+    if (!full) {
+        // half-width of the RA window: asin(sin R / cos dec), widened
+        const ZoneInfo& Z = G.zones[A.z];
+        const LatTerms L = lat_terms(G.h_f * A.zfrac, Z.sin_cf, Z.cos_cf);
+        const float ratio = sinf(Rm) / L.cd;
+        if (!(L.cd > 0.0f && ratio < 0.9999f)) full = true;
+        else dk = (int64_t)ceilf(asinf(ratio) * (1.0f + 2e-5f) * kKey32PerRadF) + 2;
+    }
+    // stored B keys are rounded down to a multiple of 256: widen the low end
+    const int64_t ka = (int64_t)(A.key64 >> 32);
+    const int64_t lo = ka - dk - 256, hi = ka + dk;
+    if (full || hi - lo >= 4294967295LL) {
+        W.nseg = 1;
+        W.lo[0] = 0;
+        W.hi[0] = 0xFFFFFFFFu;
+    } else if (lo < 0) {
+        W.nseg = 2;
+        W.lo[0] = 0;
+        W.hi[0] = (uint32_t)hi;
+        W.lo[1] = (uint32_t)(lo + 4294967296LL);
+        W.hi[1] = 0xFFFFFFFFu;
+    } else if (hi > 4294967295LL) {
+        W.nseg = 2;
+        W.lo[0] = 0;
+        W.hi[0] = (uint32_t)(hi - 4294967296LL);
+        W.lo[1] = (uint32_t)lo;
+        W.hi[1] = 0xFFFFFFFFu;
+    } else {
+        W.nseg = 1;
+        W.lo[0] = (uint32_t)lo;
+        W.hi[0] = (uint32_t)hi;
+    }
+    return W;
+}
+
+// First row in [start, end) of a zone whose ra_key >= key, or > key when
+// `upper`; the zone's RA bucket table narrows the range to one bucket.
+__device__ __forceinline__ int64_t zone_bound(const IndexGeom& G, const ZoneInfo& Z, uint32_t key,
+                                              bool upper) {
+    const uint32_t k = (uint32_t)((uint64_t)key >> Z.lut_shift);
+    int64_t lo = Z.start + __ldg(&G.lut[Z.lut_base + k]);
+    int64_t hi = Z.start + __ldg(&G.lut[Z.lut_base + k + 1]);
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        const uint32_t v = __ldg(&G.rec[mid].ra_key);
+        if (upper ? v <= key : v < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Float64 unit vector of B row `row` (exact positions are kept by row).
+__device__ __forceinline__ void load_p64(const IndexGeom& G, int32_t row, double* x, double* y,
+                                         double* z) {
+    if (G.px) {
+        *x = G.px[row];
+        *y = G.py[row];
+        *z = G.pz[row];
+    } else {
+        const double2 p = G.pos[row];
+        unit64_deg(p.x, p.y, x, y, z);
+    }
+}
+
+__device__ __forceinline__ void warp_add(unsigned long long* dst, uint32_t v) {
+    const uint32_t s = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
+}
+
+// Terms of one (A source, zone) item shared by all its candidates: A's
+// latitude relative to the zone centre and A's RA key multiplied by the
+// zone's cell count.
+struct ItemTerms {
+    float sdd, hav_d, cd, sd;  // LatTerms of A in this zone
+    float sinc, cosc;          // zone centre
+    float binw, ufrac;         // cell width; fractional cell of A, minus 1/2
+    uint32_t binA, nbins;      // integer cell of A (exact product), cells
+};
+
+__device__ __forceinline__ ItemTerms item_terms(const APrep& A, const ZoneInfo& Z, int32_t z,
+                                                float h_f) {
+    ItemTerms t;
+    const LatTerms L = lat_terms(h_f * ((float)(A.z - z) + A.zfrac), Z.sin_cf, Z.cos_cf);
+    t.sdd = L.sdd;
+    t.hav_d = L.hav_d;
+    t.cd = L.cd;
+    t.sd = L.sd;
+    t.sinc = Z.sin_cf;
+    t.cosc = Z.cos_cf;
+    t.binw = Z.binw_f;
+    t.nbins = Z.nbins;
+    t.binA = (uint32_t)__umul64hi(A.key64, (uint64_t)Z.nbins);
+    t.ufrac = (float)((A.key64 * (uint64_t)Z.nbins) >> 40) * 5.9604644775390625e-08f - 0.5f;
+    return t;
+}
+
+// Float32 region test of candidate b against A (no float64 operation).
+// Returns q (quadratic form; max form for rectangles) and the east/north
+// components (x, y) of b in A's frame.
+__device__ __forceinline__ float q32(const APrep& A, int shape, const ItemTerms& T, const BRec& b,
+                                     float* xo, float* yo) {
+    const uint32_t bin = bin_of(b.ra_key, T.nbins);
+    int32_t d = (int32_t)(T.binA - bin);  // cells from B's cell to A's, wrapped at 0/360
+    if (d > (int32_t)(T.nbins >> 1)) d -= (int32_t)T.nbins;
+    else if (d < -(int32_t)(T.nbins >> 1)) d += (int32_t)T.nbins;
+    const float dra = T.binw * ((float)d + T.ufrac);
+    float sa, hav_a;
+    sin_hav(dra, &sa, &hav_a);
+    // A's offsets in the cell frame
+    const float xa = T.cd * sa;
+    const float ya = fmaf(T.cd * T.sinc, hav_a, T.sdd);
+    const float za = -fmaf(T.cd * T.cosc, hav_a, T.hav_d);
+    // cell frame -> A's east/north frame
+    const float j00 = 1.0f - hav_a, j01 = T.sinc * sa, t0 = -T.cosc * sa;
+    const float j10 = -T.sd * sa, j11 = (1.0f - T.hav_d) - T.sd * T.sinc * hav_a;
+    const float t1 = fmaf(T.sd * T.cosc, hav_a, -T.sdd);
+    const float dxi = b.xi - xa, deta = b.eta - ya;
+    const float dz = zeta_of(b.xi, b.eta) - za;
+    const float x = fmaf(j00, dxi, fmaf(j01, deta, t0 * dz));
+    const float y = fmaf(j10, dxi, fmaf(j11, deta, t1 * dz));
+    *xo = x;
+    *yo = y;
+    const float u0 = fmaf(A.m00, x, A.m01 * y);
+    const float u1 = fmaf(A.m10, x, A.m11 * y);
+    return shape == XM_RECT ? fmaxf(fabsf(u0), fabsf(u1)) : fmaf(u0, u0, u1 * u1);
+}
+
+// ---------------------------------------------------------------- the scan
+//
+// One warp owns a chunk of up to 32 A sources (consecutive in (zone, RA)
+// order, or from a list). Work is flattened twice so all lanes stay busy
+// whatever the region sizes: first the (source, zone, RA segment) items,
+// whose window bounds lanes find in parallel, then the candidates of those
+// items, 32 per round, loaded with consecutive lanes on consecutive rows.
+// Members of a round are folded per source with a segmented warp reduction
+// (lanes of one source are contiguous), so every per-source result is
+// independent of timing; shared memory keeps the running state. In count
+// mode every member is also streamed to a record arena (one atomic per round
+// and warp) from which the pair list is placed without scanning again.
+//
+// Keys of the best-pair fold are the bit patterns of non-negative numbers,
+// compared as integers: float32 separations for sources on the float32 path,
+// float64 separations otherwise (one kind per source).
+
+constexpr int kScanWarps = 4;
+constexpr int kScanThreads = 32 * kScanWarps;
+constexpr int kItemCap = 64;
+constexpr long long kKeyInf = 0x7FF0000000000000LL;  // above every finite key of either kind
+
+struct ScanWarpSmem {
+    APrep A[32];
+    A64 a64[32];               // float64 basis of sources on float64 separations
+    long long m1[32], m2[32];  // best key, second key
+    long long r1[32];          // reported separation of the best (bits)
+    int32_t b1[32];
+    int32_t cnt[32];
+    int32_t cap[32];           // emit mode: count-pass members
+    int32_t drop[32];          // count mode: a member did not fit the arena
+    float g[32], esep[32];
+    int32_t sep64[32];
+    int32_t z0[32], nseg[32];
+    uint32_t wlo[32][2], whi[32][2];
+    int32_t ipref[33];         // first item of each source
+    int32_t it_a[kItemCap];
+    int64_t it_lo[kItemCap];
+    int32_t it_start[kItemCap + 1];  // first candidate of each item
+    ItemTerms it_t[kItemCap];
+};
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
+    extern __shared__ __align__(16) unsigned char scan_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ScanWarpSmem& W = reinterpret_cast<ScanWarpSmem*>(scan_smem)[warp];
+    const IndexGeom& G = P.G;
+    const int shape = P.shape;
+    const int64_t n_units = P.list ? P.nlist : P.nA;
+    const int64_t first = ((int64_t)blockIdx.x * kScanWarps + warp) * 32;
+    if (first >= n_units) return;  // whole warp
+    const int nloc = (int)min((int64_t)32, n_units - first);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    // ---- per-source setup (lane = source)
+    int64_t s_me = -1;
+    int n_items = 0;
+    if (lane < nloc) {
+        s_me = P.list ? P.list[first + lane] : first + lane;
+        const APrep A = P.A[s_me];
+        W.A[lane] = A;
+        const float L_box = 1.42f * A.R + 2.0f * G.h_f;
+        const float L_mem = A.R + 2.0f * G.h_f;
+        const float bmin = (float)fmin(A.a, A.b);
+        // float32 error bounds (see the notes on the precision pattern):
+        // g bounds |q32 - q| (3x margin) plus (rho/s)^2 - 1 <= R^2/3; esep
+        // bounds the float32 separation error (rad).
+        W.g[lane] = 128.0f * kEps32 * L_box / bmin + 0.34f * A.R * A.R + 16.0f * kEps32;
+        W.esep[lane] = 16.0f * kEps32 * L_mem;
+        const bool s64 = PREC == kPrecFP64 || MODE == kModeResolve ||
+                         W.esep[lane] * 206264.8f > 9e-5f;
+        W.sep64[lane] = s64;
+        if (s64 && A.R > 0.0f) W.a64[lane] = make_a64(A);
+        W.m1[lane] = kKeyInf;
+        W.m2[lane] = kKeyInf;
+        W.r1[lane] = 0;
+        W.b1[lane] = 0x7fffffff;
+        W.cnt[lane] = 0;
+        W.drop[lane] = 0;
+        W.cap[lane] = MODE == kModeEmit ? P.count[A.row] : 0;
+        if (A.R > 0.0f) {
+            const Window w = a_window(A, G);
+            W.z0[lane] = w.z0;
+            W.nseg[lane] = w.nseg;
+            W.wlo[lane][0] = w.lo[0];
+            W.whi[lane][0] = w.hi[0];
+            W.wlo[lane][1] = w.lo[1];
+            W.whi[lane][1] = w.hi[1];
+            n_items = (w.z1 - w.z0 + 1) * w.nseg;
+        } else {
+            W.nseg[lane] = 1;
+            W.z0[lane] = 0;
+        }
+    }
+    // exclusive prefix of item counts over sources
+    int incl = n_items;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    W.ipref[lane] = incl - n_items;
+    const int total_items = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 31) W.ipref[32] = total_items;
+    __syncwarp();
+
+    A64 a_own;  // float64 basis for band rechecks of float32-path sources
+    int a_own_for = -1;
+    uint32_t n_cand = 0, n_re = 0, n_flip = 0, n_mem = 0;
+
+    for (int t0 = 0; t0 < total_items; t0 += kItemCap) {
+        const int nb = min(kItemCap, total_items - t0);
+        // ---- items: (source, zone, segment) -> candidate row range + terms
+        for (int k = lane; k < nb; k += 32) {
+            const int t = t0 + k;
+            int al = 0;  // last source whose first item <= t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (al + step < nloc && W.ipref[al + step] <= t) al += step;
+            const int r = t - W.ipref[al];
+            const int ns = W.nseg[al];
+            const int z = W.z0[al] + r / ns, sg = r % ns;
+            const ZoneInfo& Z = G.zones[z];
+            int64_t lo = Z.start, hi = Z.start;
+            if (Z.end > Z.start) {
+                lo = zone_bound(G, Z, W.wlo[al][sg], false);
+                hi = zone_bound(G, Z, W.whi[al][sg], true);
+                if (hi < lo) hi = lo;
+            }
+            W.it_a[k] = al;
+            W.it_lo[k] = lo;
+            W.it_start[k] = (int32_t)(hi - lo);  // count, scanned below
+            if (PREC == kPrecFP32 && hi > lo) W.it_t[k] = item_terms(W.A[al], Z, z, G.h_f);
+        }
+        __syncwarp();
+        // exclusive scan of item candidate counts (nb <= 64: 2 per lane)
+        {
+            int v[kItemCap / 32];
+            int sum = 0;
+#pragma unroll
+            for (int q = 0; q < kItemCap / 32; q++) {
+                const int k = lane * (kItemCap / 32) + q;
+                v[q] = k < nb ? W.it_start[k] : 0;
+                sum += v[q];
+            }
+            int inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            int run = inc - sum;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kItemCap / 32; q++) {
+                const int k = lane * (kItemCap / 32) + q;
+                if (k < nb) W.it_start[k] = run;
+                run += v[q];
+            }
+            if (lane == 31) W.it_start[nb] = inc;
+        }
+        __syncwarp();
+        const int total_cand = W.it_start[nb];
+
+        // ---- candidates, 32 per round
+        int k = 0;  // item of this lane's candidate; only moves forward
+        for (int c0 = 0; c0 < total_cand; c0 += 32) {
+            const int c = c0 + lane;
+            const bool active = c < total_cand;
+            {
+                const int cc = active ? c : total_cand - 1;
+                while (W.it_start[k + 1] <= cc) k++;  // last item with start <= c
+            }
+            const int al = W.it_a[k];
+            bool is_mem = false;
+            long long key = kKeyInf, rep = 0;
+            int32_t brow = 0x7fffffff;
+            bool rep32 = false;
+            if (active) {
+                const int64_t j = W.it_lo[k] + (c - W.it_start[k]);
+                const APrep& A = W.A[al];
+                const BRec b = G.rec[j];
+                brow = b.row;
+                n_cand++;
+                const bool s64 = W.sep64[al];
+                bool need64 = PREC == kPrecFP64;
+                float x = 0.f, y = 0.f;
+                bool maybe = true, band = false, in32 = false;
+                if (PREC == kPrecFP32) {
+                    // q <= 1 - g: inside; q > 1 + g: outside; between: float64
+                    const float q = q32(A, shape, W.it_t[k], b, &x, &y);
+                    const float g = W.g[al];
+                    maybe = q <= 1.0f + g;
+                    if (maybe) {
+                        band = q >= 1.0f - g;
+                        in32 = q <= 1.0f;
+                        need64 = band || s64;
+                        n_re += band;
+                        is_mem = !need64;
+                    }
+                }
+                double exact = 0.0;
+                if (maybe && need64) {
+                    const A64* a64 = &W.a64[al];
+                    if (!s64) {  // band recheck of a float32-path source
+                        if (a_own_for != al) {
+                            a_own = make_a64(A);
+                            a_own_for = al;
+                        }
+                        a64 = &a_own;
+                    }
+                    double px, py, pz, rho;
+                    load_p64(G, b.row, &px, &py, &pz);
+                    const bool in = test64(*a64, shape, px, py, pz, &rho);
+                    n_flip += band && in != in32;
+                    is_mem = in;
+                    exact = rho * kRadToArcsec;
+                }
+                if (is_mem) {
+                    n_mem++;
+                    if (s64 && MODE != kModeResolve) {
+                        rep = __double_as_longlong(exact);
+                        key = rep;
+                    } else {
+                        const float s2 = fmaf(x, x, y * y);
+                        const float rho32 = s2 < 1e-6f ? sqrtf(s2) * fmaf(s2, 1.0f / 6.0f, 1.0f)
+                                                       : asinf(sqrtf(s2));
+                        rep = (long long)__float_as_int(rho32);
+                        rep32 = true;
+                        // resolve mode ranks by the float64 separation but
+                        // reports the float32 one, as the count pass did
+                        key = MODE == kModeResolve ? __double_as_longlong(exact) : rep;
+                    }
+                }
+            }
+            const uint32_t mem_mask = __ballot_sync(0xffffffffu, is_mem);
+            if (mem_mask == 0) continue;  // nothing to fold this round
+            // ---- fold this round's members per source (segmented over lanes)
+            const uint32_t same = __match_any_sync(0xffffffffu, active ? al : -1);
+            const int rank = __popc(mem_mask & same & lt_mask);
+            const int seg_mem = __popc(mem_mask & same);
+            long long m1 = key, m2 = kKeyInf, r1 = rep;
+            int32_t b1 = is_mem ? brow : 0x7fffffff;
+            // the lane that folds a source's members into shared memory: its
+            // only member lane, or the segment head after a reduction
+            bool leader = is_mem && rank == 0;
+            if (__any_sync(0xffffffffu, seg_mem > 1)) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long om1 = __shfl_down_sync(0xffffffffu, m1, o);
+                    const long long om2 = __shfl_down_sync(0xffffffffu, m2, o);
+                    const long long or1 = __shfl_down_sync(0xffffffffu, r1, o);
+                    const int32_t ob1 = __shfl_down_sync(0xffffffffu, b1, o);
+                    const bool same_seg = lane + o < 32 && ((same >> (lane + o)) & 1u);
+                    if (same_seg) {
+                        if (om1 < m1 || (om1 == m1 && ob1 < b1)) {
+                            m2 = min(m1, om2);
+                            m1 = om1;
+                            b1 = ob1;
+                            r1 = or1;
+                        } else {
+                            m2 = min(m2, om1);
+                        }
+                    }
+                }
+                leader = active && (same & lt_mask) == 0 && seg_mem > 0;
+            }
+            const int base = active ? W.cnt[al] : 0;
+            // arena space for this round's members (count mode, all pairs)
+            long long abase = 0;
+            if (MODE == kModeCount && P.arena) {
+                if (lane == 0)
+                    abase = (long long)atomicAdd(P.arena_n, (unsigned long long)__popc(mem_mask));
+                abase = __shfl_sync(0xffffffffu, abase, 0);
+            }
+            __syncwarp();
+            if (is_mem) {
+                const int idx = base + rank;
+                const APrep& A = W.A[al];
+                if (MODE == kModeCount) {
+                    if (P.arena) {
+                        const long long slot = abase + __popc(mem_mask & lt_mask);
+                        if (slot < P.arena_cap) {
+                            MemberRec r;
+                            r.a_row = A.row;
+                            r.k = idx;
+                            r.b_row = brow;
+                            r.f32 = rep32;
+                            r.sep = __longlong_as_double(rep);
+                            P.arena[slot] = r;
+                        } else {
+                            W.drop[al] = 1;
+                        }
+                    }
+                } else if (MODE == kModeEmit) {
+                    if (idx < W.cap[al]) {
+                        const int64_t o = P.pair_off[A.row] + idx;
+                        P.out_a[o] = A.row;
+                        P.out_b[o] = brow;
+                        P.out_sep[o] = rep32 ? (double)__int_as_float((int)rep) * kRadToArcsec
+                                             : __longlong_as_double(rep);
+                    }
+                }
+            }
+            if (leader) {
+                W.cnt[al] = base + seg_mem;
+                const long long c1 = W.m1[al];
+                const int32_t cb = W.b1[al];
+                if (m1 < c1 || (m1 == c1 && b1 < cb)) {
+                    W.m2[al] = min(c1, min(m2, W.m2[al]));
+                    W.m1[al] = m1;
+                    W.b1[al] = b1;
+                    W.r1[al] = r1;
+                } else {
+                    W.m2[al] = min(W.m2[al], m1);
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+
+    // ---- per-source results (lane = source)
+    if (lane < nloc) {
+        const APrep& A = W.A[lane];
+        const int cnt = W.cnt[lane];
+        const bool s64 = W.sep64[lane] && MODE != kModeResolve;
+        const double best_sep = cnt == 0 ? NAN
+                                : s64    ? __longlong_as_double(W.r1[lane])
+                                         : (double)__int_as_float((int)W.r1[lane]) * kRadToArcsec;
+        if (MODE == kModeCount) {
+            P.count[A.row] = cnt;
+            if (P.want_best) {
+                P.best_b[A.row] = cnt ? (int64_t)W.b1[lane] : -1;
+                P.best_sep[A.row] = best_sep;
+                // float32 separations within twice their error bound of the
+                // smallest: decide the best pair in float64
+                if (PREC == kPrecFP32 && !s64 && cnt > 1 &&
+                    __int_as_float((int)W.m2[lane]) - __int_as_float((int)W.m1[lane]) <=
+                        2.0f * W.esep[lane])
+                    P.tie_list[atomicAdd(&P.list_n[1], 1)] = (int32_t)s_me;
+            }
+            if (W.drop[lane]) P.ovf_list[atomicAdd(&P.list_n[0], 1)] = (int32_t)s_me;
+            if (P.arena && cnt > kSegMax) P.big_list[atomicAdd(&P.list_n[2], 1)] = A.row;
+        } else if (MODE == kModeEmit) {
+            if (cnt != W.cap[lane]) atomicOr(P.err, kErrOverflow);  // passes disagree
+        } else {
+            // resolve: the float64 best pair, with its float32 separation as
+            // the count pass reports it, so the pair list and best row agree
+            P.best_b[A.row] = W.b1[lane];
+            P.best_sep[A.row] = best_sep;
+        }
+    }
+    if (MODE == kModeCount) {
+        warp_add(&P.stats[0], n_cand);
+        warp_add(&P.stats[1], n_re);
+        warp_add(&P.stats[2], n_flip);
+        warp_add(&P.stats[3], n_mem);
+    } else if (MODE == kModeResolve) {
+        warp_add(&P.stats[4], (uint32_t)(lane < nloc));
+    }
+}
+
+constexpr size_t kScanSmem = sizeof(ScanWarpSmem) * kScanWarps;
+
+// Pair records from the arena to their canonical slots: row a_row, member k.
+__global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long long* n_rec,
+                        long long cap, const int64_t* __restrict__ pair_off,
+                        int64_t* __restrict__ out_a, int64_t* __restrict__ out_b,
+                        double* __restrict__ out_sep) {
+    const long long n = min((long long)*n_rec, cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const MemberRec r = arena[i];
+        const int64_t o = pair_off[r.a_row] + r.k;
+        out_a[o] = r.a_row;
+        out_b[o] = r.b_row;
+        out_sep[o] = r.f32 ? (double)__int_as_float((int)__double_as_longlong(r.sep)) * kRadToArcsec
+                           : r.sep;
+    }
+}
+
+// Members of each A row into ascending B row: up to kSmallSort by one thread.
+__global__ void k_sort_small(const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off,
+                             int64_t nA, int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nA) return;
+    const int c = count[i];
+    if (c < 2 || c > kSmallSort) return;
+    const int64_t o = pair_off[i];
+    int64_t br[kSmallSort];
+    double sp[kSmallSort];
+#pragma unroll
+    for (int k = 0; k < kSmallSort; k++)
+        if (k < c) {
+            br[k] = out_b[o + k];
+            sp[k] = out_sep[o + k];
+        }
+    for (int k = 1; k < c; k++) {
+        const int64_t kb = br[k];
+        const double ks = sp[k];
+        int m = k - 1;
+        while (m >= 0 && br[m] > kb) {
+            br[m + 1] = br[m];
+            sp[m + 1] = sp[m];
+            m--;
+        }
+        br[m + 1] = kb;
+        sp[m + 1] = ks;
+    }
+#pragma unroll
+    for (int k = 0; k < kSmallSort; k++)
+        if (k < c) {
+            out_b[o + k] = br[k];
+            out_sep[o + k] = sp[k];
+        }
+}
+
+// Members of A rows with kSmallSort < count <= kWarpSort into ascending B row,
+// one warp per row, warps striding over all rows: every entry's final place
+// is the number of entries with a smaller B row (all distinct within a row),
+// counted against a copy in shared memory.
+constexpr int kWarpSort = 512;
+constexpr int kWarpSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
+    const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off, int64_t nA,
+    int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+    __shared__ int64_t sb[kWarpSortWarps][kWarpSort];
+    __shared__ double ss[kWarpSortWarps][kWarpSort];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kWarpSortWarps;
+    for (int64_t row = (int64_t)blockIdx.x * kWarpSortWarps + w; row < nA; row += stride) {
+        const int32_t c = count[row];
+        if (c <= kSmallSort || c > kWarpSort) continue;  // uniform over the warp
+        const int64_t o = pair_off[row];
+        for (int k = lane; k < c; k += 32) {
+            sb[w][k] = out_b[o + k];
+            ss[w][k] = out_sep[o + k];
+        }
+        __syncwarp();
+        for (int k = lane; k < c; k += 32) {
+            const int64_t key = sb[w][k];
+            int rank = 0;
+            for (int j = 0; j < c; j++) rank += sb[w][j] < key;
+            out_b[o + rank] = key;
+            out_sep[o + rank] = ss[w][k];
+        }
+        __syncwarp();
+    }
+}
+
+// Members of A rows with kWarpSort < count <= kSegMax into ascending B row:
+// a bitonic network in shared memory, one block per row, blocks striding over
+// all rows (no list, so no host synchronisation is needed to launch it).
+__global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ count,
+                                                  const int64_t* __restrict__ pair_off, int64_t nA,
+                                                  int64_t* __restrict__ out_b,
+                                                  double* __restrict__ out_sep) {
+    __shared__ int64_t kb[kSegMax];
+    __shared__ double ks[kSegMax];
+    for (int64_t row = blockIdx.x; row < nA; row += gridDim.x) {
+        const int32_t c = count[row];
+        if (c <= kWarpSort || c > kSegMax) continue;  // uniform over the block
+        const int64_t o = pair_off[row];
+        int np = 1;
+        while (np < c) np <<= 1;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            kb[k] = k < c ? out_b[o + k] : INT64_MAX;
+            ks[k] = k < c ? out_sep[o + k] : 0.0;
+        }
+        __syncthreads();
+        for (int size = 2; size <= np; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                    const int partner = k ^ stride;
+                    if (partner > k) {
+                        const bool up = (k & size) == 0;
+                        if ((kb[k] > kb[partner]) == up) {
+                            const int64_t tb = kb[k];
+                            kb[k] = kb[partner];
+                            kb[partner] = tb;
+                            const double ts = ks[k];
+                            ks[k] = ks[partner];
+                            ks[partner] = ts;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = threadIdx.x; k < c; k += blockDim.x) {
+            out_b[o + k] = kb[k];
+            out_sep[o + k] = ks[k];
+        }
+        __syncthreads();
+    }
+}
+
+// Long segments: sort (b_row, position) pairs with the radix sort, then
+// permute the segment through a scratch copy.
+__global__ void k_seg_keys(const int64_t* __restrict__ b, int64_t n, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint64_t)b[i];
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_seg_permute(const uint32_t* __restrict__ vals, int64_t n,
+                              const int64_t* __restrict__ b_in, const double* __restrict__ s_in,
+                              int64_t* __restrict__ b_out, double* __restrict__ s_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b_out[i] = b_in[vals[i]];
+    s_out[i] = s_in[vals[i]];
+}
+
+}  // namespace
+}  // namespace xm

@@ -19,71 +19,115 @@ namespace xm {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
 
-__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t* __restrict__ keys,
-                                                             int64_t n, int shift, int64_t ntiles,
-                                                             int32_t* __restrict__ hist) {
-    __shared__ int32_t h[kWarps][kRadix];
-    int warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
+// Digit histograms of every pass at once (they do not depend on the order of
+// the keys): hist[p * 256 + d] counts keys whose digit p is d.
+__global__ void __launch_bounds__(kSortThreads) k_all_hist(const uint64_t* __restrict__ keys,
+                                                           int64_t n, int begin_bit, int passes,
+                                                           unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t h[8][kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int k = 0; k < kSortItems; k++) {
-        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFF], 1);
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const uint64_t k = keys[i] >> begin_bit;
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-        int32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; w++) s += h[w][d];
-        hist[(int64_t)d * ntiles + blockIdx.x] = s;
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&hist[i], (unsigned long long)v);
     }
 }
 
-struct ScatterSmem {
+// Look-back status word of one (tile, digit): flag in the top two bits,
+// count (or inclusive prefix) below.
+constexpr uint64_t kStAgg = 1ull << 62;   // tile's own count is available
+constexpr uint64_t kStInc = 2ull << 62;   // inclusive prefix is available
+constexpr uint64_t kStMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;      // polls before a look-back gives up
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+struct OnesweepSmem {
     uint64_t keys[kSortTile];
     uint32_t vals[kSortTile];
     int32_t wcount[kWarps][kRadix];  // per-warp digit counts, then warp offsets
     int32_t dstart[kRadix];          // tile-local start of each digit
     int64_t gstart[kRadix];          // global start of each digit for this tile
+    int64_t pass_off[kRadix];        // first output slot of each digit in the pass
+    int tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
+// One counting pass, in the single-kernel form of the Onesweep sort: tiles
+// take ids in launch order from a counter, rank their keys stably in shared
+// memory, publish their per-digit counts, add up the counts of the tiles
+// before them by walking back through the published words until a tile with
+// an inclusive prefix, then scatter through shared memory. A walk that finds
+// no progress for kSpinLimit polls flags a timeout and carries on, so no
+// block can wait forever; the caller turns the flag into XM_ETIMEOUT.
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
-    int shift, int64_t ntiles, const int64_t* __restrict__ offs, uint64_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out) {
+    int shift, const unsigned long long* __restrict__ hist, uint64_t* status,
+    unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    int32_t* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) S.tile = (int)atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
+    if (threadIdx.x < 32) {  // exclusive scan of the pass histogram (256 digits)
+        int64_t v[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { v[j] = (int64_t)hist[lane * 8 + j]; sum += v[j]; }
+        int64_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int64_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { S.pass_off[lane * 8 + j] = run; run += v[j]; }
+    }
     __syncthreads();
-
-    const int64_t tile_base = (int64_t)blockIdx.x * kSortTile;
+    const int tile = S.tile;
+    const int64_t tile_base = (int64_t)tile * kSortTile;
     const int64_t warp_base = tile_base + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
     int32_t rank[kSortItems];
     // warp-striped: item k of lane l is element warp_base + 32 k + l, so the
-    // (k, lane) order is the input order and ranks are stable
+    // (k, lane) order is the input order and ranks are stable. All loads are
+    // issued before the ranking so they overlap.
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
-        int64_t i = warp_base + 32 * k + lane;
-        bool valid = i < n;
-        key[k] = valid ? keys_in[i] : 0;
-        val[k] = valid ? vals_in[i] : 0;
-        uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        const int64_t i = warp_base + 32 * k + lane;
+        key[k] = i < n ? keys_in[i] : 0;
+        val[k] = i < n ? vals_in[i] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const bool valid = warp_base + 32 * k + lane < n;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
         rank[k] = -1;
         if (valid) {
-            uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
-            uint32_t peers = __match_any_sync(vmask, d);
-            int32_t before = S.wcount[warp][d];
+            const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
+            const uint32_t peers = __match_any_sync(vmask, d);
+            const int32_t before = S.wcount[warp][d];
             rank[k] = before + __popc(peers & lt_mask);
             __syncwarp(vmask);
             if ((peers & lt_mask) == 0) S.wcount[warp][d] = before + __popc(peers);
@@ -91,30 +135,56 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive scan over warps; tile total per digit
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+    // per digit (thread d): warp offsets, tile count, look-back
+    {
+        const int d = threadIdx.x;  // kSortThreads == kRadix
         int32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; w++) {
-            int32_t c = S.wcount[w][d];
+            const int32_t c = S.wcount[w][d];
             S.wcount[w][d] = run;
             run += c;
         }
-        S.dstart[d] = run;  // total, scanned below
-        S.gstart[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+        S.dstart[d] = run;  // tile count, scanned below
+        uint64_t* my = status + (int64_t)tile * kRadix + d;
+        int64_t prefix = 0;
+        if (tile == 0) {
+            st_relaxed(my, kStInc | (uint64_t)run);
+        } else {
+            st_relaxed(my, kStAgg | (uint64_t)run);
+            int t = tile - 1;
+            int spins = 0;
+            while (t >= 0) {
+                const uint64_t v = ld_relaxed(status + (int64_t)t * kRadix + d);
+                const uint64_t flag = v & ~kStMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                prefix += (int64_t)(v & kStMask);
+                if (flag == kStInc) break;
+                t--;
+            }
+            st_relaxed(my, kStInc | (uint64_t)(prefix + run));
+        }
+        S.gstart[d] = S.pass_off[d] + prefix;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of 256 digit totals by one warp
-        int32_t v[8], s = 0;
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 tile counts by one warp
+        int32_t v[8], sm = 0;
 #pragma unroll
-        for (int j = 0; j < 8; j++) { v[j] = S.dstart[lane * 8 + j]; s += v[j]; }
-        int32_t incl = s;
+        for (int j = 0; j < 8; j++) { v[j] = S.dstart[lane * 8 + j]; sm += v[j]; }
+        int32_t incl = sm;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        int32_t run = incl - s;
+        int32_t run = incl - sm;
 #pragma unroll
         for (int j = 0; j < 8; j++) { S.dstart[lane * 8 + j] = run; run += v[j]; }
     }
@@ -122,8 +192,8 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         if (rank[k] >= 0) {
-            uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
-            int32_t p = S.dstart[d] + S.wcount[warp][d] + rank[k];
+            const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
+            const int32_t p = S.dstart[d] + S.wcount[warp][d] + rank[k];
             S.keys[p] = key[k];
             S.vals[p] = val[k];
         }
@@ -132,9 +202,9 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     int64_t valid_n = n - tile_base;
     if (valid_n > kSortTile) valid_n = kSortTile;
     for (int p = threadIdx.x; p < valid_n; p += kSortThreads) {
-        uint64_t kk = S.keys[p];
-        uint32_t d = (uint32_t)(kk >> shift) & 0xFF;
-        int64_t g = S.gstart[d] + (p - S.dstart[d]);
+        const uint64_t kk = S.keys[p];
+        const uint32_t d = (uint32_t)(kk >> shift) & 0xFF;
+        const int64_t g = S.gstart[d] + (p - S.dstart[d]);
         keys_out[g] = kk;
         vals_out[g] = S.vals[p];
     }
@@ -264,39 +334,45 @@ xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t
 }
 
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                         int end_bit, cudaStream_t s) {
-    if (n <= 1 || end_bit <= 0) return XM_OK;
-    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    int32_t* hist = (int32_t*)dev_alloc(kRadix * ntiles * sizeof(int32_t), s);
-    int64_t* offs = (int64_t*)dev_alloc(kRadix * ntiles * sizeof(int64_t), s);
-    if (!hist || !offs) {
-        dev_free(hist, s);
-        dev_free(offs, s);
-        return set_error(XM_ENOMEM, "radix sort of %lld keys", (long long)n);
-    }
+                         int begin_bit, int end_bit, int32_t* err, cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return XM_OK;
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    if (passes > 8) return set_error(XM_EINVAL, "radix sort: more than 64 key bits");
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    // per pass: 256 histogram counters, ntiles x 256 status words, 1 counter
+    const size_t st_words = (size_t)ntiles * kRadix;
+    const size_t bytes = passes * (kRadix * sizeof(unsigned long long) + st_words * sizeof(uint64_t) +
+                                   sizeof(uint64_t)) + 16;
+    unsigned char* work = (unsigned char*)dev_alloc(bytes, s);
+    if (!work) return set_error(XM_ENOMEM, "radix sort of %lld keys", (long long)n);
+    unsigned long long* hist = (unsigned long long*)work;
+    uint64_t* status = (uint64_t*)(hist + passes * kRadix);
+    unsigned int* counters = (unsigned int*)(status + passes * st_words);
     static bool attr_done = false;
-    size_t smem = sizeof(ScatterSmem);
+    const size_t smem = sizeof(OnesweepSmem);
     if (!attr_done) {
-        cudaFuncSetAttribute(k_digit_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
     xm_status st = XM_OK;
+    cudaError_t e = cudaMemsetAsync(work, 0, bytes, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "radix sort memset");
     uint64_t *ki = keys, *ko = tk;
     uint32_t *vi = vals, *vo = tv;
-    int passes = (end_bit + 7) / 8;
+    if (st == XM_OK) {
+        const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
+        launch_begin("k_all_hist", s);
+        k_all_hist<<<hg, kSortThreads, 0, s>>>(keys, n, begin_bit, passes, hist);
+        e = launch_end("k_all_hist", s);
+        if (e != cudaSuccess) st = cuda_fail(e, "k_all_hist");
+    }
     for (int p = 0; p < passes && st == XM_OK; p++) {
-        int shift = 8 * p;
-        launch_begin("k_digit_hist", s);
-        k_digit_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, ntiles, hist);
-        cudaError_t e = launch_end("k_digit_hist", s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "k_digit_hist"); break; }
-        st = exclusive_scan_i32(hist, offs, kRadix * ntiles, nullptr, s);
-        if (st != XM_OK) break;
-        launch_begin("k_digit_scatter", s);
-        k_digit_scatter<<<(unsigned)ntiles, kSortThreads, smem, s>>>(ki, vi, n, shift, ntiles, offs,
-                                                                      ko, vo);
-        e = launch_end("k_digit_scatter", s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "k_digit_scatter"); break; }
+        launch_begin("k_onesweep", s);
+        k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, s>>>(
+            ki, vi, n, begin_bit + 8 * p, hist + p * kRadix, status + p * st_words, counters + p,
+            ko, vo, err);
+        e = launch_end("k_onesweep", s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;
         uint32_t* u = vi; vi = vo; vo = u;
     }
@@ -305,8 +381,7 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
         cudaError_t e2 = cudaMemcpyAsync(vals, vi, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         if (e1 != cudaSuccess || e2 != cudaSuccess) st = cuda_fail(e1 != cudaSuccess ? e1 : e2, "sort copy");
     }
-    dev_free(hist, s);
-    dev_free(offs, s);
+    dev_free(work, s);
     return st;
 }
 

@@ -171,7 +171,7 @@ class _DevArray:
     def __init__(self, ptr, n, typestr, owner):
         self.owner = owner
         self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
-                                         "data": (int(ptr or 0), True), "version": 3,
+                                         "data": (int(ptr or 0), False), "version": 3,
                                          "strides": None}
 
 

@@ -290,7 +290,7 @@ def test_single_source_and_duplicates(xm):
         res = xm.Result(idx, _cuda([10.0]), _cuda([0.0]), precision=prec, shape=0, a=2.0)
         np.testing.assert_array_equal(_host(res.b_row), [0, 1, 2])
         assert _host(res.best_b)[0] == 0
-        assert _host(res.best_sep)[0] == pytest.approx(0.36, abs=1e-6)
+        assert _host(res.best_sep)[0] == pytest.approx(0.36, abs=SEP_TOL)
 
 
 def test_zero_size_region_matches_nothing(xm):
@@ -322,21 +322,23 @@ def test_invalid_input_is_einval(xm, bad):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_many_members_overflow_and_long_segments(xm, prec):
-    """Regions with 9..2048 members take the re-scan path; one with more than
-    2048 takes the long-segment sort."""
+    """Member lists of every size class reach the canonical order: more than
+    2048 (long-segment radix sort), 513..2048 (block sort), 17..512 (warp
+    sort) and up to 16 (per-thread sort)."""
     g = synth.rng(9)
     b_lon, b_lat = synth.cap(g, 6000, 45.0, 30.0, 0.05)
-    a_lon = np.array([45.0, 45.01, 45.02, 44.99])
-    a_lat = np.array([30.0, 30.01, 30.0, 29.98])
-    a_col = np.array([170.0, 40.0, 12.0, 5.0])  # ~all, ~hundreds, ~tens, ~few
+    a_lon = np.array([45.0, 45.005, 45.01, 45.02, 44.99])
+    a_lat = np.array([30.0, 29.995, 30.01, 30.0, 29.98])
+    a_col = np.array([170.0, 70.0, 40.0, 12.0, 5.0])
     d = dict(a_lon=a_lon, a_lat=a_lat, b_lon=b_lon, b_lat=b_lat, a_frame=0, b_frame=0,
              region=dict(shape=0, a_col=a_col))
     ref = oracle_ref(d)
-    counts = np.bincount(ref["a_row"], minlength=4)
-    assert counts[0] > 2048 and 8 < counts[1] <= 2048
+    counts = np.bincount(ref["a_row"], minlength=5)
+    assert counts[0] > 2048 and 512 < counts[1] <= 2048 and 16 < counts[2] <= 512
+    assert 16 < counts[3] <= 512 and counts[4] <= 16
     _, res = run(xm, d, prec, zone_height=20.0)
     check_pairs(res, ref)
-    check_best(res, ref, 4)
+    check_best(res, ref, 5)
 
 
 # ------------------------------------------------------------------ C3
