@@ -252,6 +252,26 @@ typedef struct {
 } xm_rows_view;
 XM_API xm_status xm_rows_get(const xm_rows* rows, xm_rows_view* view);
 
+/* The join of xm_join for callers that cannot allocate device memory when
+ * they need it: a process or framework whose own allocator has reserved the
+ * whole GPU (an allocation by this library would fail or fragment its pool),
+ * or a latency-critical loop that must not enter the driver's allocator. The
+ * paper has no counterpart: it is an interface addition of this library.
+ * It allocates nothing. The caller passes device arrays a_row, b_row, sep of
+ * `capacity` rows; the rows (same content and order as xm_join's) are
+ * written there by work queued on `stream`, and *n_rows receives their
+ * number. Scratch is one device array built into the library, sized for
+ * results of at most 2^20 A rows and 2^23 B rows (about 16 MB, held on every
+ * GPU that loads the library until the process exits); larger results are
+ * XM_EOVERFLOW, as is a row count above `capacity` (*n_rows still reports
+ * it, nothing is written). The first call on a device looks up that array's
+ * device address, so make it before any stream capture. All calls share the
+ * array: calls whose work overlaps on the GPU (on different streams without
+ * ordering) race and must not be made. Synchronises `stream` once. */
+XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int32_t join_type,
+                                 int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
+                                 int64_t* n_rows, void* stream);
+
 /* Copies a device array of `bytes` bytes to host memory on `stream` and
  * waits for it (convenience for callers without their own CUDA runtime). */
 XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);

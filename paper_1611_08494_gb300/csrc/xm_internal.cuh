@@ -302,6 +302,10 @@ xm_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t
                              cudaStream_t s);
 xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
                              cudaStream_t s);
+// The same without allocating: ws holds 2 * ceil(n / 4096) int64 values and
+// n is at most 4096 * 4096.
+xm_status exclusive_scan_i32_ws(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
+                                int64_t* ws, cudaStream_t s);
 
 // Host-side galactic -> equatorial rotation (row major, v_eq = m v_gal).
 void gal_to_eq(double m[9]);

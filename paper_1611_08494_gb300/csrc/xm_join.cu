@@ -107,6 +107,138 @@ __global__ void k_write_b(const uint32_t* __restrict__ bits, const int64_t* __re
 }  // namespace
 }  // namespace xm
 
+namespace xm {
+
+// ------------------------------------------------ join without allocation
+//
+// Some callers cannot allocate device memory at the moment they need a join:
+// a serving process or a framework whose caching allocator has reserved the
+// whole GPU (a cudaMalloc would fail or fragment its pool), or a
+// latency-critical loop that must not enter the driver's allocator.
+// xm_join_noalloc gives them the join with no allocation at all: the caller
+// passes the output arrays, and the scratch lives in one file-scope device
+// array sized for results of at most kNoAllocMaxA A rows and kNoAllocMaxB B
+// rows. Every GPU that loads the library holds that array (about 16 MB)
+// until the process exits.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxA = 1 << 20;  // A rows
+constexpr int64_t kNoAllocMaxB = 1 << 23;  // B rows
+constexpr int64_t kNoAllocWords = kNoAllocMaxB / 32;
+
+struct JoinScratch {
+    uint32_t bits[kNoAllocWords];      // matched B rows
+    int32_t rows[kNoAllocMaxA];        // rows per A source
+    int64_t row_off[kNoAllocMaxA];
+    int32_t wcount[kNoAllocWords];     // unmatched B rows per word
+    int64_t word_off[kNoAllocWords];
+    int64_t ws_a[2 * (kNoAllocMaxA / 4096)];     // scan workspace (rows)
+    int64_t ws_b[2 * (kNoAllocWords / 4096)];    // scan workspace (words)
+    int64_t small[4];                  // totals, unmatched A count
+};
+
+static __device__ __align__(256) JoinScratch g_join_scratch;
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side symbol is not a device address).
+xm_status join_scratch(JoinScratch** out) {
+    static JoinScratch* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(XM_EUNSUPPORTED, "device %d", dev);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_join_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(join scratch)");
+        addr[dev] = (JoinScratch*)p;
+    }
+    *out = addr[dev];
+    return XM_OK;
+}
+
+}  // namespace
+}  // namespace xm
+
+extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int32_t join_type,
+                                     int64_t* a_row, int64_t* b_row, double* sep,
+                                     int64_t capacity, int64_t* n_rows, void* stream) {
+    using namespace xm;
+    if (!n_rows) return set_error(XM_EINVAL, "xm_join_noalloc: n_rows is NULL");
+    *n_rows = 0;
+    if (!R) return set_error(XM_EINVAL, "xm_join_noalloc: NULL result");
+    if (selection != XM_SEL_ALL && selection != XM_SEL_BEST)
+        return set_error(XM_EINVAL, "xm_join_noalloc: selection must be ALL or BEST");
+    if (!(R->selection & selection))
+        return set_error(XM_EINVAL, "xm_join_noalloc: selection not computed by xm_match");
+    if (join_type < XM_JOIN_AND || join_type > XM_JOIN_XOR)
+        return set_error(XM_EINVAL, "xm_join_noalloc: bad join type %d", join_type);
+    if (capacity < 0 || (capacity > 0 && (!a_row || !b_row || !sep)))
+        return set_error(XM_EINVAL, "xm_join_noalloc: bad output arrays");
+    const int64_t nA = R->n_a, nB = R->n_b;
+    if (nA > kNoAllocMaxA || nB > kNoAllocMaxB)
+        return set_error(XM_EOVERFLOW,
+                         "xm_join_noalloc: the result has %lld A rows and %lld B rows; this entry "
+                         "point takes at most %lld and %lld (use xm_join)",
+                         (long long)nA, (long long)nB, (long long)kNoAllocMaxA,
+                         (long long)kNoAllocMaxB);
+    const bool with_pairs = join_type == XM_JOIN_AND || join_type == XM_JOIN_OR ||
+                            join_type == XM_JOIN_ALL1 || join_type == XM_JOIN_ALL2;
+    const bool with_un_a = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL1 ||
+                           join_type == XM_JOIN_NOT1_2 || join_type == XM_JOIN_XOR;
+    const bool with_un_b = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL2 ||
+                           join_type == XM_JOIN_NOT2_1 || join_type == XM_JOIN_XOR;
+    const int sel_all = selection == XM_SEL_ALL;
+    const int64_t nwords = (nB + 31) / 32;
+    cudaStream_t s = (cudaStream_t)stream;
+    JoinScratch* S = nullptr;
+    xm_status st = join_scratch(&S);
+    if (st != XM_OK) return st;
+    // the array keeps the previous call's contents: clear what starts at zero
+    cudaError_t e = cudaMemsetAsync(S->bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->small, 0, sizeof(S->small), s);
+    if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc memset");
+    if (sel_all) {
+        if (R->n_pairs > 0) k_mark_b<<<grid_for(R->n_pairs), kBlock, 0, s>>>(R->b_row, R->n_pairs, S->bits);
+    } else if (nA > 0) {
+        k_mark_b<<<grid_for(nA), kBlock, 0, s>>>(R->best_b, nA, S->bits);
+    }
+    if (nA > 0)
+        k_rows_a<<<grid_for(nA), kBlock, 0, s>>>(R->count, nA, sel_all, (int)with_pairs,
+                                                 (int)with_un_a, S->rows,
+                                                 (unsigned long long*)&S->small[2]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc launch");
+    st = exclusive_scan_i32_ws(S->rows, S->row_off, nA, &S->small[0], S->ws_a, s);
+    if (st != XM_OK) return st;
+    if (nwords > 0)
+        k_word_unmatched<<<grid_for(nwords), kBlock, 0, s>>>(S->bits, nwords, nB, S->wcount);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc launch");
+    st = exclusive_scan_i32_ws(S->wcount, S->word_off, nwords, &S->small[1], S->ws_b, s);
+    if (st != XM_OK) return st;
+    int64_t h[4];
+    e = cudaMemcpyAsync(h, S->small, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc sync");
+    const int64_t total_a = h[0], un_b = h[1];
+    const int64_t n = total_a + (with_un_b ? un_b : 0);
+    *n_rows = n;
+    if (n > capacity)
+        return set_error(XM_EOVERFLOW, "xm_join_noalloc: %lld rows do not fit the capacity %lld",
+                         (long long)n, (long long)capacity);
+    if (nA > 0)
+        k_write_a<<<grid_for(nA), kBlock, 0, s>>>(R->count, R->pair_off, R->b_row, R->sep, R->best_b,
+                                                 R->best_sep, S->row_off, nA, sel_all,
+                                                 (int)with_pairs, (int)with_un_a, a_row, b_row, sep);
+    if (with_un_b && nB > 0)
+        k_write_b<<<grid_for(nB), kBlock, 0, s>>>(S->bits, S->word_off, nB, total_a, a_row, b_row, sep);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc launch");
+    return XM_OK;
+}
+
 using namespace xm;
 
 static void free_rows(xm_rows* J) {

@@ -323,6 +323,29 @@ xm_status scan_impl(const T* in, int64_t* out, int64_t n, int64_t* total, cudaSt
 
 }  // namespace
 
+// Exclusive scan of up to 4096 tiles of int32 input with caller-provided
+// workspace (2 * ceil(n / 4096) int64 values) instead of allocations; used
+// by the entry point that must not allocate. Plain launches, no profiling.
+xm_status exclusive_scan_i32_ws(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
+                                int64_t* ws, cudaStream_t s) {
+    if (n <= 0) {
+        if (total && cudaMemsetAsync(total, 0, sizeof(int64_t), s) != cudaSuccess)
+            return set_error(XM_ECUDA, "scan memset");
+        return XM_OK;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanTile) return set_error(XM_EOVERFLOW, "scan workspace: %lld elements", (long long)n);
+    if (ntiles == 1) {
+        k_tile_scan<int32_t><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out, total);
+    } else {
+        k_tile_sums<int32_t><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, ws);
+        k_tile_scan<int64_t><<<1, kScanThreads, 0, s>>>(ws, ntiles, nullptr, ws + ntiles, nullptr);
+        k_tile_scan<int32_t><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, ws + ntiles, out, total);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? XM_OK : cuda_fail(e, "scan");
+}
+
 xm_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
                              cudaStream_t s) {
     return scan_impl<int32_t>(in, out, n, total, s);

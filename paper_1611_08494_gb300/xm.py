@@ -102,6 +102,8 @@ xm_join = _sig("xm_join", _i32, _p, _i32, _i32, _p, ctypes.POINTER(_p))
 xm_rows_free = _sig("xm_rows_free", _i32, _p)
 xm_rows_get = _sig("xm_rows_get", _i32, _p, ctypes.POINTER(RowsView))
 xm_copy_to_host = _sig("xm_copy_to_host", _i32, _p, _p, ctypes.c_size_t, _p)
+xm_join_noalloc = _sig("xm_join_noalloc", _i32, _p, _i32, _i32, _p, _p, _p, _i64,
+                       ctypes.POINTER(_i64), _p)
 xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
 
 
