@@ -272,6 +272,76 @@ XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int
                                  int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
                                  int64_t* n_rows, void* stream);
 
+/* ---- batches of requests (one launch of the persistent scan) --------- */
+
+/* One cross-match request of a batch: an A catalogue, its region (§2.1), the
+ * selections to keep (§2.2) and optionally one join type applied to one of
+ * them. join_type < 0 asks for no join. */
+typedef struct {
+    xm_columns A;
+    xm_region region;
+    int32_t selection;       /* XM_SEL_ALL and/or XM_SEL_BEST */
+    int32_t join_type;       /* xm_join_type, or -1 */
+    int32_t join_selection;  /* XM_SEL_ALL or XM_SEL_BEST: the pairs the join uses */
+    int32_t reserved;
+} xm_request;
+
+typedef struct {
+    int32_t precision;          /* xm_precision, for every request */
+    int32_t use_graph;          /* capture the device pipeline in a CUDA graph */
+    int32_t persistent_blocks;  /* blocks per SM of the persistent scan, 0 = 4 */
+    int32_t reserved;
+    int64_t pair_capacity;      /* pair arena; 0 = estimate (grown and rerun if short) */
+    int64_t row_capacity;       /* join-row arena; 0 = estimate (likewise) */
+} xm_batch_opts;
+
+typedef struct xm_batch xm_batch;
+
+/* Matches every request of a batch against one resident index in one pass:
+ * all A sources of all requests are ingested, sorted on (zone, RA) together
+ * and scanned by one persistent kernel whose warps take 32-source chunks
+ * from a device work queue, so uneven requests share the GPU evenly. The
+ * device work of the pass has no host synchronisation inside, so with
+ * use_graph it is captured as one CUDA graph and launched once. Per request
+ * the results are those of xm_match (pairs in ascending A row then B row,
+ * best pairs, member counts), plus, when a join is asked for, its A-side rows
+ * (pairs and unmatched A rows as the join type takes them, in the order of
+ * xm_join) and its numbers of unmatched A and B rows. Synchronises `stream`
+ * once (twice if an arena was too small). Errors: as xm_match; XM_EINVAL
+ * names the request. */
+XM_API xm_status xm_match_batch(const xm_index* index, const xm_request* requests, int64_t n,
+                                const xm_batch_opts* opts, void* stream, xm_batch** out);
+XM_API xm_status xm_batch_free(xm_batch* batch);
+
+/* Device arrays of one request of a batch (valid until xm_batch_free). A rows
+ * are the request's own rows. B-only rows of a join are not materialised
+ * here (their number is n_unmatched_b); xm_batch_join builds them. */
+typedef struct {
+    int64_t n_a, n_pairs;
+    const int64_t* a_row;
+    const int64_t* b_row;
+    const double* sep_arcsec;
+    const int32_t* count;
+    const int64_t* best_b_row;
+    const double* best_sep_arcsec;
+    int64_t n_rows;            /* A-side join rows */
+    const int64_t* row_a;
+    const int64_t* row_b;
+    const double* row_sep;
+    int64_t n_unmatched_a, n_unmatched_b;
+} xm_batch_view;
+XM_API xm_status xm_batch_get(const xm_batch* batch, int64_t request, xm_batch_view* view);
+
+/* All rows of the request's join, B-only rows included, as xm_join builds
+ * them. */
+XM_API xm_status xm_batch_join(const xm_batch* batch, int64_t request, void* stream,
+                               xm_rows** out);
+
+/* Totals of a batch: A sources, pairs, and the device time of its pass (ms,
+ * from events around the device work). */
+XM_API xm_status xm_batch_info(const xm_batch* batch, int64_t* total_a, int64_t* total_pairs,
+                               double* device_ms);
+
 /* Copies a device array of `bytes` bytes to host memory on `stream` and
  * waits for it (convenience for callers without their own CUDA runtime). */
 XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);

@@ -91,8 +91,10 @@ struct __align__(16) APrep {
     int32_t z;            // zone
     float zfrac;          // t - z - 1/2 (zones)
     float R;              // bounding radius (rad); 0 = empty region
-    int32_t row;          // row in the caller's A catalogue
+    int32_t row;          // A row: in the caller's catalogue, or batch-wide
     float m00, m01, m10, m11;  // float32 map (x, y) -> (X/a, Y/b)
+    int32_t shape;        // xm_shape of the source's region
+    int32_t req;          // request of a batch (0 for single calls)
 };
 
 // Geometry of a built index, passed by value to kernels.
@@ -291,6 +293,10 @@ xm_status set_error(xm_status s, const char* fmt, ...);
 // caller reads at its next synchronisation.
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
                          int begin_bit, int end_bit, int32_t* err, cudaStream_t s);
+
+// Sets the sort kernels' shared-memory limits (done on first use; call it
+// before capturing a stream that sorts).
+void radix_sort_prepare();
 
 // Sort keys file sources by zone, then by RA to 2^-24 of a turn (0.08
 // arcsec): the low 8 bits of the RA key are dropped, so the sort starts at

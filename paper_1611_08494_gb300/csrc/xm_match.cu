@@ -74,61 +74,6 @@ struct Temps {
     }
 };
 
-// Segments of more than kSegMax members (host-listed rows): radix sort of
-// (B row, position) pairs, then a permutation through a scratch copy.
-xm_status sort_long_segments(const int32_t* d_rows, int64_t n_big, xm_result* R, int32_t* err,
-                             cudaStream_t s);
-
-}  // namespace
-}  // namespace xm
-
-namespace xm {
-namespace {
-xm_status sort_long_segments(const int32_t* d_rows, int64_t n_big, xm_result* R, int32_t* err,
-                             cudaStream_t s) {
-    int32_t* h_big = new (std::nothrow) int32_t[n_big];
-    if (!h_big) return set_error(XM_ENOMEM, "host list");
-    cudaError_t e = cudaMemcpyAsync(h_big, d_rows, n_big * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    xm_status r = XM_OK;
-    for (int64_t k = 0; k < n_big && e == cudaSuccess && r == XM_OK; k++) {
-        const int32_t row = h_big[k];
-        int32_t c = 0;
-        int64_t off = 0;
-        e = cudaMemcpyAsync(&c, R->count + row, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&off, R->pair_off + row, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) break;
-        uint64_t* sk = (uint64_t*)dev_alloc(2 * (size_t)c * sizeof(uint64_t), s);
-        uint32_t* sv = (uint32_t*)dev_alloc(2 * (size_t)c * sizeof(uint32_t), s);
-        int64_t* cb = (int64_t*)dev_alloc((size_t)c * (sizeof(int64_t) + sizeof(double)), s);
-        if (!sk || !sv || !cb) {
-            r = set_error(XM_ENOMEM, "segment sort");
-        } else {
-            double* cs = (double*)(cb + c);
-            launch_begin("k_seg_keys", s);
-            k_seg_keys<<<grid_for(c), kBlock, 0, s>>>(R->b_row + off, c, sk, sv);
-            e = launch_end("k_seg_keys", s);
-            if (e == cudaSuccess) r = radix_sort_u64(sk, sv, sk + c, sv + c, c, 0, 32, err, s);
-            if (e == cudaSuccess && r == XM_OK)
-                e = cudaMemcpyAsync(cb, R->b_row + off, c * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess && r == XM_OK)
-                e = cudaMemcpyAsync(cs, R->sep + off, c * sizeof(double), cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess && r == XM_OK) {
-                launch_begin("k_seg_permute", s);
-                k_seg_permute<<<grid_for(c), kBlock, 0, s>>>(sv, c, cb, cs, R->b_row + off, R->sep + off);
-                e = launch_end("k_seg_permute", s);
-            }
-        }
-        dev_free(sk, s);
-        dev_free(sv, s);
-        dev_free(cb, s);
-    }
-    delete[] h_big;
-    if (e != cudaSuccess) return cuda_fail(e, "segment sort");
-    return r;
-}
 }  // namespace
 }  // namespace xm
 
@@ -313,7 +258,8 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 R->b_row = R->a_row + np;
                 R->sep = (double*)(R->b_row + np);
                 XM_LAUNCH("k_place", 4 * 152, 256, 0, s, k_place, arena, arena_n, arena_cap,
-                          R->pair_off, R->a_row, R->b_row, R->sep);
+                          R->pair_off, (const int32_t*)nullptr, (long long)np, R->a_row, R->b_row,
+                          R->sep);
                 if (n_ovf > 0) {
                     ScanArgs b = a;
                     b.list = lists;
@@ -322,19 +268,20 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                     b.out_a = R->a_row;
                     b.out_b = R->b_row;
                     b.out_sep = R->sep;
+                    b.out_cap = np;
                     r = launch_scan_any(prec, b, kModeEmit, n_ovf, s);
                     if (r != XM_OK) return r;
                 }
                 if (nA > 0) {
                     XM_LAUNCH("k_sort_small", grid_for(nA), kBlock, 0, s, k_sort_small, R->count,
-                              R->pair_off, nA, R->b_row, R->sep);
+                              R->pair_off, nA, (long long)np, R->b_row, R->sep);
                     XM_LAUNCH("k_sort_warp", (unsigned)((nA + 4 * kWarpSortWarps - 1) / (4 * kWarpSortWarps) < 8 * 152
                                                          ? (nA + 4 * kWarpSortWarps - 1) / (4 * kWarpSortWarps)
                                                          : 8 * 152),
                               32 * kWarpSortWarps, 0, s, k_sort_warp, R->count, R->pair_off, nA,
-                              R->b_row, R->sep);
+                              (long long)np, R->b_row, R->sep);
                     XM_LAUNCH("k_seg_sort", (unsigned)(nA < 2 * 152 ? nA : 2 * 152), kBlock, 0, s,
-                              k_seg_sort, R->count, R->pair_off, nA, R->b_row, R->sep);
+                              k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep);
                 }
                 if (n_big > 0) {
                     // rare: regions holding more than kSegMax sources

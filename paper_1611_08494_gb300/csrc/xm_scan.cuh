@@ -15,6 +15,8 @@
 
 #include <math.h>
 
+#include <new>
+
 #include "xm_internal.cuh"
 
 namespace xm {
@@ -43,16 +45,16 @@ struct AIn {
     int32_t nz;
 };
 
-// Index-frame position of A source i, in degrees (lon in [0, 360)), and the
-// angle gamma from the index frame's north to the input frame's north (east
-// positive) at that point.
-__device__ void a_position(const AIn& I, int64_t i, double* lon_o, double* lat_o, double* gamma,
-                           bool* ok) {
-    double lon = I.lon[i], lat = I.lat[i];
+// Index-frame position of an A source given as (lon, lat) in its input
+// frame, in degrees (lon in [0, 360)), and the angle gamma from the index
+// frame's north to the input frame's north (east positive) at that point.
+// rot (row major) maps input-frame vectors to the index frame when rotate.
+__device__ void a_position_of(double lon, double lat, int32_t rotate, const double* rot,
+                              double* lon_o, double* lat_o, double* gamma, bool* ok) {
     *ok = coord_ok(lon, lat);
     if (!*ok) { lon = 0.0; lat = 0.0; }
     lon = lon_mod360(lon);
-    if (!I.rotate) {
+    if (!rotate) {
         *lon_o = lon;
         *lat_o = lat;
         *gamma = 0.0;
@@ -65,8 +67,8 @@ __device__ void a_position(const AIn& I, int64_t i, double* lon_o, double* lat_o
     const double nn[3] = {-sb * cl, -sb * sl, cb};
     double q[3], m[3];
     for (int k = 0; k < 3; k++) {
-        q[k] = I.rot[3 * k] * p[0] + I.rot[3 * k + 1] * p[1] + I.rot[3 * k + 2] * p[2];
-        m[k] = I.rot[3 * k] * nn[0] + I.rot[3 * k + 1] * nn[1] + I.rot[3 * k + 2] * nn[2];
+        q[k] = rot[3 * k] * p[0] + rot[3 * k + 1] * p[1] + rot[3 * k + 2] * p[2];
+        m[k] = rot[3 * k] * nn[0] + rot[3 * k + 1] * nn[1] + rot[3 * k + 2] * nn[2];
     }
     const double rxy = hypot(q[0], q[1]);
     double r = atan2(q[1], q[0]) / kDeg;
@@ -80,6 +82,11 @@ __device__ void a_position(const AIn& I, int64_t i, double* lon_o, double* lat_o
     const double me = -m[0] * sa + m[1] * ca;
     const double mn = -m[0] * sd * ca - m[1] * sd * sa + m[2] * cd;
     *gamma = atan2(me, mn);
+}
+
+__device__ __forceinline__ void a_position(const AIn& I, int64_t i, double* lon_o, double* lat_o,
+                                           double* gamma, bool* ok) {
+    a_position_of(I.lon[i], I.lat[i], I.rotate, I.rot, lon_o, lat_o, gamma, ok);
 }
 
 __device__ __forceinline__ bool size_ok(double a, double b, double pa) {
@@ -103,35 +110,32 @@ __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restr
     vals[i] = (uint32_t)i;
 }
 
-__global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= I.n) return;
-    const int64_t i = vals[s];
-    double lon, lat, gamma;
-    bool ok;
-    a_position(I, i, &lon, &lat, &gamma, &ok);
-    double a = I.a_col ? I.a_col[i] : I.a;
-    double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
-    double pa = I.pa_col ? I.pa_col[i] : I.pa;
+// The prepared form of one A source (position already in the index frame).
+__device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma, bool ok, double a,
+                                            double b, double pa, int32_t shape, int32_t pa_dir,
+                                            double size_k, double pa_zero, double zscale,
+                                            int32_t nz, int32_t row, int32_t req) {
     if (!size_ok(a, b, pa)) a = b = pa = 0.0;
     APrep P;
     P.alpha = lon * kDeg;
     P.delta = lat * kDeg;
-    const PosKey k = pos_key(lon, lat, I.zscale, I.nz);
+    const PosKey k = pos_key(lon, lat, zscale, nz);
     P.key64 = k.key64;
     P.z = k.z;
     P.zfrac = k.zfrac;
-    P.row = (int32_t)i;
-    P.a = a * I.size_k;
-    P.b = b * I.size_k;
-    double th = (I.pa_zero + I.pa_dir * pa) * kDeg + gamma;
+    P.row = row;
+    P.shape = shape;
+    P.req = req;
+    P.a = a * size_k;
+    P.b = b * size_k;
+    double th = (pa_zero + pa_dir * pa) * kDeg + gamma;
     th = remainder(th, kTwoPi);
     P.theta = th;
     if (P.a <= 0.0 || P.b <= 0.0 || !ok) {
         P.R = 0.0f;
         P.m00 = P.m01 = P.m10 = P.m11 = 0.0f;
     } else {
-        const double R = I.shape == XM_RECT ? hypot(P.a, P.b) : fmax(P.a, P.b);
+        const double R = shape == XM_RECT ? hypot(P.a, P.b) : fmax(P.a, P.b);
         P.R = (float)(R * (1.0 + 1e-6));
         float st, ct;
         sincosf((float)th, &st, &ct);
@@ -141,7 +145,21 @@ __global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __rest
         P.m10 = ct * ib;
         P.m11 = -st * ib;
     }
-    out[s] = P;
+    return P;
+}
+
+__global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= I.n) return;
+    const int64_t i = vals[s];
+    double lon, lat, gamma;
+    bool ok;
+    a_position(I, i, &lon, &lat, &gamma, &ok);
+    const double a = I.a_col ? I.a_col[i] : I.a;
+    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
+    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    out[s] = make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero,
+                        I.zscale, I.nz, (int32_t)i, 0);
 }
 
 // One member found by the count pass: A row, its index among that row's
@@ -160,6 +178,8 @@ struct ScanArgs {
     int32_t want_best;
     const int32_t* list;  // sorted A indices to process (overflow / ties)
     int64_t nlist;
+    const int32_t* nlist_dev;  // list length read on the device (overrides nlist)
+    unsigned int* queue;       // work queue: warps claim 32-source chunks (persistent)
     // count mode: per A row
     int32_t* count;
     int64_t* best_b;
@@ -176,6 +196,8 @@ struct ScanArgs {
     int64_t* out_a;
     int64_t* out_b;
     double* out_sep;
+    long long out_cap;          // slots of the pair list
+    const int32_t* lrow;        // batch: batch-wide A row -> request row
     int32_t* err;               // status bits
     unsigned long long* stats;  // candidates, rechecked, flipped, members, tie_resolved
 };
@@ -375,12 +397,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ScanWarpSmem& W = reinterpret_cast<ScanWarpSmem*>(scan_smem)[warp];
     const IndexGeom& G = P.G;
-    const int shape = P.shape;
-    const int64_t n_units = P.list ? P.nlist : P.nA;
-    const int64_t first = ((int64_t)blockIdx.x * kScanWarps + warp) * 32;
-    if (first >= n_units) return;  // whole warp
-    const int nloc = (int)min((int64_t)32, n_units - first);
+    const int64_t n_units = P.list ? (P.nlist_dev ? (int64_t)*P.nlist_dev : P.nlist) : P.nA;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    A64 a_own;  // float64 basis for band rechecks of float32-path sources
+    int a_own_for = -1;
+    uint32_t n_cand = 0, n_re = 0, n_flip = 0, n_mem = 0;
+    int64_t chunk = (int64_t)blockIdx.x * kScanWarps + warp;
+    // persistent mode: warps take 32-source chunks from the queue until it
+    // runs dry; otherwise each warp does one chunk
+    for (;;) {
+    if (P.queue) {
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(P.queue, 1u);
+        chunk = __shfl_sync(0xffffffffu, c, 0);
+    }
+    const int64_t first = chunk * 32;
+    if (first >= n_units) break;  // whole warp
+    const int nloc = (int)min((int64_t)32, n_units - first);
+    a_own_for = -1;
 
     // ---- per-source setup (lane = source)
     int64_t s_me = -1;
@@ -433,10 +467,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
     const int total_items = __shfl_sync(0xffffffffu, incl, 31);
     if (lane == 31) W.ipref[32] = total_items;
     __syncwarp();
-
-    A64 a_own;  // float64 basis for band rechecks of float32-path sources
-    int a_own_for = -1;
-    uint32_t n_cand = 0, n_re = 0, n_flip = 0, n_mem = 0;
 
     for (int t0 = 0; t0 < total_items; t0 += kItemCap) {
         const int nb = min(kItemCap, total_items - t0);
@@ -518,7 +548,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
                 bool maybe = true, band = false, in32 = false;
                 if (PREC == kPrecFP32) {
                     // q <= 1 - g: inside; q > 1 + g: outside; between: float64
-                    const float q = q32(A, shape, W.it_t[k], b, &x, &y);
+                    const float q = q32(A, A.shape, W.it_t[k], b, &x, &y);
                     const float g = W.g[al];
                     maybe = q <= 1.0f + g;
                     if (maybe) {
@@ -541,7 +571,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
                     }
                     double px, py, pz, rho;
                     load_p64(G, b.row, &px, &py, &pz);
-                    const bool in = test64(*a64, shape, px, py, pz, &rho);
+                    const bool in = test64(*a64, A.shape, px, py, pz, &rho);
                     n_flip += band && in != in32;
                     is_mem = in;
                     exact = rho * kRadToArcsec;
@@ -623,9 +653,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
                         }
                     }
                 } else if (MODE == kModeEmit) {
-                    if (idx < W.cap[al]) {
+                    if (idx < W.cap[al] && P.pair_off[A.row] + idx < P.out_cap) {
                         const int64_t o = P.pair_off[A.row] + idx;
-                        P.out_a[o] = A.row;
+                        P.out_a[o] = P.lrow ? P.lrow[A.row] : A.row;
                         P.out_b[o] = brow;
                         P.out_sep[o] = rep32 ? (double)__int_as_float((int)rep) * kRadToArcsec
                                              : __longlong_as_double(rep);
@@ -679,23 +709,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
             // the count pass reports it, so the pair list and best row agree
             P.best_b[A.row] = W.b1[lane];
             P.best_sep[A.row] = best_sep;
+            atomicAdd(&P.stats[4], 1ull);
         }
     }
+    __syncwarp();
+    if (!P.queue) break;
+    }  // chunks
     if (MODE == kModeCount) {
         warp_add(&P.stats[0], n_cand);
         warp_add(&P.stats[1], n_re);
         warp_add(&P.stats[2], n_flip);
         warp_add(&P.stats[3], n_mem);
-    } else if (MODE == kModeResolve) {
-        warp_add(&P.stats[4], (uint32_t)(lane < nloc));
     }
 }
 
 constexpr size_t kScanSmem = sizeof(ScanWarpSmem) * kScanWarps;
 
 // Pair records from the arena to their canonical slots: row a_row, member k.
+// In a batch, a_row is batch-wide and lrow maps it to the request's row.
 __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long long* n_rec,
                         long long cap, const int64_t* __restrict__ pair_off,
+                        const int32_t* __restrict__ lrow, long long out_cap,
                         int64_t* __restrict__ out_a, int64_t* __restrict__ out_b,
                         double* __restrict__ out_sep) {
     const long long n = min((long long)*n_rec, cap);
@@ -703,7 +737,8 @@ __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long
          i += (long long)gridDim.x * blockDim.x) {
         const MemberRec r = arena[i];
         const int64_t o = pair_off[r.a_row] + r.k;
-        out_a[o] = r.a_row;
+        if (o >= out_cap) continue;  // the batch's pair arena is short: rerun
+        out_a[o] = lrow ? lrow[r.a_row] : r.a_row;
         out_b[o] = r.b_row;
         out_sep[o] = r.f32 ? (double)__int_as_float((int)__double_as_longlong(r.sep)) * kRadToArcsec
                            : r.sep;
@@ -712,12 +747,14 @@ __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long
 
 // Members of each A row into ascending B row: up to kSmallSort by one thread.
 __global__ void k_sort_small(const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off,
-                             int64_t nA, int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+                             int64_t nA, long long out_cap, int64_t* __restrict__ out_b,
+                             double* __restrict__ out_sep) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
     const int c = count[i];
     if (c < 2 || c > kSmallSort) return;
     const int64_t o = pair_off[i];
+    if (o + c > out_cap) return;
     int64_t br[kSmallSort];
     double sp[kSmallSort];
 #pragma unroll
@@ -755,7 +792,7 @@ constexpr int kWarpSortWarps = 4;
 
 __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
     const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off, int64_t nA,
-    int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+    long long out_cap, int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
     __shared__ int64_t sb[kWarpSortWarps][kWarpSort];
     __shared__ double ss[kWarpSortWarps][kWarpSort];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -764,6 +801,7 @@ __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
         const int32_t c = count[row];
         if (c <= kSmallSort || c > kWarpSort) continue;  // uniform over the warp
         const int64_t o = pair_off[row];
+        if (o + c > out_cap) continue;
         for (int k = lane; k < c; k += 32) {
             sb[w][k] = out_b[o + k];
             ss[w][k] = out_sep[o + k];
@@ -785,7 +823,7 @@ __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
 // all rows (no list, so no host synchronisation is needed to launch it).
 __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ count,
                                                   const int64_t* __restrict__ pair_off, int64_t nA,
-                                                  int64_t* __restrict__ out_b,
+                                                  long long out_cap, int64_t* __restrict__ out_b,
                                                   double* __restrict__ out_sep) {
     __shared__ int64_t kb[kSegMax];
     __shared__ double ks[kSegMax];
@@ -793,6 +831,7 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ co
         const int32_t c = count[row];
         if (c <= kWarpSort || c > kSegMax) continue;  // uniform over the block
         const int64_t o = pair_off[row];
+        if (o + c > out_cap) continue;
         int np = 1;
         while (np < c) np <<= 1;
         for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -844,6 +883,55 @@ __global__ void k_seg_permute(const uint32_t* __restrict__ vals, int64_t n,
     if (i >= n) return;
     b_out[i] = b_in[vals[i]];
     s_out[i] = s_in[vals[i]];
+}
+
+// Segments of more than kSegMax members (rows listed on the device): radix
+// sort of (B row, position) pairs, then a permutation through a scratch copy.
+// Rare (regions holding thousands of sources); synchronises the stream.
+xm_status sort_long_segments(const int32_t* d_rows, int64_t n_big, xm_result* R, int32_t* err,
+                             cudaStream_t s) {
+    int32_t* h_big = new (std::nothrow) int32_t[n_big];
+    if (!h_big) return set_error(XM_ENOMEM, "host list");
+    cudaError_t e = cudaMemcpyAsync(h_big, d_rows, n_big * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    xm_status r = XM_OK;
+    for (int64_t k = 0; k < n_big && e == cudaSuccess && r == XM_OK; k++) {
+        const int32_t row = h_big[k];
+        int32_t c = 0;
+        int64_t off = 0;
+        e = cudaMemcpyAsync(&c, R->count + row, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&off, R->pair_off + row, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        uint64_t* sk = (uint64_t*)dev_alloc(2 * (size_t)c * sizeof(uint64_t), s);
+        uint32_t* sv = (uint32_t*)dev_alloc(2 * (size_t)c * sizeof(uint32_t), s);
+        int64_t* cb = (int64_t*)dev_alloc((size_t)c * (sizeof(int64_t) + sizeof(double)), s);
+        if (!sk || !sv || !cb) {
+            r = set_error(XM_ENOMEM, "segment sort");
+        } else {
+            double* cs = (double*)(cb + c);
+            launch_begin("k_seg_keys", s);
+            k_seg_keys<<<(unsigned)((c + 255) / 256), 256, 0, s>>>(R->b_row + off, c, sk, sv);
+            e = launch_end("k_seg_keys", s);
+            if (e == cudaSuccess) r = radix_sort_u64(sk, sv, sk + c, sv + c, c, 0, 32, err, s);
+            if (e == cudaSuccess && r == XM_OK)
+                e = cudaMemcpyAsync(cb, R->b_row + off, c * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && r == XM_OK)
+                e = cudaMemcpyAsync(cs, R->sep + off, c * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && r == XM_OK) {
+                launch_begin("k_seg_permute", s);
+                k_seg_permute<<<(unsigned)((c + 255) / 256), 256, 0, s>>>(sv, c, cb, cs, R->b_row + off, R->sep + off);
+                e = launch_end("k_seg_permute", s);
+            }
+        }
+        dev_free(sk, s);
+        dev_free(sv, s);
+        dev_free(cb, s);
+    }
+    delete[] h_big;
+    if (e != cudaSuccess) return cuda_fail(e, "segment sort");
+    return r;
 }
 
 }  // namespace

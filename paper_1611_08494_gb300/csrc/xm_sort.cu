@@ -356,6 +356,14 @@ xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t
     return scan_impl<int64_t>(in, out, n, total, s);
 }
 
+void radix_sort_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(OnesweepSmem));
+    done = true;
+}
+
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
                          int begin_bit, int end_bit, int32_t* err, cudaStream_t s) {
     if (n <= 1 || end_bit <= begin_bit) return XM_OK;
@@ -371,12 +379,8 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     unsigned long long* hist = (unsigned long long*)work;
     uint64_t* status = (uint64_t*)(hist + passes * kRadix);
     unsigned int* counters = (unsigned int*)(status + passes * st_words);
-    static bool attr_done = false;
     const size_t smem = sizeof(OnesweepSmem);
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
-    }
+    radix_sort_prepare();
     xm_status st = XM_OK;
     cudaError_t e = cudaMemsetAsync(work, 0, bytes, s);
     if (e != cudaSuccess) st = cuda_fail(e, "radix sort memset");

@@ -176,3 +176,75 @@ def c3(seed=1003, scale=1.0, special=10_000):
                 region=dict(shape=CIRCLE, a=2.0),
                 truth=dict(a_row=src.astype(np.int64), b_row=inv[:src.size].astype(np.int64),
                            rho_arcsec=rho))
+
+
+JOIN_NAMES = ("and", "or", "all1", "all2", "not1_2", "not2_1", "xor")
+
+
+def c4(seed=1004, n_b=100_000_000, n_req=4096, a_lo=100, a_hi=1_000_000):
+    """Batched jobs: B uniform on the whole sky; n_req requests, each over a
+    spherical cap centred uniformly on the sphere with a diameter log-uniform
+    in [0.1, 10] deg, n_A log-uniform in [a_lo, a_hi]; half of each request's
+    A uniform in the cap, half offset copies (sigma = 0.3 x region size) of B
+    sources drawn with replacement from the cap. Region shape uniform over
+    circle / ellipse / rectangle, size log-uniform 0.5-30 arcsec, axis ratio
+    0.3-1, PA 0-180 deg, fixed or per-source (even odds); selection and join
+    uniform over the 14 (all, best) x 7 join combinations.
+    B rows are generated cell by cell (1-degree declination bands cut into
+    near-square RA cells) so the generator can find the B rows of a cap; the
+    row order is then shuffled."""
+    g = rng(seed)
+    b_lon, b_lat = uniform_box(g, n_b, 0.0, 360.0, -90.0, 90.0)
+    band = np.clip(np.floor(b_lat + 90.0), 0, 179).astype(np.int64)
+    nra = np.maximum(1, np.floor(360.0 * np.cos(np.radians(np.minimum(
+        np.abs(np.arange(180) - 90.0), np.abs(np.arange(180) - 89.0))))).astype(np.int64))
+    cell = band * 512 + np.minimum(np.floor(b_lon / 360.0 * nra[band]).astype(np.int64), nra[band] - 1)
+    order = np.argsort(cell, kind="stable")
+    cell_sorted = cell[order]
+    p_b = _unit(b_lon, b_lat)
+    requests = []
+    for r in range(n_req):
+        c_lon = g.uniform(0.0, 360.0)
+        c_lat = float(np.degrees(np.arcsin(g.uniform(-1.0, 1.0))))
+        rad = 0.5 * float(np.exp(g.uniform(np.log(0.1), np.log(10.0))))
+        n_a = int(np.exp(g.uniform(np.log(a_lo), np.log(a_hi))))
+        shape = int(g.integers(0, 3))
+        size = float(np.exp(g.uniform(np.log(0.5), np.log(30.0))))
+        ratio = float(g.uniform(0.3, 1.0))
+        per_source = bool(g.integers(0, 2))
+        combo = int(g.integers(0, 14))
+        n_half = n_a // 2
+        u_lon, u_lat = cap(g, n_a - n_half, c_lon, c_lat, rad)
+        # B rows inside the cap, from the cells the cap touches
+        lo_band = int(np.clip(np.floor(c_lat - rad + 90.0), 0, 179))
+        hi_band = int(np.clip(np.floor(c_lat + rad + 90.0), 0, 179))
+        idx = []
+        for bd in range(lo_band, hi_band + 1):
+            a0 = np.searchsorted(cell_sorted, bd * 512)
+            a1 = np.searchsorted(cell_sorted, bd * 512 + 512)
+            idx.append(order[a0:a1])
+        idx = np.concatenate(idx) if idx else np.empty(0, np.int64)
+        pc = _unit(np.array([c_lon]), np.array([c_lat]))[:, 0]
+        inside = idx[(pc @ p_b[:, idx]) >= np.cos(np.radians(rad))] if idx.size else idx
+        if inside.size and n_half:
+            pick = inside[g.integers(0, inside.size, n_half)]
+            o_lon, o_lat, _ = gaussian_offsets(g, b_lon[pick], b_lat[pick], 0.3 * size)
+        else:
+            o_lon, o_lat = cap(g, n_half, c_lon, c_lat, rad)
+        a_lon = np.concatenate([u_lon, o_lon])
+        a_lat = np.concatenate([u_lat, o_lat])
+        region = dict(shape=shape)
+        if per_source:
+            a_col = np.exp(g.uniform(np.log(0.5), np.log(30.0), n_a))
+            region.update(a_col=a_col, b_col=a_col * g.uniform(0.3, 1.0, n_a),
+                          pa_col=g.uniform(0.0, 180.0, n_a))
+        else:
+            region.update(a=size, b=size * ratio, pa=float(g.uniform(0.0, 180.0)))
+        requests.append(dict(lon=a_lon, lat=a_lat, region=region,
+                             selection=3, join=JOIN_NAMES[combo % 7],
+                             join_selection=1 if combo < 7 else 2))
+    perm = g.permutation(n_b)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(n_b)
+    return dict(name="c4", b_lon=b_lon[perm], b_lat=b_lat[perm], b_frame=EQ, requests=requests,
+                b_row_of_generated=inv)

@@ -345,3 +345,105 @@ def frame_matrix() -> np.ndarray:
     m = (_f64 * 9)()
     check(xm_frame_matrix(m), "xm_frame_matrix")
     return np.array(m[:]).reshape(3, 3)
+
+
+# ---------------------------------------------------------------- batches
+
+class Request(ctypes.Structure):
+    _fields_ = [("A", Columns), ("region", Region), ("selection", _i32), ("join_type", _i32),
+                ("join_selection", _i32), ("reserved", _i32)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("precision", _i32), ("use_graph", _i32), ("persistent_blocks", _i32),
+                ("reserved", _i32), ("pair_capacity", _i64), ("row_capacity", _i64)]
+
+
+class BatchView(ctypes.Structure):
+    _fields_ = [("n_a", _i64), ("n_pairs", _i64), ("a_row", _p), ("b_row", _p), ("sep_arcsec", _p),
+                ("count", _p), ("best_b_row", _p), ("best_sep_arcsec", _p), ("n_rows", _i64),
+                ("row_a", _p), ("row_b", _p), ("row_sep", _p), ("n_unmatched_a", _i64),
+                ("n_unmatched_b", _i64)]
+
+
+xm_match_batch = _sig("xm_match_batch", _i32, _p, ctypes.POINTER(Request), _i64,
+                      ctypes.POINTER(BatchOpts), _p, ctypes.POINTER(_p))
+xm_batch_free = _sig("xm_batch_free", _i32, _p)
+xm_batch_get = _sig("xm_batch_get", _i32, _p, _i64, ctypes.POINTER(BatchView))
+xm_batch_join = _sig("xm_batch_join", _i32, _p, _i64, _p, ctypes.POINTER(_p))
+xm_batch_info = _sig("xm_batch_info", _i32, _p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                     ctypes.POINTER(_f64))
+
+
+def request(lon, lat, frame=EQ, selection=SEL_ALL | SEL_BEST, join=None, join_selection=SEL_ALL,
+            keep=None, **region_kw):
+    """One xm_request (paper §2.1 region, §2.2 selection and join)."""
+    keep = [] if keep is None else keep
+    cols, keep = columns(lon, lat, frame, keep=keep)
+    reg, keep = region(keep=keep, **region_kw)
+    jt = -1 if join is None else JOINS[join]
+    return Request(cols, reg, int(selection), jt, int(join_selection), 0), keep
+
+
+class Batch:
+    """Many requests against one index in one pass. ``xm_match_batch``."""
+
+    def __init__(self, index: Index, requests, precision=PREC_FP32, use_graph=False,
+                 persistent_blocks=0, pair_capacity=0, row_capacity=0, stream=None):
+        keep = []
+        arr = (Request * max(len(requests), 1))()
+        for k, rq in enumerate(requests):
+            rq = dict(rq)
+            r, keep = request(rq.pop("lon"), rq.pop("lat"), keep=keep, **rq)
+            arr[k] = r
+        opts = BatchOpts(int(precision), int(bool(use_graph)), int(persistent_blocks), 0,
+                         int(pair_capacity), int(row_capacity))
+        h = _p()
+        check(xm_match_batch(index.handle, arr, len(requests), ctypes.byref(opts),
+                             _stream_handle(stream), ctypes.byref(h)), "xm_match_batch")
+        self.handle = h.value
+        self.index = index
+        self.n = len(requests)
+        self._keep = keep
+
+    def info(self):
+        a, p, ms = _i64(), _i64(), _f64()
+        check(xm_batch_info(self.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(ms)),
+              "xm_batch_info")
+        return {"total_a": a.value, "total_pairs": p.value, "device_ms": ms.value}
+
+    def view(self, r: int) -> dict:
+        v = BatchView()
+        check(xm_batch_get(self.handle, r, ctypes.byref(v)), "xm_batch_get")
+        return {
+            "a_row": _tensor(v.a_row, v.n_pairs, "<i8", self),
+            "b_row": _tensor(v.b_row, v.n_pairs, "<i8", self),
+            "sep": _tensor(v.sep_arcsec, v.n_pairs, "<f8", self),
+            "count": _tensor(v.count, v.n_a, "<i4", self),
+            "best_b": _tensor(v.best_b_row, v.n_a if v.best_b_row else 0, "<i8", self),
+            "best_sep": _tensor(v.best_sep_arcsec, v.n_a if v.best_sep_arcsec else 0, "<f8", self),
+            "row_a": _tensor(v.row_a, v.n_rows, "<i8", self),
+            "row_b": _tensor(v.row_b, v.n_rows, "<i8", self),
+            "row_sep": _tensor(v.row_sep, v.n_rows, "<f8", self),
+            "n_unmatched_a": v.n_unmatched_a, "n_unmatched_b": v.n_unmatched_b,
+        }
+
+    def join(self, r: int, stream=None) -> "Rows":
+        h = _p()
+        check(xm_batch_join(self.handle, r, _stream_handle(stream), ctypes.byref(h)),
+              "xm_batch_join")
+        rows = Rows.__new__(Rows)
+        rows.handle = h.value
+        rows.result = self
+        v = RowsView()
+        check(xm_rows_get(rows.handle, ctypes.byref(v)), "xm_rows_get")
+        rows.view = v
+        rows.n = v.n
+        rows.n_unmatched_a, rows.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
+        return rows
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            xm_batch_free(h)
+            self.handle = None
