@@ -342,6 +342,93 @@ XM_API xm_status xm_batch_join(const xm_batch* batch, int64_t request, void* str
 XM_API xm_status xm_batch_info(const xm_batch* batch, int64_t* total_a, int64_t* total_pairs,
                                double* device_ms);
 
+/* ---- tuning (the paper's tunables: partition resolution and parallelism,
+ *      §2.3 and §4, chosen here by timed trials) ---------------------------- */
+
+typedef struct {
+    double zone_heights_arcsec[8]; /* candidate zone heights; n = 0 -> 6, 12, 24, 48 */
+    int32_t n_zone_heights;
+    int32_t blocks_per_sm[4];      /* candidate persistent grids; n = 0 -> 2, 4, 8 */
+    int32_t n_blocks;
+    int32_t repeats;               /* timed repeats per trial, 0 -> 2 (minimum kept) */
+    int32_t reserved;
+} xm_tune_space;
+
+typedef struct {
+    double zone_height_arcsec;  /* best zone height for the index */
+    int32_t persistent_blocks;  /* best blocks per SM for batches */
+    int32_t trials;             /* trials run (0 when the answer came from the cache) */
+    double best_ms;             /* device time of the best trial */
+} xm_tuned;
+
+/* Picks the index zone height and the batch kernel's grid for a catalogue B
+ * and a sample batch of requests by timing every combination of the
+ * candidates (one index build per zone height, `repeats` batch passes per
+ * grid). Answers are cached per (size of B, frame, sample) for the life of
+ * the process. Errors: as xm_build_index and xm_match_batch. */
+XM_API xm_status xm_autotune(const xm_columns* B, const xm_request* sample, int64_t n_sample,
+                             const xm_tune_space* space, int32_t precision, void* stream,
+                             xm_tuned* out);
+
+/* ---- serving: continuous batching of requests against a resident index -- */
+
+typedef struct {
+    int32_t slots;               /* batches in flight at once (0 -> 2) */
+    int32_t max_batch_requests;  /* requests per batch (0 -> 256) */
+    int64_t max_batch_a;         /* A sources per batch (0 -> 2^26) */
+    int64_t mem_budget_bytes;    /* device memory for requests in flight (0 -> 60 % of free) */
+    int32_t precision;           /* xm_precision */
+    int32_t use_graph;           /* run each batch as a CUDA graph */
+    int32_t persistent_blocks;   /* 0 -> 4 */
+    int32_t reserved;
+} xm_serve_opts;
+
+typedef struct {
+    int64_t submitted, completed, failed, refused;
+    int64_t a_sources;            /* A sources of completed requests */
+    int64_t batches;
+    double p50_ms, p99_ms, max_ms;  /* latency submit -> results complete */
+    double busy_s;                /* wall time with at least one batch on the device */
+    int64_t mem_in_use, mem_budget;
+} xm_serve_stats;
+
+typedef struct xm_server xm_server;
+
+/* Opens a server on a built index (which must outlive it). Each slot is a
+ * host thread with its own stream: it takes the requests waiting at the head
+ * of the queue (first come, first served) while they fit the batch limits
+ * and the free part of the memory budget, runs them as one xm_match_batch,
+ * and marks them done; slots work concurrently, so requests that arrive
+ * while others are on the GPU are admitted as soon as a slot and memory
+ * free up and their work overlaps on the device. */
+XM_API xm_status xm_serve_open(const xm_index* index, const xm_serve_opts* opts, xm_server** out);
+
+/* Queues a request; its columns are copied, so the caller may free them on
+ * return. *ticket identifies it. XM_EBUSY when the request alone exceeds the
+ * memory budget (it could never be admitted); XM_EINVAL as xm_match. */
+XM_API xm_status xm_serve_submit(xm_server* server, const xm_request* request, int64_t* ticket);
+
+/* State of a ticket: 0 queued, 1 running, 2 done, 3 failed (the batch's
+ * status is returned by xm_serve_wait). */
+XM_API xm_status xm_serve_poll(xm_server* server, int64_t ticket, int32_t* state);
+
+/* Waits until the ticket is done or failed, at most timeout_ms (< 0: no
+ * limit); XM_ETIMEOUT if it is still pending; the failure status otherwise. */
+XM_API xm_status xm_serve_wait(xm_server* server, int64_t ticket, int32_t timeout_ms);
+
+/* Results of a done ticket (as xm_batch_get), valid until xm_serve_release. */
+XM_API xm_status xm_serve_result(xm_server* server, int64_t ticket, xm_batch_view* view);
+
+/* Frees the ticket's results; a batch's memory returns to the budget when
+ * all its tickets are released. */
+XM_API xm_status xm_serve_release(xm_server* server, int64_t ticket);
+
+XM_API xm_status xm_serve_get_stats(xm_server* server, xm_serve_stats* out);
+
+/* Stops the slots after the batches in flight, fails queued tickets, frees
+ * everything. */
+XM_API xm_status xm_serve_close(xm_server* server);
+
 /* Copies a device array of `bytes` bytes to host memory on `stream` and
  * waits for it (convenience for callers without their own CUDA runtime). */
 XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -263,9 +264,10 @@ xm_status launch_persistent(const char* name, const ScanArgs& a, int blocks, cud
     return XM_OK;
 }
 
-// A non-blocking stream per device for graph capture.
+// A non-blocking stream per device and host thread for graph capture (slots
+// of a server capture concurrently).
 cudaStream_t capture_stream() {
-    static cudaStream_t cs[64] = {};
+    static thread_local cudaStream_t cs[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     if (!cs[dev] && cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking) != cudaSuccess) {
@@ -273,20 +275,6 @@ cudaStream_t capture_stream() {
         return nullptr;
     }
     return cs[dev];
-}
-
-// Shared-memory limits of the scan kernels, set once (outside any capture).
-void prepare_kernels() {
-    static bool done = false;
-    if (done) return;
-    const int sm = (int)kScanSmem;
-    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeResolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    radix_sort_prepare();
-    done = true;
 }
 
 xm_status launch_persistent_any(int prec, int mode, const ScanArgs& a, int blocks, cudaStream_t s) {
@@ -365,7 +353,7 @@ extern "C" xm_status xm_batch_free(xm_batch* X) {
     return XM_OK;
 }
 
-static xm_status check_request(const xm_request& q, int64_t r) {
+xm_status xm::check_request(const xm_request& q, int64_t r) {
     const xm_columns& A = q.A;
     const xm_region& g = q.region;
     if (A.n < 0 || A.n > 2147483647LL || (A.n > 0 && (!A.lon_deg || !A.lat_deg)))

@@ -316,6 +316,9 @@ xm_status exclusive_scan_i32_ws(const int32_t* in, int64_t* out, int64_t n, int6
 // Host-side galactic -> equatorial rotation (row major, v_eq = m v_gal).
 void gal_to_eq(double m[9]);
 
+// Validation of one batch request (xm_batch.cu); names the request on error.
+xm_status check_request(const xm_request& q, int64_t r);
+
 void stats_add(const unsigned long long* host_counters);  // [0..4] as in xm_stats
 // Per-device cumulative counters ([0..4] as in xm_stats) kernels add to.
 unsigned long long* device_stats();

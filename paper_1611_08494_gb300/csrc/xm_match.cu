@@ -30,12 +30,7 @@ int bits_for(int64_t v) {
 
 template <int PREC, int MODE>
 xm_status launch_scan_t(const char* name, const ScanArgs& a, int64_t n_units, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_scan<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kScanSmem);
-        attr = true;
-    }
+    prepare_kernels();
     const int64_t warps = (n_units + 31) / 32;
     const unsigned g = (unsigned)((warps + kScanWarps - 1) / kScanWarps);
     XM_LAUNCH(name, g, kScanThreads, kScanSmem, s, (k_scan<PREC, MODE>), a);

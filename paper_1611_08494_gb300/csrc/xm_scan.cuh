@@ -15,6 +15,7 @@
 
 #include <math.h>
 
+#include <mutex>
 #include <new>
 
 #include "xm_internal.cuh"
@@ -883,6 +884,25 @@ __global__ void k_seg_permute(const uint32_t* __restrict__ vals, int64_t n,
     if (i >= n) return;
     b_out[i] = b_in[vals[i]];
     s_out[i] = s_in[vals[i]];
+}
+
+// Shared-memory limits of this translation unit's scan kernels and of the
+// sort, set once per device (thread-safe; before any capture that scans).
+void prepare_kernels() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    const int sm = (int)kScanSmem;
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeResolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    radix_sort_prepare();
+    done[dev] = true;
 }
 
 // Segments of more than kSegMax members (rows listed on the device): radix

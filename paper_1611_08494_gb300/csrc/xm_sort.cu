@@ -12,6 +12,8 @@
 //      digits), a tile-local reorder in shared memory, then coalesced stores.
 // Prefix sums are reduce-then-scan over tiles of 4096 elements, applied
 // recursively to the tile sums.
+#include <mutex>
+
 #include "xm_internal.cuh"
 
 namespace xm {
@@ -357,11 +359,15 @@ xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t
 }
 
 void radix_sort_prepare() {
-    static bool done = false;
-    if (done) return;
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
     cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(OnesweepSmem));
-    done = true;
+    done[dev] = true;
 }
 
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,

@@ -447,3 +447,163 @@ class Batch:
         if h:
             xm_batch_free(h)
             self.handle = None
+
+
+# ---------------------------------------------------------------- tuning
+
+class TuneSpace(ctypes.Structure):
+    _fields_ = [("zone_heights_arcsec", _f64 * 8), ("n_zone_heights", _i32),
+                ("blocks_per_sm", _i32 * 4), ("n_blocks", _i32), ("repeats", _i32),
+                ("reserved", _i32)]
+
+
+class Tuned(ctypes.Structure):
+    _fields_ = [("zone_height_arcsec", _f64), ("persistent_blocks", _i32), ("trials", _i32),
+                ("best_ms", _f64)]
+
+
+xm_autotune = _sig("xm_autotune", _i32, ctypes.POINTER(Columns), ctypes.POINTER(Request), _i64,
+                   ctypes.POINTER(TuneSpace), _i32, _p, ctypes.POINTER(Tuned))
+
+
+def autotune(b_lon, b_lat, requests, frame=EQ, zone_heights=(), blocks_per_sm=(), repeats=0,
+             precision=PREC_FP32, stream=None) -> dict:
+    """Timed choice of the index zone height and the batch grid. ``xm_autotune``."""
+    keep = []
+    cols, keep = columns(b_lon, b_lat, frame, keep=keep)
+    arr = (Request * max(len(requests), 1))()
+    for k, rq in enumerate(requests):
+        rq = dict(rq)
+        r, keep = request(rq.pop("lon"), rq.pop("lat"), keep=keep, **rq)
+        arr[k] = r
+    sp = TuneSpace()
+    for k, z in enumerate(zone_heights):
+        sp.zone_heights_arcsec[k] = float(z)
+    sp.n_zone_heights = len(zone_heights)
+    for k, g in enumerate(blocks_per_sm):
+        sp.blocks_per_sm[k] = int(g)
+    sp.n_blocks = len(blocks_per_sm)
+    sp.repeats = int(repeats)
+    out = Tuned()
+    check(xm_autotune(ctypes.byref(cols), arr, len(requests), ctypes.byref(sp), int(precision),
+                      _stream_handle(stream), ctypes.byref(out)), "xm_autotune")
+    return {"zone_height_arcsec": out.zone_height_arcsec,
+            "persistent_blocks": out.persistent_blocks, "trials": out.trials,
+            "best_ms": out.best_ms}
+
+
+# ---------------------------------------------------------------- serving
+
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("slots", _i32), ("max_batch_requests", _i32), ("max_batch_a", _i64),
+                ("mem_budget_bytes", _i64), ("precision", _i32), ("use_graph", _i32),
+                ("persistent_blocks", _i32), ("reserved", _i32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("failed", _i64), ("refused", _i64),
+                ("a_sources", _i64), ("batches", _i64), ("p50_ms", _f64), ("p99_ms", _f64),
+                ("max_ms", _f64), ("busy_s", _f64), ("mem_in_use", _i64), ("mem_budget", _i64)]
+
+
+xm_serve_open = _sig("xm_serve_open", _i32, _p, ctypes.POINTER(ServeOpts), ctypes.POINTER(_p))
+xm_serve_submit = _sig("xm_serve_submit", _i32, _p, ctypes.POINTER(Request),
+                       ctypes.POINTER(_i64))
+xm_serve_poll = _sig("xm_serve_poll", _i32, _p, _i64, ctypes.POINTER(_i32))
+xm_serve_wait = _sig("xm_serve_wait", _i32, _p, _i64, _i32)
+xm_serve_result = _sig("xm_serve_result", _i32, _p, _i64, ctypes.POINTER(BatchView))
+xm_serve_release = _sig("xm_serve_release", _i32, _p, _i64)
+xm_serve_get_stats = _sig("xm_serve_get_stats", _i32, _p, ctypes.POINTER(ServeStats))
+xm_serve_close = _sig("xm_serve_close", _i32, _p)
+
+
+class Ticket:
+    """One submitted request. Its result tensors keep it alive; the result is
+    released when the ticket and its tensors are gone (or by ``release``)."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, server: "Server", tid: int):
+        self.server = server
+        self.id = tid
+        self._released = False
+
+    def state(self) -> int:
+        st = _i32()
+        check(xm_serve_poll(self.server.handle, self.id, ctypes.byref(st)), "xm_serve_poll")
+        return st.value
+
+    def wait(self, timeout_ms: int = -1) -> "Ticket":
+        # the wait blocks in C without the GIL (ctypes releases it)
+        check(xm_serve_wait(self.server.handle, self.id, int(timeout_ms)), "xm_serve_wait")
+        return self
+
+    def view(self) -> dict:
+        v = BatchView()
+        check(xm_serve_result(self.server.handle, self.id, ctypes.byref(v)), "xm_serve_result")
+        return {
+            "a_row": _tensor(v.a_row, v.n_pairs, "<i8", self),
+            "b_row": _tensor(v.b_row, v.n_pairs, "<i8", self),
+            "sep": _tensor(v.sep_arcsec, v.n_pairs, "<f8", self),
+            "count": _tensor(v.count, v.n_a, "<i4", self),
+            "best_b": _tensor(v.best_b_row, v.n_a if v.best_b_row else 0, "<i8", self),
+            "best_sep": _tensor(v.best_sep_arcsec, v.n_a if v.best_sep_arcsec else 0, "<f8", self),
+            "row_a": _tensor(v.row_a, v.n_rows, "<i8", self),
+            "row_b": _tensor(v.row_b, v.n_rows, "<i8", self),
+            "row_sep": _tensor(v.row_sep, v.n_rows, "<f8", self),
+            "n_unmatched_a": v.n_unmatched_a, "n_unmatched_b": v.n_unmatched_b,
+        }
+
+    def release(self) -> None:
+        if not self._released and self.server.handle:
+            check(xm_serve_release(self.server.handle, self.id), "xm_serve_release")
+        self._released = True
+
+    def __del__(self):
+        try:
+            if not self._released and self.server.handle and self.state() >= self.DONE:
+                xm_serve_release(self.server.handle, self.id)
+                self._released = True
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of requests against a resident index. ``xm_serve_*``."""
+
+    def __init__(self, index: Index, slots=0, max_batch_requests=0, max_batch_a=0,
+                 mem_budget_bytes=0, precision=PREC_FP32, use_graph=False, persistent_blocks=0):
+        opts = ServeOpts(int(slots), int(max_batch_requests), int(max_batch_a),
+                         int(mem_budget_bytes), int(precision), int(bool(use_graph)),
+                         int(persistent_blocks), 0)
+        h = _p()
+        check(xm_serve_open(index.handle, ctypes.byref(opts), ctypes.byref(h)), "xm_serve_open")
+        self.handle = h.value
+        self.index = index
+
+    def submit(self, lon, lat, **kw) -> Ticket:
+        keep = []
+        r, keep = request(lon, lat, keep=keep, **kw)
+        t = _i64()
+        check(xm_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "xm_serve_submit")
+        return Ticket(self, t.value)
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        check(xm_serve_get_stats(self.handle, ctypes.byref(s)), "xm_serve_get_stats")
+        return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def close(self) -> None:
+        h = getattr(self, "handle", None)
+        if h:
+            self.handle = None
+            xm_serve_close(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()
