@@ -46,7 +46,7 @@ KERNELS_FOR_ROOFLINE = ("k_scan_fp32_count", "k_digit_scatter", "k_scan_fp32_emi
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--zone-height", type=float, default=0.0, help="arcsec; 0 = tuned default")
@@ -105,13 +105,20 @@ def run_reference(args):
     if rank != 0:
         return
     d = workload()
-    cb = cpu_baseline(d, args.cpu_sample)
-    n_s = int(cb["sample"].split()[1])
+    nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    # each step is a bounded sample, sized so the K steps take about a minute
+    dt = oracle_sample(d, 2000, nthreads)
+    per_step_s = 60.0 / max(args.steps, 1)
+    n_s = args.cpu_sample or int(min(d["a_lon"].size, max(200, 2000 * per_step_s / max(dt, 1e-3))))
+    cb = {"kind": "oracle", "cores": nthreads, "unit": UNIT,
+          "sample": f"first {n_s} of {d['a_lon'].size} A sources per step against all "
+                    f"{d['b_lon'].size} B (voxel grid over B, pair tests, best), "
+                    f"{nthreads} threads"}
     times = []
     for _ in range(args.warmup):
-        oracle_sample(d, min(n_s, 2000), cb["cores"])
+        oracle_sample(d, min(n_s, 2000), nthreads)
     for _ in range(args.steps):
-        times.append(oracle_sample(d, n_s, cb["cores"]))
+        times.append(oracle_sample(d, n_s, nthreads))
     tot = sum(times)
     v = n_s * len(times) / tot
     cb = dict(cb, value=v)
@@ -127,7 +134,9 @@ def run_reference(args):
 # --------------------------------------------------------------- GPU arm
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling of the SM clock and throttle reasons. The sampler
+    is started, its first sample awaited, then the timed region runs; only
+    samples taken between mark_start() and mark_end() are summarised."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -136,30 +145,54 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu = gpu
         self.p = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _reader(self):
+        for ln in self.p.stdout:
+            self.lines.append((time.monotonic(), ln))
 
     def __enter__(self):
+        import threading
+
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return self
+        self.th = threading.Thread(target=self._reader, daemon=True)
+        self.th.start()
+        t_end = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < t_end:
+            time.sleep(0.02)
         return self
 
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+
     def __exit__(self, *exc):
-        self.out = ""
         if self.p:
+            time.sleep(0.15)
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.p.kill()
-                self.out, _ = self.p.communicate()
+            self.th.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in (self.out or "").splitlines():
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = (self.t1 if self.t1 is not None else 1e30) + 0.1
+        for t, ln in self.lines:
+            if not (t0 <= t <= t1):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -177,10 +210,39 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash():
+def nvtx_push(name):
+    """Marks the timed region for profilers (ncu --nvtx-include)."""
+    try:
+        import torch
+
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+# Source files each profiled kernel is built from: a DRAM-traffic record from
+# ncu is used only while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_onesweep": ("xm_sort.cu", "xm_internal.cuh"),
+    "k_scan_fp32_count": ("xm_scan.cuh", "xm_internal.cuh"),
+    "k_gather_b": ("xm_index.cu", "xm_internal.cuh"),
+    "k_ingest_b": ("xm_index.cu", "xm_internal.cuh"),
+}
+
+
+def source_hash(kernel):
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1611_08494_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
+    for f in KERNEL_SOURCES.get(kernel, sorted(os.listdir(cs))):
         if f.endswith((".cu", ".cuh")):
             h.update(open(os.path.join(cs, f), "rb").read())
     return h.hexdigest()[:16]
@@ -222,7 +284,7 @@ def run_ours(args):
         return idx, res, rows, out
 
     def timed(prec, fp64_index, steps, warmup, cols=None, reg=None, copy_out=False,
-              profile=False):
+              profile=False, clocks=None):
         for _ in range(warmup):
             step(prec, fp64_index, cols, reg, copy_out)
         torch.cuda.synchronize()
@@ -231,6 +293,9 @@ def run_ours(args):
         xm.reset_stats()
         if profile:
             xm.prof_enable(True)
+        if clocks:
+            clocks.mark_start()
+            nvtx_push("xm_timed")
         ms, bytes_out = [], 0
         for _ in range(steps):
             flush.zero_()  # evict the inputs from L2 between steps
@@ -243,6 +308,9 @@ def run_ours(args):
             if out is not None:
                 bytes_out = sum(t.numel() * t.element_size() for t in out)
         torch.cuda.synchronize()
+        if clocks:
+            nvtx_pop()
+            clocks.mark_end()
         prof = xm.prof_all() if profile else {}
         if profile:
             xm.prof_enable(False)
@@ -254,7 +322,7 @@ def run_ours(args):
     # float32 + float64 recheck (the product path)
     with Clocks(local) as clk:
         ms, st, prof, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup,
-                                           profile=True)
+                                           profile=True, clocks=clk)
     total_ms = sum(ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -278,7 +346,7 @@ def run_ours(args):
     v_e2e = n_a * len(ms_e2e) / (sum(ms_e2e) / 1e3)
 
     # roofline of the dominant kernel
-    roof = roofline(prof, st, args.steps, n_a, n_b, zone_h)
+    roof = roofline(prof, st, args.steps, n_a, n_b, zone_h, total_ms)
 
     if rank != 0:
         return
@@ -299,7 +367,7 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk.summary(),
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in
-                                sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]},
+                                sorted(prof.items(), key=lambda kv: -kv[1][0])[:16]},
         "stats_per_step": {k: v // args.steps for k, v in st.items()},
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peaks.get("_source")},
     }
@@ -340,7 +408,7 @@ def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, zone_h):
     return None
 
 
-def roofline(prof, st, steps, n_a, n_b, zone_h):
+def roofline(prof, st, steps, n_a, n_b, zone_h, total_ms):
     if not prof:
         return None
     peaks = load_peaks()
@@ -349,7 +417,8 @@ def roofline(prof, st, steps, n_a, n_b, zone_h):
     per_launch_ms = tot_ms / launches
     alg = algorithmic_bytes(name, st, steps, launches, n_a, n_b, zone_h)
     out = {"kernel": name, "bound": "hbm", "peak": peak, "unit": "GB/s", "ms_per_launch": per_launch_ms,
-           "share_of_step": tot_ms / steps, "achieved": None, "frac": None, "traffic": None,
+           "launches_per_step": launches / steps, "share_of_step": tot_ms / total_ms,
+           "achieved": None, "frac": None, "traffic": None,
            "peak_source": "of measured" if peaks.get("_source") == "measured" else "of fallback"}
     if alg is None:
         return out
@@ -366,7 +435,7 @@ def traffic_record(kernel):
     if not os.path.exists(p):
         return None
     rec = json.load(open(p)).get(kernel)
-    if not rec or rec.get("source_hash") != source_hash():
+    if not rec or rec.get("source_hash") != source_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 

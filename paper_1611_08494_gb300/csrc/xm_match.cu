@@ -270,12 +270,12 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 if (nA > 0) {
                     XM_LAUNCH("k_sort_small", grid_for(nA), kBlock, 0, s, k_sort_small, R->count,
                               R->pair_off, nA, (long long)np, R->b_row, R->sep);
-                    XM_LAUNCH("k_sort_warp", (unsigned)((nA + 4 * kWarpSortWarps - 1) / (4 * kWarpSortWarps) < 8 * 152
-                                                         ? (nA + 4 * kWarpSortWarps - 1) / (4 * kWarpSortWarps)
-                                                         : 8 * 152),
+                    const int64_t gw = (nA + 32 * kWarpSortWarps - 1) / (32 * kWarpSortWarps);
+                    XM_LAUNCH("k_sort_warp", (unsigned)(gw < 8 * 152 ? gw : 8 * 152),
                               32 * kWarpSortWarps, 0, s, k_sort_warp, R->count, R->pair_off, nA,
                               (long long)np, R->b_row, R->sep);
-                    XM_LAUNCH("k_seg_sort", (unsigned)(nA < 2 * 152 ? nA : 2 * 152), kBlock, 0, s,
+                    const int64_t gs = (nA + 255) / 256;
+                    XM_LAUNCH("k_seg_sort", (unsigned)(gs < 2 * 152 ? gs : 2 * 152), 256, 0, s,
                               k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep);
                 }
                 if (n_big > 0) {

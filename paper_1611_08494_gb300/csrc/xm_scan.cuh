@@ -785,9 +785,11 @@ __global__ void k_sort_small(const int32_t* __restrict__ count, const int64_t* _
 }
 
 // Members of A rows with kSmallSort < count <= kWarpSort into ascending B row,
-// one warp per row, warps striding over all rows: every entry's final place
-// is the number of entries with a smaller B row (all distinct within a row),
-// counted against a copy in shared memory.
+// one warp per row: every entry's final place is the number of entries with a
+// smaller B row (all distinct within a row), counted against a copy in shared
+// memory. Warps stride over the rows 32 at a time: one coalesced load of 32
+// counts and a ballot find the rows of this size class, so rows of other
+// classes cost no dependent load.
 constexpr int kWarpSort = 512;
 constexpr int kWarpSortWarps = 4;
 
@@ -797,73 +799,97 @@ __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
     __shared__ int64_t sb[kWarpSortWarps][kWarpSort];
     __shared__ double ss[kWarpSortWarps][kWarpSort];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * kWarpSortWarps;
-    for (int64_t row = (int64_t)blockIdx.x * kWarpSortWarps + w; row < nA; row += stride) {
-        const int32_t c = count[row];
-        if (c <= kSmallSort || c > kWarpSort) continue;  // uniform over the warp
-        const int64_t o = pair_off[row];
-        if (o + c > out_cap) continue;
-        for (int k = lane; k < c; k += 32) {
-            sb[w][k] = out_b[o + k];
-            ss[w][k] = out_sep[o + k];
+    const int64_t stride = (int64_t)gridDim.x * kWarpSortWarps * 32;
+    for (int64_t base = ((int64_t)blockIdx.x * kWarpSortWarps + w) * 32; base < nA; base += stride) {
+        const int64_t mine = base + lane;
+        const int32_t cm = mine < nA ? count[mine] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, cm > kSmallSort && cm <= kWarpSort);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t row = base + l;
+            const int32_t c = __shfl_sync(0xffffffffu, cm, l);
+            const int64_t o = pair_off[row];
+            if (o + c > out_cap) continue;  // uniform over the warp
+            for (int k = lane; k < c; k += 32) {
+                sb[w][k] = out_b[o + k];
+                ss[w][k] = out_sep[o + k];
+            }
+            __syncwarp();
+            for (int k = lane; k < c; k += 32) {
+                const int64_t key = sb[w][k];
+                int rank = 0;
+                for (int j = 0; j < c; j++) rank += sb[w][j] < key;
+                out_b[o + rank] = key;
+                out_sep[o + rank] = ss[w][k];
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        for (int k = lane; k < c; k += 32) {
-            const int64_t key = sb[w][k];
-            int rank = 0;
-            for (int j = 0; j < c; j++) rank += sb[w][j] < key;
-            out_b[o + rank] = key;
-            out_sep[o + rank] = ss[w][k];
-        }
-        __syncwarp();
     }
 }
 
 // Members of A rows with kWarpSort < count <= kSegMax into ascending B row:
-// a bitonic network in shared memory, one block per row, blocks striding over
-// all rows (no list, so no host synchronisation is needed to launch it).
+// a bitonic network in shared memory, one block per row. Blocks stride over
+// the rows a block's width at a time, each thread checking one count, and sort the rows
+// of this size class found in the chunk (no list, so no host
+// synchronisation is needed to launch it).
 __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ count,
                                                   const int64_t* __restrict__ pair_off, int64_t nA,
                                                   long long out_cap, int64_t* __restrict__ out_b,
                                                   double* __restrict__ out_sep) {
     __shared__ int64_t kb[kSegMax];
     __shared__ double ks[kSegMax];
-    for (int64_t row = blockIdx.x; row < nA; row += gridDim.x) {
-        const int32_t c = count[row];
-        if (c <= kWarpSort || c > kSegMax) continue;  // uniform over the block
-        const int64_t o = pair_off[row];
-        if (o + c > out_cap) continue;
-        int np = 1;
-        while (np < c) np <<= 1;
-        for (int k = threadIdx.x; k < np; k += blockDim.x) {
-            kb[k] = k < c ? out_b[o + k] : INT64_MAX;
-            ks[k] = k < c ? out_sep[o + k] : 0.0;
+    __shared__ int32_t found[256];
+    __shared__ int n_found;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nA;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) n_found = 0;
+        __syncthreads();
+        const int64_t mine = base + threadIdx.x;
+        if (mine < nA) {
+            const int32_t cm = count[mine];
+            if (cm > kWarpSort && cm <= kSegMax) found[atomicAdd(&n_found, 1)] = (int32_t)threadIdx.x;
         }
         __syncthreads();
-        for (int size = 2; size <= np; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int k = threadIdx.x; k < np; k += blockDim.x) {
-                    const int partner = k ^ stride;
-                    if (partner > k) {
-                        const bool up = (k & size) == 0;
-                        if ((kb[k] > kb[partner]) == up) {
-                            const int64_t tb = kb[k];
-                            kb[k] = kb[partner];
-                            kb[partner] = tb;
-                            const double ts = ks[k];
-                            ks[k] = ks[partner];
-                            ks[partner] = ts;
+        const int nf = n_found;
+        for (int f = 0; f < nf; f++) {
+            const int64_t row = base + found[f];
+            const int32_t c = count[row];
+            const int64_t o = pair_off[row];
+            if (o + c > out_cap) continue;  // uniform over the block
+            int np = 1;
+            while (np < c) np <<= 1;
+            for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                kb[k] = k < c ? out_b[o + k] : INT64_MAX;
+                ks[k] = k < c ? out_sep[o + k] : 0.0;
+            }
+            __syncthreads();
+            for (int size = 2; size <= np; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                        const int partner = k ^ stride;
+                        if (partner > k) {
+                            const bool up = (k & size) == 0;
+                            if ((kb[k] > kb[partner]) == up) {
+                                const int64_t tb = kb[k];
+                                kb[k] = kb[partner];
+                                kb[partner] = tb;
+                                const double ts = ks[k];
+                                ks[k] = ks[partner];
+                                ks[partner] = ts;
+                            }
                         }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
             }
+            for (int k = threadIdx.x; k < c; k += blockDim.x) {
+                out_b[o + k] = kb[k];
+                out_sep[o + k] = ks[k];
+            }
+            __syncthreads();
         }
-        for (int k = threadIdx.x; k < c; k += blockDim.x) {
-            out_b[o + k] = kb[k];
-            out_sep[o + k] = ks[k];
-        }
-        __syncthreads();
+        __syncthreads();  // n_found is reset for the next chunk
     }
 }
 
