@@ -392,7 +392,7 @@ def sort_passes(zone_height_arcsec):
 
 
 def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, zone_h):
-    """Bytes the method must move per launch of a kernel (DESIGN.md):
+    """Bytes the method must move per launch of a kernel:
     k_onesweep   per key and pass 8 B key + 4 B row, read and written (B and A
                  sorts, the same number of passes each);
     k_scan_fp32_count  per A 16 B position + 24 B region columns + 16 B best

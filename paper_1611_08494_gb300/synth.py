@@ -1,7 +1,7 @@
 """Seeded synthetic catalogues shaped like the paper's workloads.
 
 The paper's own inputs (Hi-GAL clumps against UKIDSS/GLIMPSE compact
-sources, §3, and "real public data", §4) are not available; these
+sources, §3, and the unnamed public catalogues of §4) are not available; these
 generators stand in for them with the shapes, sizes and density structure of
 the five benchmark workloads. They are the ONE module both the CUDA path and
 the oracle consume, so they hold no cross-match arithmetic: they only draw
