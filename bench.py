@@ -52,6 +52,13 @@ def parse():
     p.add_argument("--zone-height", type=float, default=0.0, help="arcsec; 0 = tuned default")
     p.add_argument("--cpu-sample", type=int, default=0, help="A sources in the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="serving window after a warm-up of 1/6 of it; 0 skips the serving leg")
+    p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    p.add_argument("--serve-b", type=int, default=300_000_000, help="resident B sources")
+    p.add_argument("--serve-pool", type=int, default=256, help="distinct request payloads")
+    p.add_argument("--serve-slots", type=int, default=3)
+    p.add_argument("--c3-scale", type=float, default=1.0, help="0 skips the all-sky C3 leg")
     return p.parse_args()
 
 
@@ -371,9 +378,173 @@ def run_ours(args):
         "stats_per_step": {k: v // args.steps for k, v in st.items()},
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peaks.get("_source")},
     }
+    if world == 1 and args.c3_scale > 0:
+        line["c3"] = c3_leg(args, xm, torch)
+    if world == 1 and args.serve_seconds > 0:
+        line["serving"] = serving_leg(args, xm, torch)
+    elif world > 1:
+        line["serving"] = {"skipped": "the serving leg runs at N = 1 only"}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(d, args.cpu_sample)
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- all-sky C3 leg
+
+def c3_leg(args, xm, torch):
+    """The all-sky circle workload at full size (A = 5e7, B = 2e8 by
+    default): index build, then match with both selections, FP32 + recheck
+    and all-FP64; the scan's count pass against the HBM roofline."""
+    from paper_1611_08494_gb300 import synth_gpu
+
+    d = synth_gpu.c3(scale=args.c3_scale)
+    n_a, n_b = d["a_lon"].numel(), d["b_lon"].numel()
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"c3 all-sky circle r=2 arcsec: A={n_a}, B={n_b}, density 1+9exp(-|b|/10deg), "
+                       "poles and 0/360 seam, int64 ids, galactic", "steps": 3}
+    peak = load_peaks().get("hbm_gbs", 6800.0)
+    for prec, fp64_index, name in ((xm.PREC_FP32, False, "fp32_recheck"), (xm.PREC_FP64, True, "fp64")):
+        t_build, t_match = [], []
+        for k in range(4):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            if k == 3:
+                xm.reset_stats()
+                xm.prof_enable(True)
+                nvtx_push(f"c3_{name}")
+            e0.record(stream)
+            idx = xm.Index(d["b_lon"], d["b_lat"], frame=d["b_frame"], ids=d["b_id"],
+                           zone_height_arcsec=12.0, build_fp64=fp64_index)
+            e1.record(stream)
+            res = xm.Result(idx, d["a_lon"], d["a_lat"], frame=d["a_frame"], precision=prec,
+                            selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
+            e2.record(stream)
+            e2.synchronize()
+            if k == 3:
+                nvtx_pop()
+            if k >= 1:
+                t_build.append(e0.elapsed_time(e1))
+                t_match.append(e1.elapsed_time(e2))
+            pairs = int(res.n_pairs)
+            del res, idx
+        prof = xm.prof_all()
+        xm.prof_enable(False)
+        st = xm.stats()
+        scan = prof.get("k_scan_fp32_count" if prec == xm.PREC_FP32 else "k_scan_fp64_count")
+        entry = {"a_per_s_match": n_a / (statistics.median(t_match) / 1e3),
+                 "a_per_s_step": n_a / ((statistics.median(t_match) + statistics.median(t_build)) / 1e3),
+                 "index_build_ms": statistics.median(t_build), "match_ms": statistics.median(t_match),
+                 "pairs": pairs, "candidates": int(st["candidates"]),
+                 "kernels_ms": {k: round(v[0], 3) for k, v in
+                                sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+        if scan:
+            alg = n_a * (16 + 24 + 16) + st["candidates"] * 12
+            ach = alg / (scan[0] / scan[1] * 1e-3) / 1e9
+            entry["scan_roofline"] = {"kernel": "k_scan count pass", "bound": "hbm",
+                                      "algorithmic_bytes": alg, "ms": scan[0] / scan[1],
+                                      "achieved": ach, "peak": peak, "unit": "GB/s",
+                                      "frac": ach / peak, "peak_source": "of measured"}
+        out[name] = entry
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------- serving leg
+
+def serving_leg(args, xm, torch):
+    """Poisson arrivals against a resident B index through the library's
+    serving loop (continuous batching, admission by free device memory).
+    Requests take their payloads from a pool of pre-generated device
+    requests; latency is submit -> results complete on the device."""
+    import threading
+
+    from paper_1611_08494_gb300 import synth_gpu
+
+    t_setup = time.perf_counter()
+    b = synth_gpu.c5_catalogue(n_b=args.serve_b)
+    pool = synth_gpu.c5_requests(b, n_pool=args.serve_pool)
+    sample = [dict(q, lon=q["lon"], lat=q["lat"], **q["region"]) for q in pool[:6]]
+    for q in sample:
+        q.pop("region")
+    tuned = xm.autotune(b["b_lon"], b["b_lat"], sample, frame=b["b_frame"],
+                        zone_heights=(10.0, 20.0, 40.0), blocks_per_sm=(2, 4))
+    idx = xm.Index(b["b_lon"], b["b_lat"], frame=b["b_frame"], ids=b["b_id"],
+                   zone_height_arcsec=tuned["zone_height_arcsec"])
+    del b
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    setup_s = time.perf_counter() - t_setup
+
+    warm = args.serve_seconds / 6.0
+    times, h = synth_gpu.poisson_arrivals(args.serve_rate, warm + args.serve_seconds)
+    which = h.integers(0, len(pool), len(times))
+    srv = xm.Server(idx, slots=args.serve_slots, precision=xm.PREC_FP32, use_graph=True,
+                    persistent_blocks=tuned["persistent_blocks"])
+    tickets = []
+    done = threading.Event()
+    lock = threading.Lock()
+
+    def complete():
+        k = 0
+        while True:
+            with lock:
+                t = tickets[k] if k < len(tickets) else None
+            if t is None:
+                if done.is_set():
+                    with lock:
+                        if k >= len(tickets):
+                            return
+                    continue
+                time.sleep(0.0005)
+                continue
+            try:
+                t.wait(600_000)
+            except xm.XMError:
+                pass
+            t.release()
+            k += 1
+
+    th = threading.Thread(target=complete, daemon=True)
+    th.start()
+    offered_a = 0
+    t0 = time.perf_counter()
+    reset_done = False
+    for t_arr, w in zip(times, which):
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        if not reset_done and t_arr >= warm:
+            srv.reset_stats()
+            t_win = time.perf_counter()
+            reset_done = True
+        q = pool[w]
+        tk = srv.submit(q["lon"], q["lat"], frame=q["frame"], selection=q["selection"],
+                        join=q["join"], join_selection=q["join_selection"], **q["region"])
+        with lock:
+            tickets.append(tk)
+        if reset_done:
+            offered_a += q["lon"].numel()
+    done.set()
+    th.join()
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    window = t_end - t_win if reset_done else float("nan")
+    out = {"workload": f"c5 serving: B={args.serve_b} resident (C3 latitude profile, galactic, "
+                       f"int64 ids), Poisson {args.serve_rate:g} req/s, n_A log-uniform 1e3-1e7, "
+                       "mixed shapes/joins/frames, admission by free HBM",
+           "window_s": args.serve_seconds, "warmup_s": warm, "requests": int(st["completed"]),
+           "failed": int(st["failed"]), "refused": int(st["refused"]),
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+           "sustained_a_per_s": st["a_sources"] / window,
+           "offered_a_per_s": offered_a / args.serve_seconds,
+           "drain_s": window - args.serve_seconds, "batches": int(st["batches"]),
+           "busy_s": st["busy_s"], "slots": args.serve_slots, "pool": len(pool),
+           "zone_height_arcsec": tuned["zone_height_arcsec"],
+           "persistent_blocks": tuned["persistent_blocks"], "setup_s": setup_s}
+    del pool, idx
+    torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():

@@ -136,11 +136,19 @@ typedef struct {
     int32_t reserved;
 } xm_index_opts;
 
+/* Order in which the scan visits the A sources (results do not depend on it):
+ * by (zone, RA) after a radix sort, which keeps the B records a warp reads
+ * close together, or in input order, which skips the sort and writes the
+ * per-source results and the pair list contiguously. The default is input
+ * order (faster on every workload measured: dense ellipses and all-sky
+ * circles). */
+typedef enum { XM_A_ORDER_DEFAULT = 0, XM_A_ORDER_SORTED = 1, XM_A_ORDER_INPUT = 2 } xm_a_order;
+
 typedef struct {
     int32_t selection; /* XM_SEL_ALL and/or XM_SEL_BEST */
     int32_t precision; /* xm_precision */
     int32_t block;     /* threads per block of the scan kernel, 0 = default */
-    int32_t reserved;
+    int32_t a_order;   /* xm_a_order */
 } xm_match_opts;
 
 typedef struct xm_index xm_index;
@@ -424,6 +432,12 @@ XM_API xm_status xm_serve_result(xm_server* server, int64_t ticket, xm_batch_vie
 XM_API xm_status xm_serve_release(xm_server* server, int64_t ticket);
 
 XM_API xm_status xm_serve_get_stats(xm_server* server, xm_serve_stats* out);
+
+/* Starts a new statistics window: counters and busy time restart from zero
+ * and latencies are kept only for requests submitted from now on (requests
+ * still in flight complete normally). mem_in_use and mem_budget are not
+ * windowed. */
+XM_API xm_status xm_serve_reset_stats(xm_server* server);
 
 /* Stops the slots after the batches in flight, fails queued tickets, frees
  * everything. */

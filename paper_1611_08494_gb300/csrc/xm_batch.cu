@@ -61,7 +61,6 @@ struct BatchConst {
     int64_t total;
     double rot_g2e[9], rot_e2g[9];  // index frame conversions
     int32_t index_frame;
-    double zscale;
     int32_t nz;
 };
 
@@ -103,7 +102,7 @@ __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
         atomicOr(err, kErrSize);
         atomicMin(bad_req, r);
     }
-    const PosKey k = pos_key(lon, lat, C.zscale, C.nz);
+    const PosKey k = pos_key(lon, lat, C.nz);
     keys[g] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
     vals[g] = (uint32_t)g;
 }
@@ -123,7 +122,7 @@ __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
     const double b = R.shape == XM_CIRCLE ? a : (R.b_col ? R.b_col[i] : R.b);
     const double pa = R.pa_col ? R.pa_col[i] : R.pa;
     out[s] = make_aprep(lon, lat, gamma, ok, a, b, pa, R.shape, R.pa_dir, R.size_k, R.pa_zero,
-                        C.zscale, C.nz, (int32_t)g, r);
+                        C.nz, (int32_t)g, r);
     lrow[g] = (int32_t)i;
 }
 
@@ -466,7 +465,6 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
             C.rot_e2g[3 * r2 + c] = m[3 * c + r2];
         }
     C.index_frame = X->frame;
-    C.zscale = X->geom().zscale;
     C.nz = X->nz;
     int32_t* err = (int32_t*)(B.small + 3);
     int32_t* bad_req = err + 1;

@@ -50,7 +50,7 @@ __global__ void k_zone_geom(int32_t nz, ZoneInfo* __restrict__ zones) {
 }
 
 __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restrict__ lat,
-                           int64_t n, double zscale, int32_t nz, float h_f,
+                           int64_t n, int32_t nz, float h_f,
                            const ZoneInfo* __restrict__ zones, uint64_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, BRec* __restrict__ rec_in,
                            double2* __restrict__ pos, double* __restrict__ px,
@@ -64,7 +64,7 @@ __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restr
         la = 0.0;
     }
     lo = lon_mod360(lo);
-    const PosKey k = pos_key(lo, la, zscale, nz);
+    const PosKey k = pos_key(lo, la, nz);
     const uint32_t ra_key = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
     const ZoneInfo& Z = zones[k.z];
     const uint32_t bin = bin_of(ra_key, Z.nbins);
@@ -267,7 +267,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             XM_LAUNCH("k_zone_geom", gz, kBlock, 0, s, k_zone_geom, X->nz, X->zones);
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, G.zscale, X->nz,
+                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz,
                           G.h_f, X->zones, keys, vals, rec_in, X->pos, X->px, X->py, X->pz, err);
                 xm_status r = radix_sort_u64(keys, vals, tk, tv, n, kSortBeginBit,
                                              32 + bits_for(X->nz - 1), err, s);

@@ -34,6 +34,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "xm.h"
 
@@ -84,7 +85,7 @@ struct __align__(16) BRec {
 
 // One A source, prepared in (zone, RA) order.
 struct __align__(16) APrep {
-    double alpha, delta;  // index-frame RA / Dec (rad), for float64 tests
+    double lon, lat;      // index-frame RA / Dec (deg), for float64 tests
     double theta;         // position angle in the index frame (rad)
     double a, b;          // region sizes (rad); circle: a = b = radius
     uint64_t key64;       // fixed-point RA
@@ -108,7 +109,6 @@ struct IndexGeom {
     const uint32_t* lut;    // RA bucket tables of all zones
     int32_t nz;
     double h;        // zone height (rad)
-    double zscale;   // zones per degree of latitude (nz / 180)
     float h_f;       // zone height (rad), float32
 };
 
@@ -136,17 +136,77 @@ struct PosKey {
     float zfrac;     // zone coordinate minus zone centre line, in zones
 };
 
-// The single place positions (degrees, lon already in [0, 360)) become zone
-// and key: every caller uses it, so zone spans and key windows computed from
-// it cover the sources filed under them.
-__device__ __forceinline__ PosKey pos_key(double lon, double lat, double zscale, int32_t nz) {
+// High 64 bits of the 128-bit product (host and device).
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// floor(m * 2^s / 45) for m < 2^53 and s <= 18, exactly, in integer
+// arithmetic (long division in base 2^32); *exact tells whether the quotient
+// had no remainder.
+__host__ __device__ __forceinline__ uint64_t fx_div45(uint64_t m, int s, bool* exact) {
+    if (s < 0) {
+        if (s <= -54) {  // m * 2^s < 1
+            *exact = m == 0;
+            return 0;
+        }
+        const uint64_t t = m >> (-s);
+        const uint64_t q = t / 45u;
+        *exact = (t << (-s)) == m && q * 45u == t;
+        return q;
+    }
+    const uint64_t lo = m << s;
+    const uint64_t hi = s ? (m >> (64 - s)) : 0;  // N = hi * 2^64 + lo < 45 * 2^64
+    const uint64_t t1 = (hi << 32) | (lo >> 32);
+    const uint64_t q1 = t1 / 45u;
+    const uint64_t t0 = ((t1 - q1 * 45u) << 32) | (lo & 0xFFFFFFFFull);
+    const uint64_t q0 = t0 / 45u;
+    *exact = q0 * 45u == t0;
+    return (q1 << 32) + q0;
+}
+
+// Significand and exponent of |x| (x finite): |x| = m * 2^(e - 52).
+__host__ __device__ __forceinline__ void split_double(double x, uint64_t* m, int* e) {
+#ifdef __CUDA_ARCH__
+    uint64_t bits = (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t bits;
+    memcpy(&bits, &x, sizeof(bits));
+#endif
+    bits &= 0x7FFFFFFFFFFFFFFFull;
+    const int eb = (int)(bits >> 52);
+    const uint64_t f = bits & 0xFFFFFFFFFFFFFull;
+    *m = eb ? (f | (1ull << 52)) : f;
+    *e = eb ? eb - 1023 : -1022;
+}
+
+// The single place positions (degrees, lon already in [0, 360), |lat| <= 90)
+// become zone and key: every caller uses it, so zone spans and key windows
+// computed from it cover the sources filed under them. All integer: the RA
+// key is floor(lon / 360 * 2^64) and the latitude key floor((lat + 90) / 180
+// * 2^64) (clamped below 2^64), both exact; the zone is the top part of the
+// latitude key times the zone count and the zone fraction its low part.
+__host__ __device__ __forceinline__ PosKey pos_key(double lon, double lat, int32_t nz) {
     PosKey k;
-    const double t = (lat + 90.0) * zscale;
-    int32_t z = __double2int_rd(t);
-    z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
-    k.z = z;
-    k.zfrac = (float)(t - (double)z) - 0.5f;
-    k.key64 = __double2ull_rd(lon * kKey64PerDeg);
+    uint64_t m;
+    int e;
+    bool exact;
+    // lon * 2^64 / 360 = m * 2^(e + 9) / 45
+    split_double(lon, &m, &e);
+    k.key64 = fx_div45(m, e + 9, &exact);
+    // |lat| * 2^64 / 180 = m * 2^(e + 10) / 45
+    split_double(lat, &m, &e);
+    const uint64_t u = fx_div45(m, e + 10, &exact);
+    const uint64_t half = 1ull << 63;
+    uint64_t lk;
+    if (lat >= 0.0) lk = u >= half ? ~0ull : half + u;
+    else lk = half - (u + (exact ? 0 : 1));
+    k.z = (int32_t)mulhi64(lk, (uint64_t)nz);
+    k.zfrac = (float)((lk * (uint64_t)nz) >> 40) * 5.9604644775390625e-08f - 0.5f;  // 2^-24
     return k;
 }
 
@@ -210,8 +270,8 @@ struct A64 {
 
 __device__ __forceinline__ A64 make_a64(const APrep& A) {
     A64 r;
-    sincos(A.alpha, &r.sa, &r.ca);
-    sincos(A.delta, &r.sd, &r.cd);
+    sincos(A.lon * kDeg, &r.sa, &r.ca);
+    sincos(A.lat * kDeg, &r.sd, &r.cd);
     sincos(A.theta, &r.st, &r.ct);
     r.a = A.a;
     r.b = A.b;
@@ -344,7 +404,7 @@ struct xm_index {
     int64_t lut_n;
     int64_t bytes;
     xm::IndexGeom geom() const {
-        return xm::IndexGeom{rec, pos, px, py, pz, zones, lut, nz, h, nz / 180.0, (float)h};
+        return xm::IndexGeom{rec, pos, px, py, pz, zones, lut, nz, h, (float)h};
     }
 };
 

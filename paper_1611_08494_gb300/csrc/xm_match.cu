@@ -19,6 +19,8 @@ namespace xm {
 namespace {
 
 constexpr int kBlock = 256;
+// Scan order when the caller leaves it to the library.
+constexpr bool kDefaultSortedA = false;
 
 unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -115,6 +117,8 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
         return set_error(XM_EINVAL, "xm_match: bad precision %d", prec);
     if (opts->block != 0 && opts->block != kScanThreads)
         return set_error(XM_EINVAL, "xm_match: block must be 0 or %d", kScanThreads);
+    if (opts->a_order < XM_A_ORDER_DEFAULT || opts->a_order > XM_A_ORDER_INPUT)
+        return set_error(XM_EINVAL, "xm_match: bad a_order %d", opts->a_order);
 
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
@@ -179,22 +183,23 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             I.pa_col = pc;
             I.size_k = region->size_scale * region->size_unit_arcsec * kArcsec;
             I.pa_zero = region->pa_zero_deg;
-            I.zscale = X->geom().zscale;
             I.nz = X->nz;
 
             const bool want_all = (sel & XM_SEL_ALL) != 0;
             // member records: room for 12 per A source on average; sources
             // that overflow it are scanned again in emit mode
             const long long arena_cap = want_all ? 12LL * nA + 65536 : 0;
-            uint64_t* keys = T.get<uint64_t>(2 * nn);
-            uint32_t* vals = T.get<uint32_t>(2 * nn);
+            const bool sorted_a = opts->a_order == XM_A_ORDER_SORTED ||
+                                  (opts->a_order == XM_A_ORDER_DEFAULT && kDefaultSortedA);
+            uint64_t* keys = sorted_a ? T.get<uint64_t>(2 * nn) : nullptr;
+            uint32_t* vals = sorted_a ? T.get<uint32_t>(2 * nn) : nullptr;
             APrep* prep = T.get<APrep>(nn);
             int32_t* lists = T.get<int32_t>(3 * nn);
             int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts
             int64_t* total = T.get<int64_t>(2);
             unsigned long long* stats = device_stats();
             MemberRec* arena = want_all ? T.get<MemberRec>(arena_cap) : nullptr;
-            if (!keys || !vals || !prep || !lists || !small || !total || !stats ||
+            if ((sorted_a && (!keys || !vals)) || !prep || !lists || !small || !total || !stats ||
                 (want_all && !arena))
                 return set_error(XM_ENOMEM, "xm_match: work buffers");
             e = cudaMemsetAsync(small, 0, 8 * sizeof(int32_t), s);
@@ -202,12 +207,15 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             if (e != cudaSuccess) return cuda_fail(e, "memset");
             int32_t* err = small;
             unsigned long long* arena_n = (unsigned long long*)(total + 1);
-            if (nA > 0) {
+            if (nA > 0 && sorted_a) {
                 XM_LAUNCH("k_ingest_a", grid_for(nA), kBlock, 0, s, k_ingest_a, I, keys, vals, err);
                 xm_status r = radix_sort_u64(keys, vals, keys + nn, vals + nn, nA, kSortBeginBit,
                                              32 + bits_for(X->nz - 1), err, s);
                 if (r != XM_OK) return r;
-                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I, vals, prep);
+                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I, vals, prep, err);
+            } else if (nA > 0) {
+                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I,
+                          (const uint32_t*)nullptr, prep, err);
             }
             ScanArgs a{};
             a.G = X->geom();

@@ -42,7 +42,6 @@ struct AIn {
     const double* pa_col;
     double size_k;   // radians per size unit (scale * unit * arcsec)
     double pa_zero;  // degrees
-    double zscale;   // zones per degree of latitude
     int32_t nz;
 };
 
@@ -106,7 +105,7 @@ __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restr
     const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
     const double pa = I.pa_col ? I.pa_col[i] : I.pa;
     if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
-    const PosKey k = pos_key(lon, lat, I.zscale, I.nz);
+    const PosKey k = pos_key(lon, lat, I.nz);
     keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
     vals[i] = (uint32_t)i;
 }
@@ -114,13 +113,13 @@ __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restr
 // The prepared form of one A source (position already in the index frame).
 __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma, bool ok, double a,
                                             double b, double pa, int32_t shape, int32_t pa_dir,
-                                            double size_k, double pa_zero, double zscale,
-                                            int32_t nz, int32_t row, int32_t req) {
+                                            double size_k, double pa_zero, int32_t nz, int32_t row,
+                                            int32_t req) {
     if (!size_ok(a, b, pa)) a = b = pa = 0.0;
     APrep P;
-    P.alpha = lon * kDeg;
-    P.delta = lat * kDeg;
-    const PosKey k = pos_key(lon, lat, zscale, nz);
+    P.lon = lon;
+    P.lat = lat;
+    const PosKey k = pos_key(lon, lat, nz);
     P.key64 = k.key64;
     P.z = k.z;
     P.zfrac = k.zfrac;
@@ -129,18 +128,23 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
     P.req = req;
     P.a = a * size_k;
     P.b = b * size_k;
-    double th = (pa_zero + pa_dir * pa) * kDeg + gamma;
-    th = remainder(th, kTwoPi);
-    P.theta = th;
+    // position angle: reduced to [0, 360) deg in float64 (the only float64
+    // steps here besides the sizes), so the float32 rotation sees a small
+    // argument; gamma turns it from the input frame's north to the index's
+    double td = pa_zero + (pa_dir > 0 ? pa : -pa);
+    td -= 360.0 * floor(td * (1.0 / 360.0));
+    P.theta = td * kDeg + gamma;
     if (P.a <= 0.0 || P.b <= 0.0 || !ok) {
         P.R = 0.0f;
         P.m00 = P.m01 = P.m10 = P.m11 = 0.0f;
     } else {
-        const double R = shape == XM_RECT ? hypot(P.a, P.b) : fmax(P.a, P.b);
-        P.R = (float)(R * (1.0 + 1e-6));
+        const float af = (float)P.a, bf = (float)P.b;
+        // bounding radius with a margin far above the float32 rounding here
+        const float R = shape == XM_RECT ? sqrtf(fmaf(af, af, bf * bf)) : fmaxf(af, bf);
+        P.R = R * (1.0f + 1e-6f);
         float st, ct;
-        sincosf((float)th, &st, &ct);
-        const float ia = (float)(1.0 / P.a), ib = (float)(1.0 / P.b);
+        sincosf((float)td * 0.017453292519943295f + (float)gamma, &st, &ct);
+        const float ia = 1.0f / af, ib = 1.0f / bf;
         P.m00 = st * ia;
         P.m01 = ct * ia;
         P.m10 = ct * ib;
@@ -149,18 +153,25 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
     return P;
 }
 
-__global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out) {
+// Prepared sources in scan order: vals[s] is the A row of position s (the
+// sorted order), or NULL for input order. Invalid positions and sizes set
+// the error bits (the sorted path found them already; setting them twice is
+// harmless).
+__global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out,
+                         int32_t* err) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= I.n) return;
-    const int64_t i = vals[s];
+    const int64_t i = vals ? (int64_t)vals[s] : s;
     double lon, lat, gamma;
     bool ok;
     a_position(I, i, &lon, &lat, &gamma, &ok);
     const double a = I.a_col ? I.a_col[i] : I.a;
     const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
     const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    if (!ok) atomicOr(err, kErrCoord);
+    if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
     out[s] = make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero,
-                        I.zscale, I.nz, (int32_t)i, 0);
+                        I.nz, (int32_t)i, 0);
 }
 
 // One member found by the count pass: A row, its index among that row's

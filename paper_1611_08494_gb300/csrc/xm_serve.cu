@@ -75,6 +75,7 @@ struct xm_server {
     int active = 0;
     Clock::time_point busy_since;
     double busy_s = 0.0;
+    Clock::time_point window_start;  // latencies of requests submitted before are not kept
 };
 
 namespace {
@@ -139,8 +140,9 @@ void slot_loop(xm_server* S, int k) {
                 if (status == XM_OK) {
                     S->completed++;
                     S->a_sources += t->n_a;
-                    S->latency_ms.push_back(
-                        std::chrono::duration<double, std::milli>(t_done - t->t_submit).count());
+                    if (t->t_submit >= S->window_start)
+                        S->latency_ms.push_back(
+                            std::chrono::duration<double, std::milli>(t_done - t->t_submit).count());
                 } else {
                     S->failed++;
                 }
@@ -170,6 +172,7 @@ extern "C" xm_status xm_serve_open(const xm_index* index, const xm_serve_opts* o
     xm_server* S = new (std::nothrow) xm_server();
     if (!S) return set_error(XM_ENOMEM, "xm_serve_open: host allocation");
     S->index = index;
+    S->window_start = Clock::now();
     if (opts) S->opts = *opts;
     xm_serve_opts& o = S->opts;
     if (o.slots <= 0) o.slots = 2;
@@ -358,6 +361,18 @@ extern "C" xm_status xm_serve_get_stats(xm_server* S, xm_serve_stats* out) {
         out->p99_ms = q(0.99);
         out->max_ms = v.back();
     }
+    return XM_OK;
+}
+
+extern "C" xm_status xm_serve_reset_stats(xm_server* S) {
+    if (!S) return set_error(XM_EINVAL, "xm_serve_reset_stats: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    const Clock::time_point now = Clock::now();
+    S->window_start = now;
+    S->submitted = S->completed = S->failed = S->refused = S->a_sources = S->batches = 0;
+    S->latency_ms.clear();
+    S->busy_s = 0.0;
+    if (S->active > 0) S->busy_since = now;
     return XM_OK;
 }
 

@@ -23,6 +23,7 @@ EQ, GAL = 0, 1
 CIRCLE, ELLIPSE, RECT = 0, 1, 2
 SEL_ALL, SEL_BEST = 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
+A_ORDER_DEFAULT, A_ORDER_SORTED, A_ORDER_INPUT = 0, 1, 2
 JOINS = {"and": 0, "or": 1, "all1": 2, "all2": 3, "not1_2": 4, "not2_1": 5, "xor": 6}
 STATUS = {0: "XM_OK", 1: "XM_EINVAL", 2: "XM_ENOMEM", 3: "XM_ECUDA", 4: "XM_ETIMEOUT",
           5: "XM_EOVERFLOW", 6: "XM_EBUSY", 7: "XM_EUNSUPPORTED"}
@@ -52,7 +53,7 @@ class IndexOpts(ctypes.Structure):
 
 
 class MatchOpts(ctypes.Structure):
-    _fields_ = [("selection", _i32), ("precision", _i32), ("block", _i32), ("reserved", _i32)]
+    _fields_ = [("selection", _i32), ("precision", _i32), ("block", _i32), ("a_order", _i32)]
 
 
 class ResultView(ctypes.Structure):
@@ -227,10 +228,10 @@ class Result:
     """Members of every A source. ``xm_match``."""
 
     def __init__(self, index: Index, lon, lat, frame=EQ, selection=SEL_ALL | SEL_BEST,
-                 precision=PREC_FP32, block=0, stream=None, **region_kw):
+                 precision=PREC_FP32, block=0, a_order=A_ORDER_DEFAULT, stream=None, **region_kw):
         cols, keep = columns(lon, lat, frame)
         reg, keep = region(keep=keep, **region_kw)
-        opts = MatchOpts(int(selection), int(precision), int(block), 0)
+        opts = MatchOpts(int(selection), int(precision), int(block), int(a_order))
         h = _p()
         check(xm_match(index.handle, ctypes.byref(cols), ctypes.byref(reg), ctypes.byref(opts),
                        _stream_handle(stream), ctypes.byref(h)), "xm_match")
@@ -515,6 +516,7 @@ xm_serve_result = _sig("xm_serve_result", _i32, _p, _i64, ctypes.POINTER(BatchVi
 xm_serve_release = _sig("xm_serve_release", _i32, _p, _i64)
 xm_serve_get_stats = _sig("xm_serve_get_stats", _i32, _p, ctypes.POINTER(ServeStats))
 xm_serve_close = _sig("xm_serve_close", _i32, _p)
+xm_serve_reset_stats = _sig("xm_serve_reset_stats", _i32, _p)
 
 
 class Ticket:
@@ -592,6 +594,9 @@ class Server:
         s = ServeStats()
         check(xm_serve_get_stats(self.handle, ctypes.byref(s)), "xm_serve_get_stats")
         return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def reset_stats(self) -> None:
+        check(xm_serve_reset_stats(self.handle), "xm_serve_reset_stats")
 
     def close(self) -> None:
         h = getattr(self, "handle", None)

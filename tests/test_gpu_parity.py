@@ -79,13 +79,14 @@ def check_best(res, ref, n_a, subset=None):
         assert np.max(np.abs(got_s[rows][has] - bb["best_sep"][rows][has])) <= SEP_TOL
 
 
-def run(xm, d, prec, zone_height=0.0, fp64_index=True, selection=None, device_input=True):
+def run(xm, d, prec, zone_height=0.0, fp64_index=True, selection=None, device_input=True,
+        a_order=0):
     conv = _cuda if device_input else np.asarray
     idx = xm.Index(conv(d["b_lon"]), conv(d["b_lat"]), frame=d["b_frame"],
                    zone_height_arcsec=zone_height, build_fp64=fp64_index)
     kw = _region_kw(d["region"], device_input)
     res = xm.Result(idx, conv(d["a_lon"]), conv(d["a_lat"]), frame=d["a_frame"],
-                    precision=_prec(xm, prec),
+                    precision=_prec(xm, prec), a_order=a_order,
                     selection=selection or (xm.SEL_ALL | xm.SEL_BEST), **kw)
     return idx, res
 
@@ -158,9 +159,10 @@ def c2_small():
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_c2_small_ellipses_galactic(xm, c2_small, prec):
+@pytest.mark.parametrize("a_order", [1, 2])
+def test_c2_small_ellipses_galactic(xm, c2_small, prec, a_order):
     d, ref = c2_small
-    _, res = run(xm, d, prec)
+    _, res = run(xm, d, prec, a_order=a_order)
     check_pairs(res, ref)
     check_best(res, ref, d["a_lon"].size)
 
@@ -222,9 +224,10 @@ def test_shapes_frames_poles_seam(xm, prec, shape, frames):
     ref = oracle_ref(d)
     assert ref["a_row"].size > 30
     for zone in (5.0, 60.0):
-        _, res = run(xm, d, prec, zone_height=zone)
-        check_pairs(res, ref)
-        check_best(res, ref, d["a_lon"].size)
+        for a_order in (1, 2):
+            _, res = run(xm, d, prec, zone_height=zone, a_order=a_order)
+            check_pairs(res, ref)
+            check_best(res, ref, d["a_lon"].size)
 
 
 def _region_points(lon0, lat0, theta_deg, xy):
@@ -316,8 +319,12 @@ def test_invalid_input_is_einval(xm, bad):
         a_lat = _cuda([-91.0, 0.0])
     else:
         kw = dict(shape=0, a_col=_cuda([1.0, -2.0]))
-    with pytest.raises(xm.XMError, match="EINVAL"):
-        xm.Result(idx, a_lon, a_lat, **kw)
+    for a_order in (1, 2):  # found with and without the A sort
+        with pytest.raises(xm.XMError, match="EINVAL"):
+            xm.Result(idx, a_lon, a_lat, a_order=a_order, **kw)
+    if bad == "nan_a":
+        with pytest.raises(xm.XMError, match="a_order"):
+            xm.Result(idx, good, lat, a_order=3, **dict(shape=0, a=1.0))
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -336,9 +343,10 @@ def test_many_members_overflow_and_long_segments(xm, prec):
     counts = np.bincount(ref["a_row"], minlength=5)
     assert counts[0] > 2048 and 512 < counts[1] <= 2048 and 16 < counts[2] <= 512
     assert 16 < counts[3] <= 512 and counts[4] <= 16
-    _, res = run(xm, d, prec, zone_height=20.0)
-    check_pairs(res, ref)
-    check_best(res, ref, 5)
+    for a_order in (1, 2):
+        _, res = run(xm, d, prec, zone_height=20.0, a_order=a_order)
+        check_pairs(res, ref)
+        check_best(res, ref, 5)
 
 
 # ------------------------------------------------------------------ C3
