@@ -104,10 +104,12 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start,
     ZoneInfo& Z = zones[z];
     Z.start = zone_start[z];
     Z.end = zone_start[z + 1];
-    // RA buckets: a power of two, about one per 4 sources, at most 2^20
+    // RA buckets: a power of two, one to two per source (so a window bound
+    // is one table read and rarely a step of search), at most 2^24 (the
+    // resolution of the stored RA keys)
     const int64_t m = Z.end - Z.start;
     int lg = 0;
-    while (lg < 20 && ((int64_t)1 << lg) * 4 < m) lg++;
+    while (lg < 24 && ((int64_t)1 << lg) < m) lg++;
     Z.lut_shift = 32u - (uint32_t)lg;
     lut_cnt[z] = (1 << lg) + 1;
 }
@@ -248,8 +250,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         err = (int32_t*)dev_alloc(sizeof(int32_t), s);
         lut_cnt = (int32_t*)dev_alloc(X->nz * sizeof(int32_t), s);
         lut_off = (int64_t*)dev_alloc(X->nz * sizeof(int64_t), s);
-        // bucket tables: a zone of m rows has at most max(1, m/2) + 1 entries
-        X->lut_n = n / 2 + 2 * (int64_t)X->nz + 16;
+        // bucket tables: a zone of m rows has at most max(2, 2m) + 1 entries
+        X->lut_n = 2 * n + 3 * (int64_t)X->nz + 16;
         X->lut = (uint32_t*)dev_alloc(X->lut_n * sizeof(uint32_t), s);
         if (!keys || !vals || !rec_in || !err || !lut_cnt || !lut_off || !X->lut) {
             fail(set_error(XM_ENOMEM, "index build buffers"));

@@ -269,20 +269,33 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
     return W;
 }
 
-// First row in [start, end) of a zone whose ra_key >= key, or > key when
-// `upper`; the zone's RA bucket table narrows the range to one bucket.
-__device__ __forceinline__ int64_t zone_bound(const IndexGeom& G, const ZoneInfo& Z, uint32_t key,
-                                              bool upper) {
-    const uint32_t k = (uint32_t)((uint64_t)key >> Z.lut_shift);
-    int64_t lo = Z.start + __ldg(&G.lut[Z.lut_base + k]);
-    int64_t hi = Z.start + __ldg(&G.lut[Z.lut_base + k + 1]);
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        const uint32_t v = __ldg(&G.rec[mid].ra_key);
-        if (upper ? v <= key : v < key) lo = mid + 1;
-        else hi = mid;
+// Rows [lo, hi) of a zone whose ra_key lies in [klo, khi]: the zone's RA
+// bucket table narrows each bound to one bucket (about one source), and the
+// two searches run in step so their loads overlap.
+__device__ __forceinline__ void zone_bounds(const IndexGeom& G, const ZoneInfo& Z, uint32_t klo,
+                                            uint32_t khi, int64_t* lo_out, int64_t* hi_out) {
+    const uint32_t* L = G.lut + Z.lut_base;
+    // (a 64-bit shift: an empty table has lut_shift 32)
+    const uint32_t bl = (uint32_t)((uint64_t)klo >> Z.lut_shift);
+    const uint32_t bh = (uint32_t)((uint64_t)khi >> Z.lut_shift);
+    int64_t lo0 = Z.start + __ldg(&L[bl]), lo1 = Z.start + __ldg(&L[bl + 1]);
+    int64_t hi0 = Z.start + __ldg(&L[bh]), hi1 = Z.start + __ldg(&L[bh + 1]);
+    // first row with key >= klo in [lo0, lo1]; first row with key > khi in [hi0, hi1]
+    while (lo0 < lo1 || hi0 < hi1) {
+        const int64_t ml = lo0 + ((lo1 - lo0) >> 1), mh = hi0 + ((hi1 - hi0) >> 1);
+        const uint32_t vl = lo0 < lo1 ? __ldg(&G.rec[ml].ra_key) : 0u;
+        const uint32_t vh = hi0 < hi1 ? __ldg(&G.rec[mh].ra_key) : 0u;
+        if (lo0 < lo1) {
+            if (vl < klo) lo0 = ml + 1;
+            else lo1 = ml;
+        }
+        if (hi0 < hi1) {
+            if (vh <= khi) hi0 = mh + 1;
+            else hi1 = mh;
+        }
     }
-    return lo;
+    *lo_out = lo0;
+    *hi_out = hi0 < lo0 ? lo0 : hi0;
 }
 
 // Float64 unit vector of B row `row` (exact positions are kept by row).
@@ -494,11 +507,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
             const int z = W.z0[al] + r / ns, sg = r % ns;
             const ZoneInfo& Z = G.zones[z];
             int64_t lo = Z.start, hi = Z.start;
-            if (Z.end > Z.start) {
-                lo = zone_bound(G, Z, W.wlo[al][sg], false);
-                hi = zone_bound(G, Z, W.whi[al][sg], true);
-                if (hi < lo) hi = lo;
-            }
+            if (Z.end > Z.start) zone_bounds(G, Z, W.wlo[al][sg], W.whi[al][sg], &lo, &hi);
             W.it_a[k] = al;
             W.it_lo[k] = lo;
             W.it_start[k] = (int32_t)(hi - lo);  // count, scanned below
