@@ -114,9 +114,12 @@ struct IndexGeom {
 
 // ------------------------------------------------------ fixed-point position
 
-// Longitude (deg) reduced to [0, 360); the in-range case costs two compares.
+// Longitude (deg) reduced to [0, 360); the in-range case is decided on the
+// bit pattern (0 <= lon < 360 as an integer compare; -0 counts as 0).
 __host__ __device__ inline double lon_mod360(double lon) {
-    if (lon >= 0.0 && lon < 360.0) return lon;
+    uint64_t u;
+    memcpy(&u, &lon, sizeof(u));
+    if (u < 0x4076800000000000ull || u == 0x8000000000000000ull) return lon;  // bits of 360.0
     double l = lon - 360.0 * floor(lon * (1.0 / 360.0));
     if (l >= 360.0) l -= 360.0;
     if (l < 0.0) l += 360.0;
@@ -203,7 +206,9 @@ __host__ __device__ __forceinline__ PosKey pos_key(double lon, double lat, int32
     const uint64_t u = fx_div45(m, e + 10, &exact);
     const uint64_t half = 1ull << 63;
     uint64_t lk;
-    if (lat >= 0.0) lk = u >= half ? ~0ull : half + u;
+    uint64_t lat_bits;
+    memcpy(&lat_bits, &lat, sizeof(lat_bits));
+    if ((lat_bits >> 63) == 0) lk = u >= half ? ~0ull : half + u;
     else lk = half - (u + (exact ? 0 : 1));
     k.z = (int32_t)mulhi64(lk, (uint64_t)nz);
     k.zfrac = (float)((lk * (uint64_t)nz) >> 40) * 5.9604644775390625e-08f - 0.5f;  // 2^-24

@@ -89,8 +89,20 @@ __device__ __forceinline__ void a_position(const AIn& I, int64_t i, double* lon_
     a_position_of(I.lon[i], I.lat[i], I.rotate, I.rot, lon_o, lat_o, gamma, ok);
 }
 
+// Finite and not negative (-0 counts as 0), and finite, decided on the bit
+// patterns (no float64 instruction).
+__device__ __forceinline__ bool nonneg_finite(double x) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    return (u & 0x7FFFFFFFFFFFFFFFull) < 0x7FF0000000000000ull &&
+           ((u >> 63) == 0 || (u << 1) == 0);
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) < 0x7FF0000000000000ull;
+}
+
 __device__ __forceinline__ bool size_ok(double a, double b, double pa) {
-    return isfinite(a) && isfinite(b) && isfinite(pa) && a >= 0.0 && b >= 0.0;
+    return nonneg_finite(a) && nonneg_finite(b) && finite_bits(pa);
 }
 
 __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
@@ -108,6 +120,11 @@ __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restr
     const PosKey k = pos_key(lon, lat, I.nz);
     keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
     vals[i] = (uint32_t)i;
+}
+
+// gamma as float32 (zero, and no conversion, when the frames agree).
+__device__ __forceinline__ float gamma_f(double gamma) {
+    return ((uint64_t)__double_as_longlong(gamma) << 1) == 0 ? 0.0f : (float)gamma;
 }
 
 // The prepared form of one A source (position already in the index frame).
@@ -128,22 +145,29 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
     P.req = req;
     P.a = a * size_k;
     P.b = b * size_k;
-    // position angle: reduced to [0, 360) deg in float64 (the only float64
-    // steps here besides the sizes), so the float32 rotation sees a small
-    // argument; gamma turns it from the input frame's north to the index's
-    double td = pa_zero + (pa_dir > 0 ? pa : -pa);
-    td -= 360.0 * floor(td * (1.0 / 360.0));
-    P.theta = td * kDeg + gamma;
-    if (P.a <= 0.0 || P.b <= 0.0 || !ok) {
+    // position angle east of north of the input frame, in degrees; gamma
+    // turns it to the index frame's north. The float64 angle (for rechecks)
+    // is one fused step; the float32 one is reduced to [0, 360) first so the
+    // float32 rotation sees a small argument (in float64 only when large).
+    double raw = pa_zero + (pa_dir > 0 ? pa : -pa);
+    P.theta = fma(raw, kDeg, gamma);
+    float af = (float)P.a, bf = (float)P.b;
+    if (!ok || !(af > 0.0f || P.a > 0.0) || !(bf > 0.0f || P.b > 0.0)) {
         P.R = 0.0f;
         P.m00 = P.m01 = P.m10 = P.m11 = 0.0f;
     } else {
-        const float af = (float)P.a, bf = (float)P.b;
+        // sizes below the float32 range stay regions (the float64 recheck
+        // decides every candidate of so small a region)
+        af = fmaxf(af, 1.17549435e-38f);
+        bf = fmaxf(bf, 1.17549435e-38f);
         // bounding radius with a margin far above the float32 rounding here
         const float R = shape == XM_RECT ? sqrtf(fmaf(af, af, bf * bf)) : fmaxf(af, bf);
         P.R = R * (1.0f + 1e-6f);
+        if (!(fabs(raw) < 720.0)) raw -= 360.0 * floor(raw * (1.0 / 360.0));
+        float tf = (float)raw;
+        tf -= 360.0f * floorf(tf * (1.0f / 360.0f));
         float st, ct;
-        sincosf((float)td * 0.017453292519943295f + (float)gamma, &st, &ct);
+        sincosf(fmaf(tf, 0.017453292519943295f, gamma_f(gamma)), &st, &ct);
         const float ia = 1.0f / af, ib = 1.0f / bf;
         P.m00 = st * ia;
         P.m01 = ct * ia;
