@@ -62,6 +62,23 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(local_ms, world, device):
+    """The slowest rank's time (every rank gets it): the job's time."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def weak_scaling_value(units_per_rank, steps, world, job_ms):
+    """Whole-job throughput: every rank processed its own units each step."""
+    return world * units_per_rank * steps / (job_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -69,10 +86,12 @@ def dist_env():
     return rank, world, local
 
 
-def workload(seed_offset=0):
+def workload(seed_offset=0, scale=1.0):
+    """The C2 workload of one rank: ranks draw different catalogues of the
+    same shape (seed 1002 + rank)."""
     from paper_1611_08494_gb300 import synth
 
-    d = synth.c2(seed=1002 + seed_offset)
+    d = synth.c2(seed=1002 + seed_offset, scale=scale)
     d["desc"] = ("c2 clump-vs-compact-source: A=200000 per-source ellipses (a 5-60 arcsec "
                  "log-uniform, b/a 0.3-1, PA 0-180), B=5000000, galactic l 0-60 |b|<=1 "
                  "density exp(-|b|/0.3deg)")
@@ -330,12 +349,8 @@ def run_ours(args):
     with Clocks(local) as clk:
         ms, st, prof, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup,
                                            profile=True, clocks=clk)
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * n_a * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), world, "cuda")
+    value = weak_scaling_value(n_a, args.steps, world, total_ms)
     launches = st["kernel_launches"]
 
     # all-float64 path
