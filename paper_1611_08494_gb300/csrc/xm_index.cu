@@ -10,9 +10,10 @@
 //                 frame, RA key, row), sort key; exact position kept by row
 //   radix sort    (xm_sort.cu)
 //   k_zone_start  first sorted source of each zone (binary search)
-//   k_zone_rows   rows of each zone, size of its RA bucket table (about one
-//                 bucket per 4 sources); prefix sum; k_zone_lut the offsets
+//   k_zone_rows   rows of each zone, size of its RA bucket table (one to two
+//                 buckets per source); prefix sum; k_zone_lut the offsets
 //   k_gather_b    records into (zone, RA) order, and the bucket tables
+//   k_gap_fill    the long runs of the bucket tables
 #include <math.h>
 #include <string.h>
 
@@ -130,26 +131,61 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t key, uint32_t shift) {
     return (uint32_t)((uint64_t)(uint32_t)key >> shift);
 }
 
+// A run of bucket-table entries that take one value, too long for the
+// thread that found it (filled by k_gap_fill).
+struct LutGap {
+    int64_t first;   // index into the table array
+    uint32_t count;  // entries
+    uint32_t value;  // row (relative to the zone)
+};
+
+constexpr uint32_t kGapInline = 32;  // longest run written by the finding thread
+
 // Records into index order, and each zone's RA bucket table: bucket k holds
-// the first row (relative to the zone) whose key reaches it.
+// the first row (relative to the zone) whose key reaches it. The first row of
+// each run of equal buckets writes the entries from just after the previous
+// row's bucket up to its own; the zone's last row also writes the entries
+// after its bucket (the value: the zone's row count). Runs longer than
+// kGapInline go to a list for k_gap_fill.
 __global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                            int64_t n, const BRec* __restrict__ rec_in,
                            const ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut,
-                           BRec* __restrict__ rec) {
+                           BRec* __restrict__ rec, LutGap* __restrict__ gaps,
+                           unsigned long long* __restrict__ n_gaps, long long gap_cap,
+                           int32_t* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     rec[i] = rec_in[vals[i]];
     const uint64_t key = keys[i];
     const ZoneInfo& Z = zones[key >> 32];
-    const int64_t start = Z.start, rows = Z.end - Z.start, rel = i - start;
+    const int64_t rows = Z.end - Z.start, rel = i - Z.start;
     const uint32_t shift = Z.lut_shift;
-    const uint32_t b = bucket_of(key, shift);
-    const int64_t prev = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], shift);
-    uint32_t* L = lut + Z.lut_base;
-    for (int64_t k = prev + 1; k <= b; k++) L[k] = (uint32_t)rel;
+    const int64_t b = bucket_of(key, shift);
+    const int64_t pb = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], shift);
+    auto run = [&](int64_t first, int64_t count, uint32_t value) {
+        if (count <= 0) return;
+        if (count <= kGapInline) {
+            for (int64_t k = 0; k < count; k++) lut[Z.lut_base + first + k] = value;
+        } else {
+            const unsigned long long g = atomicAdd(n_gaps, 1ull);
+            if ((long long)g < gap_cap) gaps[g] = LutGap{Z.lut_base + first, (uint32_t)count, value};
+            else atomicOr(err, kErrOverflow);
+        }
+    };
+    run(pb + 1, b - pb, (uint32_t)rel);
     if (rel == rows - 1) {
         const int64_t nb = (int64_t)1 << (32 - shift);
-        for (int64_t k = (int64_t)b + 1; k <= nb; k++) L[k] = (uint32_t)rows;
+        run(b + 1, nb - b, (uint32_t)rows);
+    }
+}
+
+// The long runs of the bucket tables, one block per run.
+__global__ void k_gap_fill(const LutGap* __restrict__ gaps, const unsigned long long* n_gaps,
+                           long long gap_cap, uint32_t* __restrict__ lut) {
+    const long long ng = min((long long)*n_gaps, gap_cap);
+    for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
+        const LutGap G = gaps[g];
+        for (uint32_t k = threadIdx.x; k < G.count; k += blockDim.x) lut[G.first + k] = G.value;
     }
 }
 
@@ -203,6 +239,9 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     int32_t* err = nullptr;
     int32_t* lut_cnt = nullptr;
     int64_t* lut_off = nullptr;
+    LutGap* gaps = nullptr;
+    unsigned long long* n_gaps = nullptr;
+    long long gap_cap = 0;
     int32_t h_err = 0;
 
     auto fail = [&](xm_status code) { st = code; };
@@ -253,7 +292,12 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         // bucket tables: a zone of m rows has at most max(2, 2m) + 1 entries
         X->lut_n = 2 * n + 3 * (int64_t)X->nz + 16;
         X->lut = (uint32_t*)dev_alloc(X->lut_n * sizeof(uint32_t), s);
-        if (!keys || !vals || !rec_in || !err || !lut_cnt || !lut_off || !X->lut) {
+        // runs of more than kGapInline entries: at most one per kGapInline + 1
+        // entries, plus one per zone for its last run
+        gap_cap = X->lut_n / (kGapInline + 1) + 2 * (int64_t)X->nz + 16;
+        gaps = (LutGap*)dev_alloc(gap_cap * sizeof(LutGap) + 16, s);
+        n_gaps = gaps ? (unsigned long long*)(gaps + gap_cap) : nullptr;
+        if (!keys || !vals || !rec_in || !err || !lut_cnt || !lut_off || !X->lut || !gaps) {
             fail(set_error(XM_ENOMEM, "index build buffers"));
             break;
         }
@@ -261,6 +305,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         tk = keys + nn;
         tv = vals + nn;
         e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(n_gaps, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) { fail(cuda_fail(e, "memset")); break; }
 
         auto body = [&]() -> xm_status {
@@ -285,7 +330,9 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
                 XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, keys, vals, n, rec_in,
-                          X->zones, X->lut, X->rec);
+                          X->zones, X->lut, X->rec, gaps, n_gaps, gap_cap, err);
+                XM_LAUNCH("k_gap_fill", 4 * 152, kBlock, 0, s, k_gap_fill, gaps, n_gaps, gap_cap,
+                          X->lut);
             }
             return XM_OK;
         };
@@ -296,6 +343,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         if (e != cudaSuccess) { fail(cuda_fail(e, "xm_build_index sync")); break; }
         if (h_err & kErrCoord) { fail(set_error(XM_EINVAL, "B: NaN/inf or |lat| > 90")); break; }
         if (h_err & kErrTimeout) { fail(set_error(XM_ETIMEOUT, "index sort: look-back timed out")); break; }
+        if (h_err & kErrOverflow) { fail(set_error(XM_ECUDA, "index bucket tables: run list overflow")); break; }
     } while (0);
 
     dev_free(d_lon, s);
@@ -305,6 +353,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     dev_free(err, s);
     dev_free(lut_cnt, s);
     dev_free(lut_off, s);
+    dev_free(gaps, s);
     if (st != XM_OK) {
         xm_index_free(X);
         return st;

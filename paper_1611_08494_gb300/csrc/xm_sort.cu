@@ -3,13 +3,13 @@
 // The sky partition of paper §2.3 assigns every source of the second
 // catalogue to a cell; here the assignment is realised by sorting sources on
 // a (zone, RA) key. The sort is a stable least-significant-digit radix sort
-// with 8-bit digits, one pass per digit, each pass three phases with no
-// inter-block waiting:
-//   1. per tile of 4096 keys, a histogram of the pass's digit;
-//   2. an exclusive scan of the digit-major (digit, tile) counts, giving each
-//      tile the first output slot of each of its digits;
-//   3. per tile, stable local ranks by warp-level match (lanes with equal
-//      digits), a tile-local reorder in shared memory, then coalesced stores.
+// with 8-bit digits: one kernel counts the digits of every pass at once
+// (they do not depend on the order of the keys), then one kernel per pass in
+// the single-kernel Onesweep form: tiles of 4096 keys take ids in launch
+// order, rank their keys stably with warp-level match (lanes with equal
+// digits), publish their per-digit counts, add the counts of earlier tiles by
+// a decoupled look-back (bounded, see kSpinLimit), and scatter through shared
+// memory so stores of one digit are contiguous.
 // Prefix sums are reduce-then-scan over tiles of 4096 elements, applied
 // recursively to the tile sums.
 #include <mutex>
@@ -20,9 +20,9 @@ namespace xm {
 
 namespace {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
 
@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     __syncthreads();
     // per digit (thread d): warp offsets, tile count, look-back
-    {
-        const int d = threadIdx.x;  // kSortThreads == kRadix
+    static_assert(kSortThreads >= kRadix, "one thread per digit");
+    if (threadIdx.x < kRadix) {
+        const int d = threadIdx.x;
         int32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; w++) {
