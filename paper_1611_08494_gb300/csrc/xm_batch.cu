@@ -528,7 +528,7 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
             r = launch_persistent_any(prec, kModeCount, a, pblocks, s);
             if (r != XM_OK) return r;
         }
-        r = exclusive_scan_i32(B.count, B.pair_off, total, B.small + 0, s);
+        r = exclusive_scan_i32(B.count, B.pair_off, total, B.small + 0, err, s);
         if (r != XM_OK) return r;
         if (total > 0) {
             XM_LAUNCH("k_place", 4 * sms, 256, 0, s, k_place, B.arena, arena_n, arena_cap,
@@ -565,7 +565,7 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
                       B.count, B.rows, req_un_a);
         }
         if (want_rows) {
-            r = exclusive_scan_i32(B.rows, B.row_off, total, B.small + 1, s);
+            r = exclusive_scan_i32(B.rows, B.row_off, total, B.small + 1, err, s);
             if (r != XM_OK) return r;
             if (total > 0) {
                 XM_LAUNCH("k_batch_write_a", grid_for(total), kBlock, 0, s, k_batch_write_a, C,
@@ -876,11 +876,26 @@ extern "C" xm_status xm_batch_join(const xm_batch* X, int64_t r, void* stream, x
     view.best_sep = X->B.best_sep + a0;
     // pair offsets relative to the slice
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t* rel = (int64_t*)dev_alloc(std::max<int64_t>(view.n_a, 1) * sizeof(int64_t), s);
+    const int64_t na1 = std::max<int64_t>(view.n_a, 1);
+    int64_t* rel = (int64_t*)dev_alloc((na1 + 1) * sizeof(int64_t), s);
     if (!rel) return set_error(XM_ENOMEM, "xm_batch_join: offsets");
-    xm_status st = exclusive_scan_i32(view.count, rel, view.n_a, nullptr, s);
+    int32_t* err = (int32_t*)(rel + na1);
+    xm_status st = XM_OK;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "xm_batch_join memset");
+    if (st == XM_OK) st = exclusive_scan_i32(view.count, rel, view.n_a, nullptr, err, s);
     view.pair_off = rel;
     if (st == XM_OK) st = xm_join(&view, X->join_sel[r], X->join_type[r], stream, out);
+    if (st == XM_OK) {  // xm_join synchronised the stream: the scan's error bits are final
+        int32_t h_err = 0;
+        e = cudaMemcpy(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "xm_batch_join");
+        else if (h_err & kErrTimeout) st = set_error(XM_ETIMEOUT, "xm_batch_join: scan look-back timed out");
+        if (st != XM_OK) {
+            xm_rows_free(*out);
+            *out = nullptr;
+        }
+    }
     dev_free(rel, s);
     return st;
 }

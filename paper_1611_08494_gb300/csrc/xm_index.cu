@@ -17,7 +17,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "xm_internal.cuh"
 
@@ -189,6 +191,49 @@ __global__ void k_gap_fill(const LutGap* __restrict__ gaps, const unsigned long 
     }
 }
 
+// Zone geometry depends only on the zone count: it is computed once per
+// (device, zone count) into a table kept for the life of the process and
+// copied into each new index.
+struct GeomCache {
+    int device;
+    int32_t nz;
+    ZoneInfo* zones;
+};
+
+xm_status zone_geometry(int32_t nz, ZoneInfo* zones, cudaStream_t s) {
+    static std::mutex mu;
+    static std::vector<GeomCache> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const ZoneInfo* src = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (const GeomCache& c : cache)
+            if (c.device == dev && c.nz == nz) src = c.zones;
+        if (!src && cache.size() < 64) {
+            ZoneInfo* t = nullptr;
+            if (cudaMalloc(&t, (size_t)nz * sizeof(ZoneInfo)) == cudaSuccess) {
+                k_zone_geom<<<(unsigned)((nz + kBlock - 1) / kBlock), kBlock>>>(nz, t);
+                if (cudaDeviceSynchronize() == cudaSuccess) {
+                    cache.push_back(GeomCache{dev, nz, t});
+                    src = t;
+                } else {
+                    cudaFree(t);
+                }
+            }
+            cudaGetLastError();
+        }
+    }
+    if (src) {
+        e = cudaMemcpyAsync(zones, src, (size_t)nz * sizeof(ZoneInfo), cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? XM_OK : cuda_fail(e, "zone geometry copy");
+    }
+    XM_LAUNCH("k_zone_geom", (unsigned)((nz + kBlock - 1) / kBlock), kBlock, 0, s, k_zone_geom, nz,
+              zones);
+    return XM_OK;
+}
+
 int bits_for(int64_t v) {
     int b = 0;
     while (v > 0) { b++; v >>= 1; }
@@ -311,7 +356,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         auto body = [&]() -> xm_status {
             const IndexGeom G = X->geom();
             const unsigned gz = (unsigned)((X->nz + kBlock) / kBlock);
-            XM_LAUNCH("k_zone_geom", gz, kBlock, 0, s, k_zone_geom, X->nz, X->zones);
+            xm_status rg = zone_geometry(X->nz, X->zones, s);
+            if (rg != XM_OK) return rg;
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
                 XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz,
@@ -324,7 +370,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
                       X->zone_start);
             XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, X->zones,
                       lut_cnt);
-            xm_status r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, s);
+            xm_status r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, err, s);
             if (r != XM_OK) return r;
             XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->lut);
             if (n > 0) {

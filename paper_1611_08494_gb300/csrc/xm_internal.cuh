@@ -368,11 +368,14 @@ void radix_sort_prepare();
 // bit 8. Search windows are widened by one such quantum.
 constexpr uint32_t kRaKeyMask = 0xFFFFFF00u;
 constexpr int kSortBeginBit = 8;
-// out[i] = sum of in[0..i) (int64); *total (device) = sum of all.
+// out[i] = sum of in[0..i) (int64); *total (device) = sum of all. One
+// launch (single-pass, decoupled look-back); a look-back that timed out sets
+// kErrTimeout in *err (device), which the caller reads at its next
+// synchronisation.
 xm_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
-                             cudaStream_t s);
+                             int32_t* err, cudaStream_t s);
 xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
-                             cudaStream_t s);
+                             int32_t* err, cudaStream_t s);
 // The same without allocating: ws holds 2 * ceil(n / 4096) int64 values and
 // n is at most 4096 * 4096.
 xm_status exclusive_scan_i32_ws(const int32_t* in, int64_t* out, int64_t n, int64_t* total,

@@ -276,12 +276,12 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
     int64_t* row_off = (int64_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int64_t), s);
     int32_t* wcount = (int32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int32_t), s);
     int64_t* word_off = (int64_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int64_t), s);
-    int64_t* small = (int64_t*)dev_alloc(4 * sizeof(int64_t), s);
+    int64_t* small = (int64_t*)dev_alloc(5 * sizeof(int64_t), s);  // [4]: error bits
     auto body = [&]() -> xm_status {
         if (!bits || !rows || !row_off || !wcount || !word_off || !small)
             return set_error(XM_ENOMEM, "xm_join: work buffers");
         cudaError_t e = cudaMemsetAsync(bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 4 * sizeof(int64_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 5 * sizeof(int64_t), s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
         if (sel_all) {
             if (R->n_pairs > 0)
@@ -293,17 +293,19 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
         if (nA > 0)
             XM_LAUNCH("k_rows_a", grid_for(nA), kBlock, 0, s, k_rows_a, R->count, nA, sel_all,
                       (int)with_pairs, (int)with_un_a, rows, (unsigned long long*)small + 2);
-        xm_status r = exclusive_scan_i32(rows, row_off, nA, small + 0, s);
+        int32_t* err = (int32_t*)(small + 4);
+        xm_status r = exclusive_scan_i32(rows, row_off, nA, small + 0, err, s);
         if (r != XM_OK) return r;
         if (nwords > 0)
             XM_LAUNCH("k_word_unmatched", grid_for(nwords), kBlock, 0, s, k_word_unmatched, bits,
                       nwords, nB, wcount);
-        r = exclusive_scan_i32(wcount, word_off, nwords, small + 1, s);
+        r = exclusive_scan_i32(wcount, word_off, nwords, small + 1, err, s);
         if (r != XM_OK) return r;
-        int64_t h[4];
+        int64_t h[5];
         e = cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "xm_join sync");
+        if ((int32_t)h[4] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_join: scan look-back timed out");
         const int64_t total_a = h[0], un_b = h[1];
         J->n_unmatched_a = h[2];
         J->n_unmatched_b = un_b;

@@ -71,6 +71,44 @@ struct Temps {
     }
 };
 
+// A second stream per host thread and device, with a fork and a join event,
+// for work of a call that can overlap the rest of it (the near-tie resolve
+// runs beside the pair placement and sorts).
+struct Side {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+Side* side_stream() {
+    static thread_local Side sd[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    Side& d = sd[dev];
+    if (!d.st) {
+        if (cudaStreamCreateWithFlags(&d.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            d = Side();
+            return nullptr;
+        }
+    }
+    return &d;
+}
+
+// Makes `s` wait for the side stream's work when it goes out of scope (so
+// temporaries freed on `s` afterwards are no longer read there).
+struct Joiner {
+    cudaStream_t s = nullptr;
+    Side* side = nullptr;
+    ~Joiner() {
+        if (side) {
+            cudaEventRecord(side->join, side->st);
+            cudaStreamWaitEvent(s, side->join, 0);
+        }
+    }
+};
+
 }  // namespace
 }  // namespace xm
 
@@ -237,7 +275,7 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             a.err = err;
             xm_status r = launch_scan_any(prec, a, kModeCount, nA, s);
             if (r != XM_OK) return r;
-            r = exclusive_scan_i32(R->count, R->pair_off, nA, total, s);
+            r = exclusive_scan_i32(R->count, R->pair_off, nA, total, err, s);
             if (r != XM_OK) return r;
             // one synchronisation: total pairs, list lengths, error bits
             int32_t h_small[8];
@@ -254,6 +292,24 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             const int64_t n_ovf = h_small[1], n_tie = h_small[2], n_big = h_small[3];
             R->n_pairs = want_all ? h_total[0] : 0;
 
+            // near ties of the best pair, decided in float64 on the side
+            // stream while the pair list is placed and sorted here
+            Joiner joiner;
+            if ((sel & XM_SEL_BEST) && n_tie > 0 && prec == XM_PREC_FP32_RECHECK) {
+                ScanArgs b = a;
+                b.list = lists + nn;
+                b.nlist = n_tie;
+                Side* side = side_stream();
+                cudaStream_t rs = s;
+                if (side && cudaEventRecord(side->fork, s) == cudaSuccess &&
+                    cudaStreamWaitEvent(side->st, side->fork, 0) == cudaSuccess) {
+                    joiner.s = s;
+                    joiner.side = side;
+                    rs = side->st;
+                }
+                r = launch_scan_any(prec, b, kModeResolve, n_tie, rs);
+                if (r != XM_OK) return r;
+            }
             if (want_all) {
                 const int64_t np = h_total[0] > 0 ? h_total[0] : 1;
                 R->a_row = (int64_t*)dev_alloc(np * (2 * sizeof(int64_t) + sizeof(double)), s);
@@ -291,13 +347,6 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                     r = sort_long_segments(lists + 2 * nn, n_big, R, err, s);
                     if (r != XM_OK) return r;
                 }
-            }
-            if ((sel & XM_SEL_BEST) && n_tie > 0 && prec == XM_PREC_FP32_RECHECK) {
-                ScanArgs b = a;
-                b.list = lists + nn;
-                b.nlist = n_tie;
-                r = launch_scan_any(prec, b, kModeResolve, n_tie, s);
-                if (r != XM_OK) return r;
             }
             if (n_ovf > 0 || n_big > 0) {
                 // the re-scan and the long-segment sorts can report errors

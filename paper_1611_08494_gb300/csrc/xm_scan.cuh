@@ -790,42 +790,48 @@ __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long
     }
 }
 
-// Members of each A row into ascending B row: up to kSmallSort by one thread.
-__global__ void k_sort_small(const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off,
-                             int64_t nA, long long out_cap, int64_t* __restrict__ out_b,
-                             double* __restrict__ out_sep) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nA) return;
-    const int c = count[i];
-    if (c < 2 || c > kSmallSort) return;
-    const int64_t o = pair_off[i];
-    if (o + c > out_cap) return;
-    int64_t br[kSmallSort];
-    double sp[kSmallSort];
+// Members of A rows with 2 <= count <= kSmallSort (16) into ascending B row.
+// Each warp takes 32 consecutive rows and sorts the qualifying ones two at a
+// time, one per half-warp: lane l of the half loads member l (coalesced),
+// counts the members of its row with a smaller B row by shuffles across the
+// half (B rows of a row are distinct), and stores itself at that rank. Launch
+// with 256 threads per block and at least nA / 256 blocks.
+__global__ void __launch_bounds__(256) k_sort_small(const int32_t* __restrict__ count,
+                                                    const int64_t* __restrict__ pair_off,
+                                                    int64_t nA, long long out_cap,
+                                                    int64_t* __restrict__ out_b,
+                                                    double* __restrict__ out_sep) {
+    static_assert(kSmallSort == 16, "one row per half-warp");
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         base < nA; base += warps * 32) {
+        const int64_t mine = base + lane;
+        const int32_t cm = mine < nA ? count[mine] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, cm >= 2 && cm <= kSmallSort);
+        while (todo) {  // uniform over the warp
+            const int r0 = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int r1 = todo ? __ffs(todo) - 1 : -1;
+            if (todo) todo &= todo - 1;
+            const int32_t c0 = __shfl_sync(0xffffffffu, cm, r0);
+            const int32_t c1 = __shfl_sync(0xffffffffu, cm, r1 < 0 ? 0 : r1);
+            const int r = half ? r1 : r0;
+            const int32_t c = r < 0 ? 0 : (half ? c1 : c0);
+            const int64_t o = r < 0 ? 0 : pair_off[base + r];
+            const bool valid = hl < c && o + c <= out_cap;
+            const int64_t kb = valid ? out_b[o + hl] : INT64_MAX;
+            const double ks = valid ? out_sep[o + hl] : 0.0;
+            int rank = 0;
 #pragma unroll
-    for (int k = 0; k < kSmallSort; k++)
-        if (k < c) {
-            br[k] = out_b[o + k];
-            sp[k] = out_sep[o + k];
+            for (int j = 0; j < 16; j++) rank += __shfl_sync(0xffffffffu, kb, (half << 4) | j) < kb;
+            __syncwarp();  // every load of the rows is done before any store
+            if (valid) {
+                out_b[o + rank] = kb;
+                out_sep[o + rank] = ks;
+            }
         }
-    for (int k = 1; k < c; k++) {
-        const int64_t kb = br[k];
-        const double ks = sp[k];
-        int m = k - 1;
-        while (m >= 0 && br[m] > kb) {
-            br[m + 1] = br[m];
-            sp[m + 1] = sp[m];
-            m--;
-        }
-        br[m + 1] = kb;
-        sp[m + 1] = ks;
     }
-#pragma unroll
-    for (int k = 0; k < kSmallSort; k++)
-        if (k < c) {
-            out_b[o + k] = br[k];
-            out_sep[o + k] = sp[k];
-        }
 }
 
 // Members of A rows with kSmallSort < count <= kWarpSort into ascending B row,

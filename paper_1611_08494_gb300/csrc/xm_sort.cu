@@ -290,8 +290,86 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
         *total = (tile_offs ? tile_offs[blockIdx.x] : 0) + all;
 }
 
+// Single-pass exclusive scan: tiles take ids in launch order, scan their
+// 4096 elements in blocked order, publish their sum, and add the sums of
+// earlier tiles by a decoupled look-back (bounded like the sort's; a timeout
+// sets kErrTimeout in *err). The last tile writes the total.
 template <typename T>
-xm_status scan_impl(const T* in, int64_t* out, int64_t n, int64_t* total, cudaStream_t s) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_chained(
+    const T* __restrict__ in, int64_t n, int64_t* __restrict__ out, int64_t* __restrict__ total,
+    uint64_t* status, unsigned int* tile_counter, int32_t* err) {
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    __shared__ int64_t tile_prefix;
+    __shared__ unsigned int tile_s;
+    if (threadIdx.x == 0) tile_s = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const int64_t tile = tile_s;
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const int64_t i = base + k;
+        v[k] = i < n ? (int64_t)in[i] : 0;
+        sum += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int64_t woff = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; w++) {
+        if (w < warp) woff += warp_tot[w];
+        all += warp_tot[w];
+    }
+    if (threadIdx.x == 0) {
+        uint64_t* my = status + tile;
+        int64_t prefix = 0;
+        if (tile == 0) {
+            st_relaxed(my, kStInc | (uint64_t)all);
+        } else {
+            st_relaxed(my, kStAgg | (uint64_t)all);
+            int64_t t = tile - 1;
+            int spins = 0;
+            while (t >= 0) {
+                const uint64_t w = ld_relaxed(status + t);
+                const uint64_t flag = w & ~kStMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                prefix += (int64_t)(w & kStMask);
+                if (flag == kStInc) break;
+                t--;
+            }
+            st_relaxed(my, kStInc | (uint64_t)(prefix + all));
+        }
+        tile_prefix = prefix;
+        if (total && (tile + 1) * kScanTile >= n) *total = prefix + all;
+    }
+    __syncthreads();
+    int64_t run = tile_prefix + woff + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+}
+
+template <typename T>
+xm_status scan_impl(const T* in, int64_t* out, int64_t n, int64_t* total, int32_t* err,
+                    cudaStream_t s) {
     if (n <= 0) {
         if (total) {
             cudaError_t e = cudaMemsetAsync(total, 0, sizeof(int64_t), s);
@@ -304,23 +382,22 @@ xm_status scan_impl(const T* in, int64_t* out, int64_t n, int64_t* total, cudaSt
         XM_LAUNCH("k_tile_scan", 1, kScanThreads, 0, s, k_tile_scan<T>, in, n, nullptr, out, total);
         return XM_OK;
     }
-    int64_t* sums = (int64_t*)dev_alloc(2 * ntiles * sizeof(int64_t), s);
-    if (!sums) return set_error(XM_ENOMEM, "scan: %lld tile sums", (long long)ntiles);
-    int64_t* offs = sums + ntiles;
+    // status words of the tiles and the tile counter
+    const size_t bytes = (size_t)(ntiles + 1) * sizeof(uint64_t);
+    uint64_t* status = (uint64_t*)dev_alloc(bytes, s);
+    if (!status) return set_error(XM_ENOMEM, "scan: %lld tiles", (long long)ntiles);
+    unsigned int* counter = (unsigned int*)(status + ntiles);
     xm_status st = XM_OK;
-    do {
-        launch_begin("k_tile_sums", s);
-        k_tile_sums<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, sums);
-        cudaError_t e = launch_end("k_tile_sums", s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "k_tile_sums"); break; }
-        st = scan_impl<int64_t>(sums, offs, ntiles, nullptr, s);
-        if (st != XM_OK) break;
-        launch_begin("k_tile_scan", s);
-        k_tile_scan<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, offs, out, total);
-        e = launch_end("k_tile_scan", s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "k_tile_scan"); break; }
-    } while (0);
-    dev_free(sums, s);
+    cudaError_t e = cudaMemsetAsync(status, 0, bytes, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "scan memset");
+    if (st == XM_OK) {
+        launch_begin("k_scan_chained", s);
+        k_scan_chained<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, total, status,
+                                                                     counter, err);
+        e = launch_end("k_scan_chained", s);
+        if (e != cudaSuccess) st = cuda_fail(e, "k_scan_chained");
+    }
+    dev_free(status, s);
     return st;
 }
 
@@ -350,13 +427,13 @@ xm_status exclusive_scan_i32_ws(const int32_t* in, int64_t* out, int64_t n, int6
 }
 
 xm_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* total,
-                             cudaStream_t s) {
-    return scan_impl<int32_t>(in, out, n, total, s);
+                             int32_t* err, cudaStream_t s) {
+    return scan_impl<int32_t>(in, out, n, total, err, s);
 }
 
 xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
-                             cudaStream_t s) {
-    return scan_impl<int64_t>(in, out, n, total, s);
+                             int32_t* err, cudaStream_t s) {
+    return scan_impl<int64_t>(in, out, n, total, err, s);
 }
 
 void radix_sort_prepare() {
