@@ -52,6 +52,7 @@ constexpr uint64_t kStAgg = 1ull << 62;   // tile's own count is available
 constexpr uint64_t kStInc = 2ull << 62;   // inclusive prefix is available
 constexpr uint64_t kStMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;      // polls before a look-back gives up
+constexpr int kLookWindow = 8;           // status words loaded per look-back step
 
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
     uint64_t v;
@@ -155,22 +156,33 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             st_relaxed(my, kStInc | (uint64_t)run);
         } else {
             st_relaxed(my, kStAgg | (uint64_t)run);
+            // walk back kLookWindow tiles per step: their words are loaded
+            // together, then taken in order until an inclusive prefix (done)
+            // or a tile that has not published yet (wait there)
             int t = tile - 1;
             int spins = 0;
-            while (t >= 0) {
-                const uint64_t v = ld_relaxed(status + (int64_t)t * kRadix + d);
-                const uint64_t flag = v & ~kStMask;
-                if (flag == 0) {
+            bool done = false;
+            while (t >= 0 && !done) {
+                uint64_t w[kLookWindow];
+#pragma unroll
+                for (int j = 0; j < kLookWindow; j++)
+                    w[j] = t - j >= 0 ? ld_relaxed(status + (int64_t)(t - j) * kRadix + d) : kStInc;
+#pragma unroll
+                for (int j = 0; j < kLookWindow; j++) {
+                    if (done) break;
+                    const uint64_t flag = w[j] & ~kStMask;
+                    if (flag == 0) break;  // not published: reload from here
+                    prefix += (int64_t)(w[j] & kStMask);  // (before tile 0: 0)
+                    if (flag == kStInc) done = true;
+                    else t--;
+                }
+                if (!done && t >= 0 && (w[0] & ~kStMask) == 0) {
                     if (++spins > kSpinLimit) {
                         atomicOr(err, kErrTimeout);
                         break;
                     }
                     __nanosleep(64);
-                    continue;
                 }
-                prefix += (int64_t)(v & kStMask);
-                if (flag == kStInc) break;
-                t--;
             }
             st_relaxed(my, kStInc | (uint64_t)(prefix + run));
         }
