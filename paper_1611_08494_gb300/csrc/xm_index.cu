@@ -101,19 +101,28 @@ __global__ void k_zone_start(const uint64_t* __restrict__ keys, int64_t n, int32
 }
 
 __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start,
-                            ZoneInfo* __restrict__ zones, int32_t* __restrict__ lut_cnt) {
+                            const uint64_t* __restrict__ keys, ZoneInfo* __restrict__ zones,
+                            int32_t* __restrict__ lut_cnt) {
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
     ZoneInfo& Z = zones[z];
     Z.start = zone_start[z];
     Z.end = zone_start[z + 1];
-    // RA buckets: a power of two, one to two per source (so a window bound
-    // is one table read and rarely a step of search), at most 2^24 (the
-    // resolution of the stored RA keys)
+    // RA buckets over the zone's own key range: a power of two, one to two
+    // per source (so a window bound is one table read and rarely a step of
+    // search), at most 2^24 (the resolution of the stored RA keys)
     const int64_t m = Z.end - Z.start;
     int lg = 0;
     while (lg < 24 && ((int64_t)1 << lg) < m) lg++;
-    Z.lut_shift = 32u - (uint32_t)lg;
+    uint32_t kmin = 0, range = 0;
+    if (m > 0) {
+        kmin = (uint32_t)keys[Z.start];
+        range = (uint32_t)keys[Z.end - 1] - kmin;
+    }
+    const int bits = range ? 32 - __clz(range) : 0;  // range >> shift < 2^lg
+    Z.lut_shift = (uint32_t)(bits > lg ? bits - lg : 0);
+    Z.lut_kmin = kmin;
+    Z.lut_nb = 1u << lg;
     lut_cnt[z] = (1 << lg) + 1;
 }
 
@@ -129,8 +138,8 @@ __global__ void k_zone_lut(int32_t nz, const int64_t* __restrict__ lut_off,
     }
 }
 
-__device__ __forceinline__ uint32_t bucket_of(uint64_t key, uint32_t shift) {
-    return (uint32_t)((uint64_t)(uint32_t)key >> shift);
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, const ZoneInfo& Z) {
+    return ((uint32_t)key - Z.lut_kmin) >> Z.lut_shift;
 }
 
 // A run of bucket-table entries that take one value, too long for the
@@ -161,9 +170,8 @@ __global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __
     const uint64_t key = keys[i];
     const ZoneInfo& Z = zones[key >> 32];
     const int64_t rows = Z.end - Z.start, rel = i - Z.start;
-    const uint32_t shift = Z.lut_shift;
-    const int64_t b = bucket_of(key, shift);
-    const int64_t pb = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], shift);
+    const int64_t b = bucket_of(key, Z);
+    const int64_t pb = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], Z);
     auto run = [&](int64_t first, int64_t count, uint32_t value) {
         if (count <= 0) return;
         if (count <= kGapInline) {
@@ -175,10 +183,7 @@ __global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __
         }
     };
     run(pb + 1, b - pb, (uint32_t)rel);
-    if (rel == rows - 1) {
-        const int64_t nb = (int64_t)1 << (32 - shift);
-        run(b + 1, nb - b, (uint32_t)rows);
-    }
+    if (rel == rows - 1) run(b + 1, (int64_t)Z.lut_nb - b, (uint32_t)rows);
 }
 
 // The long runs of the bucket tables, one block per run.
@@ -368,7 +373,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             }
             XM_LAUNCH("k_zone_start", gz, kBlock, 0, s, k_zone_start, keys, n, X->nz,
                       X->zone_start);
-            XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, X->zones,
+            XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, keys,
+                      X->zones,
                       lut_cnt);
             xm_status r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, err, s);
             if (r != XM_OK) return r;

@@ -60,9 +60,11 @@ enum : int32_t {
 };
 
 // One declination zone. Its B sources are rows [start, end) of the index,
-// sorted by ra_key. The RA bucket table lut[lut_base + k], k = ra_key >>
-// lut_shift, holds the first row (relative to start) whose key reaches bucket
-// k, so a window bound is found with two table reads and a short search.
+// sorted by ra_key. The RA bucket table spans the zone's own key range
+// [lut_kmin, last key]: lut[lut_base + k], k = (ra_key - lut_kmin) >>
+// lut_shift (k < lut_nb), holds the first row (relative to start) whose key
+// reaches bucket k, and lut[lut_base + lut_nb] the zone's row count; a window
+// bound is two table reads and a short search.
 struct __align__(16) ZoneInfo {
     double dec_c;          // zone centre latitude (rad)
     double sin_c, cos_c;   // of dec_c, float64
@@ -72,8 +74,9 @@ struct __align__(16) ZoneInfo {
     float sin_cf, cos_cf;  // of dec_c, float32
     float binw_f;          // RA cell width (rad), float32
     uint32_t nbins;        // RA cells
-    uint32_t lut_shift;    // 32 - log2(buckets)
-    uint32_t pad;
+    uint32_t lut_shift;    // key bits per bucket
+    uint32_t lut_kmin;     // smallest ra_key of the zone
+    uint32_t lut_nb;       // buckets (a power of two)
 };
 
 // One B source in index order (16 bytes: one vector load per candidate).
@@ -211,7 +214,7 @@ __host__ __device__ __forceinline__ PosKey pos_key(double lon, double lat, int32
     if ((lat_bits >> 63) == 0) lk = u >= half ? ~0ull : half + u;
     else lk = half - (u + (exact ? 0 : 1));
     k.z = (int32_t)mulhi64(lk, (uint64_t)nz);
-    k.zfrac = (float)((lk * (uint64_t)nz) >> 40) * 5.9604644775390625e-08f - 0.5f;  // 2^-24
+    k.zfrac = (float)(uint32_t)((lk * (uint64_t)nz) >> 40) * 5.9604644775390625e-08f - 0.5f;  // 2^-24
     return k;
 }
 
@@ -225,7 +228,9 @@ __device__ __forceinline__ uint32_t bin_of(uint32_t ra_key, uint32_t nbins) {
 __device__ __forceinline__ float cells_from_centre(uint64_t key64, uint32_t nbins, uint32_t bin) {
     const uint64_t hi = __umul64hi(key64, (uint64_t)nbins);
     const uint64_t lo = key64 * (uint64_t)nbins;
-    const float frac = (float)(lo >> 40) * 5.9604644775390625e-08f;  // 2^-24
+    // (the 24-bit fraction converts through 32 bits: a 64-bit integer
+    // conversion would take the float64 pipe)
+    const float frac = (float)(uint32_t)(lo >> 40) * 5.9604644775390625e-08f;  // 2^-24
     return (float)(int32_t)((uint32_t)hi - bin) + (frac - 0.5f);
 }
 

@@ -264,7 +264,7 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
         const LatTerms L = lat_terms(G.h_f * A.zfrac, Z.sin_cf, Z.cos_cf);
         const float ratio = sinf(Rm) / L.cd;
         if (!(L.cd > 0.0f && ratio < 0.9999f)) full = true;
-        else dk = (int64_t)ceilf(asinf(ratio) * (1.0f + 2e-5f) * kKey32PerRadF) + 2;
+        else dk = (int64_t)(int32_t)ceilf(asinf(ratio) * (1.0f + 2e-5f) * kKey32PerRadF) + 2;  // < 2^30
     }
     // stored B keys are rounded down to a multiple of 256: widen the low end
     const int64_t ka = (int64_t)(A.key64 >> 32);
@@ -295,13 +295,18 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
 
 // Rows [lo, hi) of a zone whose ra_key lies in [klo, khi]: the zone's RA
 // bucket table narrows each bound to one bucket (about one source), and the
-// two searches run in step so their loads overlap.
+// two searches run in step so their loads overlap. Keys outside the zone's
+// key range clamp to its first or last bucket.
 __device__ __forceinline__ void zone_bounds(const IndexGeom& G, const ZoneInfo& Z, uint32_t klo,
                                             uint32_t khi, int64_t* lo_out, int64_t* hi_out) {
     const uint32_t* L = G.lut + Z.lut_base;
-    // (a 64-bit shift: an empty table has lut_shift 32)
-    const uint32_t bl = (uint32_t)((uint64_t)klo >> Z.lut_shift);
-    const uint32_t bh = (uint32_t)((uint64_t)khi >> Z.lut_shift);
+    const uint32_t last = Z.lut_nb - 1;
+    if (khi < Z.lut_kmin) {  // the whole window lies before the zone's first key
+        *lo_out = *hi_out = Z.start;
+        return;
+    }
+    const uint32_t bl = klo <= Z.lut_kmin ? 0u : min((klo - Z.lut_kmin) >> Z.lut_shift, last);
+    const uint32_t bh = min((khi - Z.lut_kmin) >> Z.lut_shift, last);
     int64_t lo0 = Z.start + __ldg(&L[bl]), lo1 = Z.start + __ldg(&L[bl + 1]);
     int64_t hi0 = Z.start + __ldg(&L[bh]), hi1 = Z.start + __ldg(&L[bh + 1]);
     // first row with key >= klo in [lo0, lo1]; first row with key > khi in [hi0, hi1]
@@ -363,7 +368,7 @@ __device__ __forceinline__ ItemTerms item_terms(const APrep& A, const ZoneInfo& 
     t.binw = Z.binw_f;
     t.nbins = Z.nbins;
     t.binA = (uint32_t)__umul64hi(A.key64, (uint64_t)Z.nbins);
-    t.ufrac = (float)((A.key64 * (uint64_t)Z.nbins) >> 40) * 5.9604644775390625e-08f - 0.5f;
+    t.ufrac = (float)(uint32_t)((A.key64 * (uint64_t)Z.nbins) >> 40) * 5.9604644775390625e-08f - 0.5f;
     return t;
 }
 
