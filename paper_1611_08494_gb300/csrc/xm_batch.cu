@@ -62,6 +62,7 @@ struct BatchConst {
     double rot_g2e[9], rot_e2g[9];  // index frame conversions
     int32_t index_frame;
     int32_t nz;
+    float h_f;  // zone height of the index (rad)
 };
 
 __device__ __forceinline__ int32_t find_req(const int64_t* __restrict__ off, int32_t n_req,
@@ -108,7 +109,8 @@ __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
 }
 
 __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
-                             APrep* __restrict__ out, int32_t* __restrict__ lrow) {
+                             APrep* __restrict__ out, ACold* __restrict__ cold,
+                             int32_t* __restrict__ lrow) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= C.total) return;
     const int64_t g = vals[s];
@@ -121,8 +123,8 @@ __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
     const double a = R.a_col ? R.a_col[i] : R.a;
     const double b = R.shape == XM_CIRCLE ? a : (R.b_col ? R.b_col[i] : R.b);
     const double pa = R.pa_col ? R.pa_col[i] : R.pa;
-    out[s] = make_aprep(lon, lat, gamma, ok, a, b, pa, R.shape, R.pa_dir, R.size_k, R.pa_zero,
-                        C.nz, (int32_t)g, r);
+    make_aprep(lon, lat, gamma, ok, a, b, pa, R.shape, R.pa_dir, R.size_k, R.pa_zero, C.nz, C.h_f,
+               (int32_t)g, &out[s], &cold[s]);
     lrow[g] = (int32_t)i;
 }
 
@@ -306,6 +308,7 @@ struct BatchBufs {
     uint64_t* keys = nullptr;
     uint32_t* vals = nullptr;
     APrep* prep = nullptr;
+    ACold* cold = nullptr;
     int32_t* lrow = nullptr;
     int32_t* lists = nullptr;
     MemberRec* arena = nullptr;
@@ -430,6 +433,7 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
     B.keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
     B.vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
     B.prep = (APrep*)dev_alloc(nn * sizeof(APrep), s);
+    B.cold = (ACold*)dev_alloc(nn * sizeof(ACold), s);
     B.lrow = (int32_t*)dev_alloc(nn * sizeof(int32_t), s);
     B.lists = (int32_t*)dev_alloc(3 * nn * sizeof(int32_t), s);
     B.arena = (MemberRec*)dev_alloc(arena_cap * sizeof(MemberRec), s);
@@ -439,14 +443,15 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
     B.small = (int64_t*)dev_alloc((kSmallWords + 2 * n + 1) * sizeof(int64_t), s);
     B.bounds = (int64_t*)dev_alloc((4 * n + 1) * sizeof(int64_t), s);
     auto release_tmp = [&]() {
-        void* p[] = {B.keys, B.vals, B.prep, B.lrow, B.lists, B.arena, B.rows, B.row_off,
+        void* p[] = {B.keys, B.vals, B.prep, B.cold, B.lrow, B.lists, B.arena, B.rows, B.row_off,
                      B.table, B.small, B.bounds};
         for (void* q : p) dev_free(q, s);
-        B.keys = nullptr; B.vals = nullptr; B.prep = nullptr; B.lrow = nullptr; B.lists = nullptr;
+        B.keys = nullptr; B.vals = nullptr; B.prep = nullptr; B.cold = nullptr; B.lrow = nullptr;
+        B.lists = nullptr;
         B.arena = nullptr; B.rows = nullptr; B.row_off = nullptr; B.table = nullptr;
         B.small = nullptr; B.bounds = nullptr;
     };
-    if (!B.keys || !B.vals || !B.prep || !B.lrow || !B.lists || !B.arena || !B.rows ||
+    if (!B.keys || !B.vals || !B.prep || !B.cold || !B.lrow || !B.lists || !B.arena || !B.rows ||
         !B.row_off || (tsize && !B.table) || !B.small || !B.bounds) {
         release_tmp();
         return set_error(XM_ENOMEM, "batch of %lld A sources: work buffers", (long long)total);
@@ -466,6 +471,7 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
         }
     C.index_frame = X->frame;
     C.nz = X->nz;
+    C.h_f = (float)X->h;
     int32_t* err = (int32_t*)(B.small + 3);
     int32_t* bad_req = err + 1;
     int32_t* list_n = (int32_t*)(B.small + 4);
@@ -502,11 +508,12 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
                                          kSortBeginBit, 32 + bits_for(X->nz - 1), err, s);
             if (r != XM_OK) return r;
             XM_LAUNCH("k_batch_prep", grid_for(total), kBlock, 0, s, k_batch_prep, C, B.vals,
-                      B.prep, B.lrow);
+                      B.prep, B.cold, B.lrow);
         }
         ScanArgs a{};
         a.G = X->geom();
         a.A = B.prep;
+        a.Ac = B.cold;
         a.nA = total;
         a.want_best = 1;
         a.count = B.count;

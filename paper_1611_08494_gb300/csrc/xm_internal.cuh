@@ -88,9 +88,6 @@ struct __align__(16) BRec {
 
 // One A source, prepared in (zone, RA) order.
 struct __align__(16) APrep {
-    double lon, lat;      // index-frame RA / Dec (deg), for float64 tests
-    double theta;         // position angle in the index frame (rad)
-    double a, b;          // region sizes (rad); circle: a = b = radius
     uint64_t key64;       // fixed-point RA
     int32_t z;            // zone
     float zfrac;          // t - z - 1/2 (zones)
@@ -98,7 +95,15 @@ struct __align__(16) APrep {
     int32_t row;          // A row: in the caller's catalogue, or batch-wide
     float m00, m01, m10, m11;  // float32 map (x, y) -> (X/a, Y/b)
     int32_t shape;        // xm_shape of the source's region
-    int32_t req;          // request of a batch (0 for single calls)
+    float g;              // guard band of the float32 test (see make_aprep)
+};
+
+// The float64 description of an A source, read only by float64 tests
+// (kept apart so the scan's per-source load stays at 48 bytes).
+struct ACold {
+    double lon, lat;      // index-frame RA / Dec (deg)
+    double theta;         // position angle in the index frame (rad)
+    double a, b;          // region sizes (rad); circle: a = b = radius
 };
 
 // Geometry of a built index, passed by value to kernels.
@@ -278,7 +283,7 @@ struct A64 {
     double a, b;
 };
 
-__device__ __forceinline__ A64 make_a64(const APrep& A) {
+__device__ __forceinline__ A64 make_a64(const ACold& A) {
     A64 r;
     sincos(A.lon * kDeg, &r.sa, &r.ca);
     sincos(A.lat * kDeg, &r.sd, &r.cd);

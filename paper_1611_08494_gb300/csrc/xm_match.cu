@@ -222,6 +222,7 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             I.size_k = region->size_scale * region->size_unit_arcsec * kArcsec;
             I.pa_zero = region->pa_zero_deg;
             I.nz = X->nz;
+            I.h_f = (float)X->h;
 
             const bool want_all = (sel & XM_SEL_ALL) != 0;
             // member records: room for 12 per A source on average; sources
@@ -232,12 +233,13 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             uint64_t* keys = sorted_a ? T.get<uint64_t>(2 * nn) : nullptr;
             uint32_t* vals = sorted_a ? T.get<uint32_t>(2 * nn) : nullptr;
             APrep* prep = T.get<APrep>(nn);
+            ACold* cold = T.get<ACold>(nn);
             int32_t* lists = T.get<int32_t>(3 * nn);
             int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts
             int64_t* total = T.get<int64_t>(2);
             unsigned long long* stats = device_stats();
             MemberRec* arena = want_all ? T.get<MemberRec>(arena_cap) : nullptr;
-            if ((sorted_a && (!keys || !vals)) || !prep || !lists || !small || !total || !stats ||
+            if ((sorted_a && (!keys || !vals)) || !prep || !cold || !lists || !small || !total || !stats ||
                 (want_all && !arena))
                 return set_error(XM_ENOMEM, "xm_match: work buffers");
             e = cudaMemsetAsync(small, 0, 8 * sizeof(int32_t), s);
@@ -250,14 +252,15 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 xm_status r = radix_sort_u64(keys, vals, keys + nn, vals + nn, nA, kSortBeginBit,
                                              32 + bits_for(X->nz - 1), err, s);
                 if (r != XM_OK) return r;
-                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I, vals, prep, err);
+                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I, vals, prep, cold, err);
             } else if (nA > 0) {
                 XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I,
-                          (const uint32_t*)nullptr, prep, err);
+                          (const uint32_t*)nullptr, prep, cold, err);
             }
             ScanArgs a{};
             a.G = X->geom();
             a.A = prep;
+            a.Ac = cold;
             a.nA = nA;
             a.shape = region->shape;
             a.want_best = (sel & XM_SEL_BEST) != 0;

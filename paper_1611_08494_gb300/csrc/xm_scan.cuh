@@ -42,6 +42,7 @@ struct AIn {
     const double* pa_col;
     double size_k;   // radians per size unit (scale * unit * arcsec)
     double pa_zero;  // degrees
+    float h_f;       // zone height of the index (rad)
     int32_t nz;
 };
 
@@ -127,33 +128,36 @@ __device__ __forceinline__ float gamma_f(double gamma) {
     return ((uint64_t)__double_as_longlong(gamma) << 1) == 0 ? 0.0f : (float)gamma;
 }
 
-// The prepared form of one A source (position already in the index frame).
-__device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma, bool ok, double a,
-                                            double b, double pa, int32_t shape, int32_t pa_dir,
-                                            double size_k, double pa_zero, int32_t nz, int32_t row,
-                                            int32_t req) {
+// The prepared form of one A source (position already in the index frame),
+// for an index of zone height h_f (rad): the float32 part P and the float64
+// part C.
+__device__ __forceinline__ void make_aprep(double lon, double lat, double gamma, bool ok, double a,
+                                           double b, double pa, int32_t shape, int32_t pa_dir,
+                                           double size_k, double pa_zero, int32_t nz, float h_f,
+                                           int32_t row, APrep* P_out, ACold* C_out) {
     if (!size_ok(a, b, pa)) a = b = pa = 0.0;
     APrep P;
-    P.lon = lon;
-    P.lat = lat;
+    ACold C;
+    C.lon = lon;
+    C.lat = lat;
     const PosKey k = pos_key(lon, lat, nz);
     P.key64 = k.key64;
     P.z = k.z;
     P.zfrac = k.zfrac;
     P.row = row;
     P.shape = shape;
-    P.req = req;
-    P.a = a * size_k;
-    P.b = b * size_k;
+    C.a = a * size_k;
+    C.b = b * size_k;
     // position angle east of north of the input frame, in degrees; gamma
     // turns it to the index frame's north. The float64 angle (for rechecks)
     // is one fused step; the float32 one is reduced to [0, 360) first so the
     // float32 rotation sees a small argument (in float64 only when large).
     double raw = pa_zero + (pa_dir > 0 ? pa : -pa);
-    P.theta = fma(raw, kDeg, gamma);
-    float af = (float)P.a, bf = (float)P.b;
-    if (!ok || !(af > 0.0f || P.a > 0.0) || !(bf > 0.0f || P.b > 0.0)) {
+    C.theta = fma(raw, kDeg, gamma);
+    float af = (float)C.a, bf = (float)C.b;
+    if (!ok || !(af > 0.0f || C.a > 0.0) || !(bf > 0.0f || C.b > 0.0)) {
         P.R = 0.0f;
+        P.g = 0.0f;
         P.m00 = P.m01 = P.m10 = P.m11 = 0.0f;
     } else {
         // sizes below the float32 range stay regions (the float64 recheck
@@ -163,6 +167,11 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
         // bounding radius with a margin far above the float32 rounding here
         const float R = shape == XM_RECT ? sqrtf(fmaf(af, af, bf * bf)) : fmaxf(af, bf);
         P.R = R * (1.0f + 1e-6f);
+        // the guard band: g bounds |q32 - q| with a 3x margin (rounding of
+        // the offsets and of the map over a box of L_box), plus
+        // (rho / s)^2 - 1 <= R^2 / 3 (planar against azimuthal distance)
+        const float L_box = 1.42f * P.R + 2.0f * h_f;
+        P.g = 128.0f * kEps32 * L_box / fminf(af, bf) + 0.34f * P.R * P.R + 16.0f * kEps32;
         if (!(fabs(raw) < 720.0)) raw -= 360.0 * floor(raw * (1.0 / 360.0));
         float tf = (float)raw;
         tf -= 360.0f * floorf(tf * (1.0f / 360.0f));
@@ -174,7 +183,8 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
         P.m10 = ct * ib;
         P.m11 = -st * ib;
     }
-    return P;
+    *P_out = P;
+    *C_out = C;
 }
 
 // Prepared sources in scan order: vals[s] is the A row of position s (the
@@ -182,7 +192,7 @@ __device__ __forceinline__ APrep make_aprep(double lon, double lat, double gamma
 // the error bits (the sorted path found them already; setting them twice is
 // harmless).
 __global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out,
-                         int32_t* err) {
+                         ACold* __restrict__ cold, int32_t* err) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= I.n) return;
     const int64_t i = vals ? (int64_t)vals[s] : s;
@@ -194,8 +204,8 @@ __global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __rest
     const double pa = I.pa_col ? I.pa_col[i] : I.pa;
     if (!ok) atomicOr(err, kErrCoord);
     if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
-    out[s] = make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero,
-                        I.nz, (int32_t)i, 0);
+    make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero, I.nz, I.h_f,
+               (int32_t)i, &out[s], &cold[s]);
 }
 
 // One member found by the count pass: A row, its index among that row's
@@ -209,6 +219,7 @@ struct MemberRec {
 struct ScanArgs {
     IndexGeom G;
     const APrep* A;
+    const ACold* Ac;  // float64 part of A, same order
     int64_t nA;
     int32_t shape;
     int32_t want_best;
@@ -422,11 +433,12 @@ __device__ __forceinline__ float q32(const APrep& A, int shape, const ItemTerms&
 
 constexpr int kScanWarps = 4;
 constexpr int kScanThreads = 32 * kScanWarps;
-constexpr int kItemCap = 64;
+constexpr int kItemCap = 32;
 constexpr long long kKeyInf = 0x7FF0000000000000LL;  // above every finite key of either kind
 
 struct ScanWarpSmem {
     APrep A[32];
+    int32_t sidx[32];          // index of each source in P.A / P.Ac
     A64 a64[32];               // float64 basis of sources on float64 separations
     long long m1[32], m2[32];  // best key, second key
     long long r1[32];          // reported separation of the best (bits)
@@ -446,7 +458,7 @@ struct ScanWarpSmem {
 };
 
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
+__global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
     extern __shared__ __align__(16) unsigned char scan_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ScanWarpSmem& W = reinterpret_cast<ScanWarpSmem*>(scan_smem)[warp];
@@ -477,18 +489,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
         s_me = P.list ? P.list[first + lane] : first + lane;
         const APrep A = P.A[s_me];
         W.A[lane] = A;
-        const float L_box = 1.42f * A.R + 2.0f * G.h_f;
+        W.sidx[lane] = (int32_t)s_me;
+        // float32 error bounds: g (from the preparation) bounds |q32 - q|;
+        // esep bounds the float32 separation error (rad)
         const float L_mem = A.R + 2.0f * G.h_f;
-        const float bmin = (float)fmin(A.a, A.b);
-        // float32 error bounds (see the notes on the precision pattern):
-        // g bounds |q32 - q| (3x margin) plus (rho/s)^2 - 1 <= R^2/3; esep
-        // bounds the float32 separation error (rad).
-        W.g[lane] = 128.0f * kEps32 * L_box / bmin + 0.34f * A.R * A.R + 16.0f * kEps32;
+        W.g[lane] = A.g;
         W.esep[lane] = 16.0f * kEps32 * L_mem;
         const bool s64 = PREC == kPrecFP64 || MODE == kModeResolve ||
                          W.esep[lane] * 206264.8f > 9e-5f;
         W.sep64[lane] = s64;
-        if (s64 && A.R > 0.0f) W.a64[lane] = make_a64(A);
+        if (s64 && A.R > 0.0f) W.a64[lane] = make_a64(P.Ac[s_me]);
         W.m1[lane] = kKeyInf;
         W.m2[lane] = kKeyInf;
         W.r1[lane] = 0;
@@ -614,7 +624,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs P) {
                     const A64* a64 = &W.a64[al];
                     if (!s64) {  // band recheck of a float32-path source
                         if (a_own_for != al) {
-                            a_own = make_a64(A);
+                            a_own = make_a64(P.Ac[W.sidx[al]]);
                             a_own_for = al;
                         }
                         a64 = &a_own;
