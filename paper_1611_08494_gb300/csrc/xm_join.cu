@@ -58,11 +58,13 @@ __global__ void k_word_unmatched(const uint32_t* __restrict__ bits, int64_t nwor
     wcount[w] = __popc(~bits[w] & word_valid(w, nB));
 }
 
+// A-side join rows, one thread per A row. With pairs_apart the pair rows of
+// the "all" selection are written by k_write_pairs instead.
 __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off,
                           const int64_t* __restrict__ pb, const double* __restrict__ ps,
                           const int64_t* __restrict__ best_b, const double* __restrict__ best_s,
                           const int64_t* __restrict__ row_off, int64_t nA, int sel_all,
-                          int with_pairs, int with_un_a, int64_t* __restrict__ oa,
+                          int with_pairs, int with_un_a, int pairs_apart, int64_t* __restrict__ oa,
                           int64_t* __restrict__ ob, double* __restrict__ os) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
@@ -71,6 +73,7 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
     if (c > 0) {
         if (!with_pairs) return;
         if (sel_all) {
+            if (pairs_apart) return;
             int64_t p = pair_off[i];
             for (int32_t k = 0; k < c; k++) {
                 oa[o + k] = i;
@@ -87,6 +90,23 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
         ob[o] = -1;
         os[o] = NAN;
     }
+}
+
+// The pair rows of the "all" selection, one thread per pair: pair p of A
+// row a goes to row_off[a] + (p - pair_off[a]); reads and writes run in pair
+// order (coalesced).
+__global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
+                              const double* __restrict__ ps, const int64_t* __restrict__ pair_off,
+                              const int64_t* __restrict__ row_off, int64_t n_pairs,
+                              int64_t* __restrict__ oa, int64_t* __restrict__ ob,
+                              double* __restrict__ os) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const int64_t a = pa[p];
+    const int64_t o = row_off[a] + (p - pair_off[a]);
+    oa[o] = a;
+    ob[o] = pb[p];
+    os[o] = ps[p];
 }
 
 __global__ void k_write_b(const uint32_t* __restrict__ bits, const int64_t* __restrict__ word_off,
@@ -231,7 +251,8 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
     if (nA > 0)
         k_write_a<<<grid_for(nA), kBlock, 0, s>>>(R->count, R->pair_off, R->b_row, R->sep, R->best_b,
                                                  R->best_sep, S->row_off, nA, sel_all,
-                                                 (int)with_pairs, (int)with_un_a, a_row, b_row, sep);
+                                                 (int)with_pairs, (int)with_un_a, 0, a_row, b_row,
+                                                 sep);
     if (with_un_b && nB > 0)
         k_write_b<<<grid_for(nB), kBlock, 0, s>>>(S->bits, S->word_off, nB, total_a, a_row, b_row, sep);
     e = cudaGetLastError();
@@ -315,10 +336,15 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
         if (!J->a_row) return set_error(XM_ENOMEM, "xm_join: %lld rows", (long long)J->n);
         J->b_row = J->a_row + nr;
         J->sep = (double*)(J->b_row + nr);
-        if (nA > 0)
+        const int pairs_apart = sel_all && with_pairs && R->n_pairs > 0 && R->a_row;
+        if (pairs_apart)
+            XM_LAUNCH("k_write_pairs", grid_for(R->n_pairs), kBlock, 0, s, k_write_pairs, R->a_row,
+                      R->b_row, R->sep, R->pair_off, row_off, R->n_pairs, J->a_row, J->b_row,
+                      J->sep);
+        if (nA > 0 && (with_un_a || !pairs_apart))
             XM_LAUNCH("k_write_a", grid_for(nA), kBlock, 0, s, k_write_a, R->count, R->pair_off,
                       R->b_row, R->sep, R->best_b, R->best_sep, row_off, nA, sel_all,
-                      (int)with_pairs, (int)with_un_a, J->a_row, J->b_row, J->sep);
+                      (int)with_pairs, (int)with_un_a, pairs_apart, J->a_row, J->b_row, J->sep);
         if (with_un_b && nB > 0)
             XM_LAUNCH("k_write_b", grid_for(nB), kBlock, 0, s, k_write_b, bits, word_off, nB,
                       total_a, J->a_row, J->b_row, J->sep);
