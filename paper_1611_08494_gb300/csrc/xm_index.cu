@@ -5,14 +5,16 @@
 // partition is a set of equal-height declination zones cut into RA cells,
 // realised by a stable radix sort of the sources on (zone, RA key):
 //   k_zone_geom   per zone: centre, its sin/cos, number and width of RA cells
+//                 (once per device and zone count, then copied)
 //   k_ingest_b    per source, input order: validity, fixed-point position,
-//                 the 16-byte record (float32 offsets in its cell's tangent
-//                 frame, RA key, row), sort key; exact position kept by row
+//                 sort key; exact position kept by row
 //   radix sort    (xm_sort.cu)
 //   k_zone_start  first sorted source of each zone (binary search)
 //   k_zone_rows   rows of each zone, size of its RA bucket table (one to two
 //                 buckets per source); prefix sum; k_zone_lut the offsets
-//   k_gather_b    records into (zone, RA) order, and the bucket tables
+//   k_gather_b    the 16-byte records in (zone, RA) order (float32 offsets
+//                 in the cell's tangent frame, RA key, row), and the bucket
+//                 tables
 //   k_gap_fill    the long runs of the bucket tables
 #include <math.h>
 #include <string.h>
@@ -53,11 +55,10 @@ __global__ void k_zone_geom(int32_t nz, ZoneInfo* __restrict__ zones) {
 }
 
 __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restrict__ lat,
-                           int64_t n, int32_t nz, float h_f,
-                           const ZoneInfo* __restrict__ zones, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ vals, BRec* __restrict__ rec_in,
-                           double2* __restrict__ pos, double* __restrict__ px,
-                           double* __restrict__ py, double* __restrict__ pz, int32_t* err) {
+                           int64_t n, int32_t nz, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals, double2* __restrict__ pos,
+                           double* __restrict__ px, double* __restrict__ py,
+                           double* __restrict__ pz, int32_t* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double lo = lon[i], la = lat[i];
@@ -68,8 +69,19 @@ __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restr
     }
     lo = lon_mod360(lo);
     const PosKey k = pos_key(lo, la, nz);
+    keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
+    vals[i] = (uint32_t)i;
+    pos[i] = make_double2(lo, la);
+    if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
+}
+
+// The index record of a source at (lon, lat): float32 offsets in the tangent
+// frame of its cell (zone centre line, RA cell centre), from the exact
+// fixed-point position.
+__device__ __forceinline__ BRec make_brec(double lon, double lat, int32_t row, int32_t nz, float h_f,
+                                          const ZoneInfo& Z) {
+    const PosKey k = pos_key(lon, lat, nz);
     const uint32_t ra_key = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
-    const ZoneInfo& Z = zones[k.z];
     const uint32_t bin = bin_of(ra_key, Z.nbins);
     const LatTerms L = lat_terms(h_f * k.zfrac, Z.sin_cf, Z.cos_cf);
     float sa, hav_a;
@@ -78,12 +90,8 @@ __global__ void k_ingest_b(const double* __restrict__ lon, const double* __restr
     r.xi = L.cd * sa;
     r.eta = fmaf(L.cd * Z.sin_cf, hav_a, L.sdd);
     r.ra_key = ra_key;
-    r.row = (int32_t)i;
-    rec_in[i] = r;
-    keys[i] = ((uint64_t)k.z << 32) | ra_key;
-    vals[i] = (uint32_t)i;
-    pos[i] = make_double2(lo, la);
-    if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
+    r.row = row;
+    return r;
 }
 
 __global__ void k_zone_start(const uint64_t* __restrict__ keys, int64_t n, int32_t nz,
@@ -159,16 +167,18 @@ constexpr uint32_t kGapInline = 32;  // longest run written by the finding threa
 // after its bucket (the value: the zone's row count). Runs longer than
 // kGapInline go to a list for k_gap_fill.
 __global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                           int64_t n, const BRec* __restrict__ rec_in,
+                           int64_t n, const double2* __restrict__ pos, int32_t nz, float h_f,
                            const ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut,
                            BRec* __restrict__ rec, LutGap* __restrict__ gaps,
                            unsigned long long* __restrict__ n_gaps, long long gap_cap,
                            int32_t* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    rec[i] = rec_in[vals[i]];
     const uint64_t key = keys[i];
     const ZoneInfo& Z = zones[key >> 32];
+    const uint32_t row = vals[i];
+    const double2 p = pos[row];
+    rec[i] = make_brec(p.x, p.y, (int32_t)row, nz, h_f, Z);
     const int64_t rows = Z.end - Z.start, rel = i - Z.start;
     const int64_t b = bucket_of(key, Z);
     const int64_t pb = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], Z);
@@ -285,7 +295,6 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     double *d_lon = nullptr, *d_lat = nullptr;
     uint64_t *keys = nullptr, *tk = nullptr;
     uint32_t *vals = nullptr, *tv = nullptr;
-    BRec* rec_in = nullptr;
     int32_t* err = nullptr;
     int32_t* lut_cnt = nullptr;
     int64_t* lut_off = nullptr;
@@ -335,7 +344,6 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         }
         keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
         vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
-        rec_in = (BRec*)dev_alloc(nn * sizeof(BRec), s);
         err = (int32_t*)dev_alloc(sizeof(int32_t), s);
         lut_cnt = (int32_t*)dev_alloc(X->nz * sizeof(int32_t), s);
         lut_off = (int64_t*)dev_alloc(X->nz * sizeof(int64_t), s);
@@ -347,7 +355,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         gap_cap = X->lut_n / (kGapInline + 1) + 2 * (int64_t)X->nz + 16;
         gaps = (LutGap*)dev_alloc(gap_cap * sizeof(LutGap) + 16, s);
         n_gaps = gaps ? (unsigned long long*)(gaps + gap_cap) : nullptr;
-        if (!keys || !vals || !rec_in || !err || !lut_cnt || !lut_off || !X->lut || !gaps) {
+        if (!keys || !vals || !err || !lut_cnt || !lut_off || !X->lut || !gaps) {
             fail(set_error(XM_ENOMEM, "index build buffers"));
             break;
         }
@@ -365,8 +373,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             if (rg != XM_OK) return rg;
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz,
-                          G.h_f, X->zones, keys, vals, rec_in, X->pos, X->px, X->py, X->pz, err);
+                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz, keys, vals,
+                          X->pos, X->px, X->py, X->pz, err);
                 xm_status r = radix_sort_u64(keys, vals, tk, tv, n, kSortBeginBit,
                                              32 + bits_for(X->nz - 1), err, s);
                 if (r != XM_OK) return r;
@@ -381,8 +389,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->lut);
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, keys, vals, n, rec_in,
-                          X->zones, X->lut, X->rec, gaps, n_gaps, gap_cap, err);
+                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, keys, vals, n, X->pos, X->nz,
+                          G.h_f, X->zones, X->lut, X->rec, gaps, n_gaps, gap_cap, err);
                 XM_LAUNCH("k_gap_fill", 4 * 152, kBlock, 0, s, k_gap_fill, gaps, n_gaps, gap_cap,
                           X->lut);
             }
@@ -399,7 +407,6 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     } while (0);
 
     dev_free(d_lon, s);
-    dev_free(rec_in, s);
     dev_free(keys, s);
     dev_free(vals, s);
     dev_free(err, s);
