@@ -116,9 +116,14 @@ def oracle_sample(d, n_sample, nthreads):
 def cpu_baseline(d, n_sample=0):
     nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     if not n_sample:
-        # size the sample so the run takes ~10-20 s of CPU work
-        dt = oracle_sample(d, 2000, nthreads)
-        n_sample = int(min(d["a_lon"].size, max(2000, 2000 * 12.0 / max(dt, 1e-3))))
+        # size the sample so the run takes ~10-20 s of CPU work: the time of
+        # a sample is a fixed part (the oracle's grid over all of B) plus a
+        # part per A source, estimated from two small samples
+        t1 = oracle_sample(d, 2000, nthreads)
+        t2 = oracle_sample(d, 12000, nthreads)
+        per_a = max((t2 - t1) / 10000, 1e-9)
+        fixed = max(t1 - 2000 * per_a, 0.0)
+        n_sample = int(min(d["a_lon"].size, max(2000, (12.0 - fixed) / per_a)))
     dt = oracle_sample(d, n_sample, nthreads)
     return {"value": n_sample / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"first {n_sample} of {d['a_lon'].size} A sources against all "
