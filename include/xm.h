@@ -298,7 +298,7 @@ typedef struct {
     int32_t precision;          /* xm_precision, for every request */
     int32_t use_graph;          /* capture the device pipeline in a CUDA graph */
     int32_t persistent_blocks;  /* blocks per SM of the persistent scan, 0 = 4 */
-    int32_t reserved;
+    int32_t a_order;            /* xm_a_order of the scan over all requests' sources */
     int64_t pair_capacity;      /* pair arena; 0 = estimate (grown and rerun if short) */
     int64_t row_capacity;       /* join-row arena; 0 = estimate (likewise) */
 } xm_batch_opts;

@@ -103,6 +103,7 @@ __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
         atomicOr(err, kErrSize);
         atomicMin(bad_req, r);
     }
+    if (!keys) return;  // validation only (input order)
     const PosKey k = pos_key(lon, lat, C.nz);
     keys[g] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
     vals[g] = (uint32_t)g;
@@ -113,7 +114,7 @@ __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
                              int32_t* __restrict__ lrow) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= C.total) return;
-    const int64_t g = vals[s];
+    const int64_t g = vals ? (int64_t)vals[s] : s;
     const int32_t r = find_req(C.off, C.n_req, g);
     const ReqDev& R = C.req[r];
     const int64_t i = g - R.off;
@@ -398,6 +399,9 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = (opts && opts->persistent_blocks > 0) ? opts->persistent_blocks : 4;
+    // scan order of the sources: input order (request by request) unless
+    // the caller asks for the sorted (zone, RA) order
+    const bool sorted_a = opts && opts->a_order == XM_A_ORDER_SORTED;
     const int pblocks = std::max(1, sms * per_sm);
     const bool want_rows = std::any_of(out->join_type.begin(), out->join_type.end(),
                                        [](int32_t t) { return t >= 0; });
@@ -502,13 +506,19 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
         if (e2 == cudaSuccess && tsize) e2 = cudaMemsetAsync(B.table, 0xff, tsize * sizeof(uint64_t), s);
         if (e2 != cudaSuccess) return cuda_fail(e2, "batch memset");
         if (total > 0) {
-            XM_LAUNCH("k_batch_ingest", grid_for(total), kBlock, 0, s, k_batch_ingest, C, B.keys,
-                      B.vals, err, bad_req);
-            xm_status r = radix_sort_u64(B.keys, B.vals, B.keys + nn, B.vals + nn, total,
-                                         kSortBeginBit, 32 + bits_for(X->nz - 1), err, s);
-            if (r != XM_OK) return r;
-            XM_LAUNCH("k_batch_prep", grid_for(total), kBlock, 0, s, k_batch_prep, C, B.vals,
-                      B.prep, B.cold, B.lrow);
+            if (sorted_a) {
+                XM_LAUNCH("k_batch_ingest", grid_for(total), kBlock, 0, s, k_batch_ingest, C,
+                          B.keys, B.vals, err, bad_req);
+                xm_status r = radix_sort_u64(B.keys, B.vals, B.keys + nn, B.vals + nn, total,
+                                             kSortBeginBit, 32 + bits_for(X->nz - 1), err, s);
+                if (r != XM_OK) return r;
+            } else {  // validation only; the scan takes the sources request by request
+                XM_LAUNCH("k_batch_ingest", grid_for(total), kBlock, 0, s, k_batch_ingest, C,
+                          (uint64_t*)nullptr, (uint32_t*)nullptr, err, bad_req);
+            }
+            XM_LAUNCH("k_batch_prep", grid_for(total), kBlock, 0, s, k_batch_prep, C,
+                      sorted_a ? (const uint32_t*)B.vals : (const uint32_t*)nullptr, B.prep, B.cold,
+                      B.lrow);
         }
         ScanArgs a{};
         a.G = X->geom();

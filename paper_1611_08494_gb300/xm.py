@@ -357,7 +357,7 @@ class Request(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", _i32), ("use_graph", _i32), ("persistent_blocks", _i32),
-                ("reserved", _i32), ("pair_capacity", _i64), ("row_capacity", _i64)]
+                ("a_order", _i32), ("pair_capacity", _i64), ("row_capacity", _i64)]
 
 
 class BatchView(ctypes.Structure):
@@ -390,15 +390,16 @@ class Batch:
     """Many requests against one index in one pass. ``xm_match_batch``."""
 
     def __init__(self, index: Index, requests, precision=PREC_FP32, use_graph=False,
-                 persistent_blocks=0, pair_capacity=0, row_capacity=0, stream=None):
+                 persistent_blocks=0, pair_capacity=0, row_capacity=0, a_order=A_ORDER_DEFAULT,
+                 stream=None):
         keep = []
         arr = (Request * max(len(requests), 1))()
         for k, rq in enumerate(requests):
             rq = dict(rq)
             r, keep = request(rq.pop("lon"), rq.pop("lat"), keep=keep, **rq)
             arr[k] = r
-        opts = BatchOpts(int(precision), int(bool(use_graph)), int(persistent_blocks), 0,
-                         int(pair_capacity), int(row_capacity))
+        opts = BatchOpts(int(precision), int(bool(use_graph)), int(persistent_blocks),
+                         int(a_order), int(pair_capacity), int(row_capacity))
         h = _p()
         check(xm_match_batch(index.handle, arr, len(requests), ctypes.byref(opts),
                              _stream_handle(stream), ctypes.byref(h)), "xm_match_batch")

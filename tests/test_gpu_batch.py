@@ -96,7 +96,8 @@ def test_batch_equals_single_requests(xm, c4_small):
         np.testing.assert_array_equal(_h(full.b_row), rb)
 
 
-@pytest.mark.parametrize("mode", ["graph", "blocks1", "blocks8", "host", "short_arenas", "graph_short"])
+@pytest.mark.parametrize("mode", ["graph", "blocks1", "blocks8", "host", "short_arenas", "graph_short",
+                                  "sorted", "sorted_graph_short"])
 def test_batch_modes_agree(xm, c4_small, mode):
     d, idx = c4_small
     base = xm.Batch(idx, _dev_requests(d))
@@ -112,6 +113,10 @@ def test_batch_modes_agree(xm, c4_small, mode):
         reqs = _dev_requests(d, on_device=False)
     elif mode == "short_arenas":
         kw = dict(pair_capacity=16, row_capacity=16)
+    elif mode == "sorted":
+        kw = dict(a_order=xm.A_ORDER_SORTED)
+    elif mode == "sorted_graph_short":
+        kw = dict(a_order=xm.A_ORDER_SORTED, use_graph=True, pair_capacity=64, row_capacity=64)
     else:
         kw = dict(use_graph=True, pair_capacity=64, row_capacity=64)
     other = xm.Batch(idx, reqs, **kw)
