@@ -434,8 +434,10 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
         B.rb = B.ra + std::max(row_cap, 1LL);
         B.rs = (double*)(B.rb + std::max(row_cap, 1LL));
     }
-    B.keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
-    B.vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
+    if (sorted_a) {  // sort keys and permutation (input order needs neither)
+        B.keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
+        B.vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
+    }
     B.prep = (APrep*)dev_alloc(nn * sizeof(APrep), s);
     B.cold = (ACold*)dev_alloc(nn * sizeof(ACold), s);
     B.lrow = (int32_t*)dev_alloc(nn * sizeof(int32_t), s);
@@ -455,7 +457,8 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
         B.arena = nullptr; B.rows = nullptr; B.row_off = nullptr; B.table = nullptr;
         B.small = nullptr; B.bounds = nullptr;
     };
-    if (!B.keys || !B.vals || !B.prep || !B.cold || !B.lrow || !B.lists || !B.arena || !B.rows ||
+    if ((sorted_a && (!B.keys || !B.vals)) || !B.prep || !B.cold || !B.lrow || !B.lists ||
+        !B.arena || !B.rows ||
         !B.row_off || (tsize && !B.table) || !B.small || !B.bounds) {
         release_tmp();
         return set_error(XM_ENOMEM, "batch of %lld A sources: work buffers", (long long)total);
