@@ -187,6 +187,39 @@ def best(pairs, n_a, tau=1e-9):
     return {"best_b": best_b, "best_sep": best_sep, "near_tie": np.asarray(near, np.int64)}
 
 
+def best_per_b(pairs, n_b, tau=1e-9):
+    """Best pair of every B source, the other reading of paper §2.2's "best
+    pairs": among the pairs holding B_j, the one of smallest separation, ties
+    to the lowest A row. Returns ``best_a`` (int64, -1 when no pair holds B_j),
+    ``best_sep`` and ``near_tie`` (B rows), as ``best`` does for A."""
+    swapped = {"a_row": pairs["b_row"], "b_row": pairs["a_row"], "sep": pairs["sep"]}
+    r = best(swapped, n_b, tau)
+    return {"best_a": r["best_b"], "best_sep": r["best_sep"], "near_tie": r["near_tie"]}
+
+
+PICKS = ("best_b", "mutual")
+
+
+def pick(pairs, n_a, n_b, kind, tau=1e-9):
+    """The pairs kept by a further reading of "best pairs" (paper §2.2):
+    "best_b" keeps each B source's best pair, "mutual" the pairs that are the
+    best pair of both their A and their B source. Rows in ascending A row,
+    then B row, with the near ties of both selections."""
+    if kind not in PICKS:
+        raise OracleError(kind)
+    a, b, sep = pairs["a_row"], pairs["b_row"], pairs["sep"]
+    pb = best_per_b(pairs, n_b, tau)
+    keep = pb["best_a"][b] == a if a.size else np.zeros(0, bool)
+    near_a = np.empty(0, np.int64)
+    if kind == "mutual":
+        pa = best(pairs, n_a, tau)
+        keep = keep & (pa["best_b"][a] == b) if a.size else keep
+        near_a = pa["near_tie"]
+    order = np.lexsort((b[keep], a[keep]))
+    return {"a_row": a[keep][order], "b_row": b[keep][order], "sep": sep[keep][order],
+            "near_tie_b": pb["near_tie"], "near_tie_a": near_a}
+
+
 def selected_pairs(pairs, n_a, selection, tau=1e-9):
     """The pair set after match selection ("all" or "best")."""
     if selection == "all":

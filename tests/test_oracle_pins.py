@@ -413,3 +413,55 @@ def test_c2_small_grid_equals_brute_and_no_borderline():
     assert g["a_row"].size > 500
     assert _pairs(g) == _pairs(b)
     assert g["border_a"].size == 0
+
+
+# ------------------------------------------- further readings of "best pairs"
+
+def test_pick_hand_example():
+    """Best per B and mutual best on a hand-made pair set (paper §2.2 "best
+    pairs" read per B and symmetrically): B0 is held by A0 (1.0) and A1 (0.5);
+    B1 by A0 (2.0), A1 (3.0) and A2 (2.0), a tie broken to the lower A row."""
+    pairs = {"a_row": np.array([0, 0, 1, 1, 2]), "b_row": np.array([0, 1, 0, 1, 1]),
+             "sep": np.array([1.0, 2.0, 0.5, 3.0, 2.0])}
+    pb = oracle.best_per_b(pairs, 3)
+    np.testing.assert_array_equal(pb["best_a"], [1, 0, -1])
+    r = oracle.pick(pairs, 3, 3, "best_b")
+    np.testing.assert_array_equal(r["a_row"], [0, 1])
+    np.testing.assert_array_equal(r["b_row"], [1, 0])
+    np.testing.assert_array_equal(r["sep"], [2.0, 0.5])
+    m = oracle.pick(pairs, 3, 3, "mutual")
+    np.testing.assert_array_equal(m["a_row"], [1])
+    np.testing.assert_array_equal(m["b_row"], [0])
+
+
+def test_best_per_b_is_best_of_the_swapped_match_for_circles():
+    """For circles membership is symmetric, so the best pair of each B source
+    in match(A, B) is the best pair of that source in match(B, A)."""
+    d = synth.c1()
+    ab = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], shape=0, a=1.0)
+    ba = oracle.match(d["b_lon"], d["b_lat"], d["a_lon"], d["a_lat"], shape=0, a=1.0)
+    pb = oracle.best_per_b(ab, d["b_lon"].size)
+    bb = oracle.best(ba, d["b_lon"].size)
+    assert pb["near_tie"].size == 0 and bb["near_tie"].size == 0
+    np.testing.assert_array_equal(pb["best_a"], bb["best_b"])
+    has = pb["best_a"] >= 0
+    np.testing.assert_allclose(pb["best_sep"][has], bb["best_sep"][has], rtol=0, atol=1e-9)
+
+
+def test_mutual_best_is_symmetric_and_inside_both_bests():
+    d = synth.c1()
+    n_a, n_b = d["a_lon"].size, d["b_lon"].size
+    ab = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], shape=0, a=1.0)
+    ba = oracle.match(d["b_lon"], d["b_lat"], d["a_lon"], d["a_lat"], shape=0, a=1.0)
+    m_ab = oracle.pick(ab, n_a, n_b, "mutual")
+    m_ba = oracle.pick(ba, n_b, n_a, "mutual")
+    assert m_ab["a_row"].size > 6000  # planted pairs are mostly mutual
+    got = set(zip(m_ab["a_row"].tolist(), m_ab["b_row"].tolist()))
+    assert got == set(zip(m_ba["b_row"].tolist(), m_ba["a_row"].tolist()))
+    best_a = oracle.best(ab, n_a)["best_b"]
+    best_b = oracle.best_per_b(ab, n_b)["best_a"]
+    assert all(best_a[a] == b and best_b[b] == a for a, b in got)
+    # every pair that is best both ways is kept
+    both = [(a, b) for a, b in zip(ab["a_row"].tolist(), ab["b_row"].tolist())
+            if best_a[a] == b and best_b[b] == a]
+    assert set(both) == got
