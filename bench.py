@@ -385,6 +385,9 @@ def run_ours(args):
     # roofline of the dominant kernel
     roof = roofline(prof, st, args.steps, n_a, n_b, zone_h, total_ms)
 
+    # further readings of "best pairs" over the C2 pair list (index resident)
+    picks = pick_leg(xm, torch, step, stream)
+
     if rank != 0:
         return
     peaks = load_peaks()
@@ -403,6 +406,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk.summary(),
+        "picks": picks,
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in
                                 sorted(prof.items(), key=lambda kv: -kv[1][0])[:16]},
         "stats_per_step": {k: v // args.steps for k, v in st.items()},
@@ -419,6 +423,26 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(d, args.cpu_sample)
     print(json.dumps(line), flush=True)
+
+
+def pick_leg(xm, torch, step, stream):
+    """Best pair per B source and mutual best pairs over one C2 result:
+    device time of xm_pick_pairs (median of 10) and pairs per second."""
+    idx, res, _, _ = step(xm.PREC_FP32, False)
+    out = {"pairs_in": int(res.n_pairs)}
+    for kind in ("best_b", "mutual"):
+        ms = []
+        for k in range(11):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rows = res.pick(kind)
+            e1.record(stream)
+            e1.synchronize()
+            if k:
+                ms.append(e0.elapsed_time(e1))
+        out[kind] = {"ms": statistics.median(ms), "rows": int(rows.n),
+                     "pairs_per_s": res.n_pairs / (statistics.median(ms) / 1e3)}
+    return out
 
 
 # ------------------------------------------------------- all-sky C3 leg

@@ -280,6 +280,27 @@ XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int
                                  int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
                                  int64_t* n_rows, void* stream);
 
+/* ---- further readings of "best pairs" (paper §2.2) ----------------------- */
+
+/* The paper keeps "all" matches or only the "best pairs" without saying
+ * whose best; XM_SEL_BEST reads it per A source. These are the other two
+ * readings, over the pair list of an "all" result:
+ *   XM_PICK_BEST_B  for every B source held by some pair, the pair of
+ *                   smallest angular separation (ties to the lowest A row);
+ *   XM_PICK_MUTUAL  the pairs that are the best pair of both their A source
+ *                   (as XM_SEL_BEST) and their B source. */
+typedef enum { XM_PICK_BEST_B = 1, XM_PICK_MUTUAL = 2 } xm_pick;
+
+/* Rows (a_row, b_row, sep_arcsec; n_unmatched_* = 0) of the pairs kept by
+ * `pick`, in ascending A row then B row. Separations closer than the float32
+ * error bound are decided in float64 from the exact positions, so the choice
+ * is the float64 one. `result` must come from xm_match on `index` with the
+ * ALL selection (and BEST for XM_PICK_MUTUAL). Synchronises `stream` once.
+ * Errors: XM_EINVAL (selection missing, another index), XM_EUNSUPPORTED
+ * (views of batch results), XM_ENOMEM, XM_ECUDA, XM_ETIMEOUT. */
+XM_API xm_status xm_pick_pairs(const xm_index* index, const xm_result* result, int32_t pick,
+                               void* stream, xm_rows** out);
+
 /* ---- batches of requests (one launch of the persistent scan) --------- */
 
 /* One cross-match request of a batch: an A catalogue, its region (§2.1), the

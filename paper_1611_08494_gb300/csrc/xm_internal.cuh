@@ -436,6 +436,11 @@ struct xm_result {
     double* sep;
     int64_t* best_b;
     double* best_sep;
+    // float64 description of the A sources (kept for float64 decisions after
+    // the match; NULL in views of batch results): acold[slot], slot = a_slot[a]
+    // (or a itself when a_slot is NULL)
+    xm::ACold* acold;
+    int32_t* a_slot;
 };
 
 struct xm_rows {

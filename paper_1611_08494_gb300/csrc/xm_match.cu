@@ -71,6 +71,13 @@ struct Temps {
     }
 };
 
+// a_slot[row] = position of A row `row` in the sorted order.
+__global__ void k_slot_of_row(const uint32_t* __restrict__ vals, int64_t n,
+                              int32_t* __restrict__ a_slot) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) a_slot[vals[s]] = (int32_t)s;
+}
+
 // A second stream per host thread and device, with a fork and a join event,
 // for work of a call that can overlap the rest of it (the near-tie resolve
 // runs beside the pair placement and sorts).
@@ -121,6 +128,8 @@ static void free_result(xm_result* R) {
     dev_free(R->pair_off, s);
     dev_free(R->a_row, s);
     dev_free(R->best_b, s);
+    dev_free(R->acold, s);
+    dev_free(R->a_slot, s);
     delete R;
 }
 
@@ -233,7 +242,10 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             uint64_t* keys = sorted_a ? T.get<uint64_t>(2 * nn) : nullptr;
             uint32_t* vals = sorted_a ? T.get<uint32_t>(2 * nn) : nullptr;
             APrep* prep = T.get<APrep>(nn);
-            ACold* cold = T.get<ACold>(nn);
+            // the float64 part stays with the result (float64 decisions after
+            // the match); in sorted order with the row -> slot map
+            R->acold = (ACold*)dev_alloc(nn * sizeof(ACold), s);
+            ACold* cold = R->acold;
             int32_t* lists = T.get<int32_t>(3 * nn);
             int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts
             int64_t* total = T.get<int64_t>(2);
@@ -253,6 +265,10 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                                              32 + bits_for(X->nz - 1), err, s);
                 if (r != XM_OK) return r;
                 XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I, vals, prep, cold, err);
+                R->a_slot = (int32_t*)dev_alloc(nn * sizeof(int32_t), s);
+                if (!R->a_slot) return set_error(XM_ENOMEM, "xm_match: slot map");
+                XM_LAUNCH("k_slot_of_row", grid_for(nA), kBlock, 0, s, k_slot_of_row, vals, nA,
+                          R->a_slot);
             } else if (nA > 0) {
                 XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I,
                           (const uint32_t*)nullptr, prep, cold, err);

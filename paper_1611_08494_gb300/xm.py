@@ -106,6 +106,8 @@ xm_copy_to_host = _sig("xm_copy_to_host", _i32, _p, _p, ctypes.c_size_t, _p)
 xm_join_noalloc = _sig("xm_join_noalloc", _i32, _p, _i32, _i32, _p, _p, _p, _i64,
                        ctypes.POINTER(_i64), _p)
 xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
+xm_pick_pairs = _sig("xm_pick_pairs", _i32, _p, _p, _i32, _p, ctypes.POINTER(_p))
+PICKS = {"best_b": 1, "mutual": 2}
 
 
 class XMError(RuntimeError):
@@ -267,6 +269,22 @@ class Result:
     def best_sep(self):
         return _tensor(self.view.best_sep_arcsec, self.n_a if self.view.best_sep_arcsec else 0,
                        "<f8", self)
+
+    def pick(self, kind: str, stream=None) -> "Rows":
+        """Best pair per B source ("best_b") or mutual best pairs ("mutual").
+        ``xm_pick_pairs``."""
+        h = _p()
+        check(xm_pick_pairs(self.index.handle, self.handle, PICKS[kind], _stream_handle(stream),
+                            ctypes.byref(h)), "xm_pick_pairs")
+        rows = Rows.__new__(Rows)
+        rows.handle = h.value
+        rows.result = self
+        v = RowsView()
+        check(xm_rows_get(rows.handle, ctypes.byref(v)), "xm_rows_get")
+        rows.view = v
+        rows.n = v.n
+        rows.n_unmatched_a, rows.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
+        return rows
 
     def join(self, join_type: str, selection=SEL_ALL, stream=None) -> "Rows":
         return Rows(self, join_type, selection, stream)

@@ -362,3 +362,57 @@ def test_c3_scaled_all_sky(xm, prec):
     got = set(zip(_host(res.a_row).tolist(), _host(res.b_row).tolist()))
     found = np.array([(a, b) in got for a, b in zip(t["a_row"].tolist(), t["b_row"].tolist())])
     np.testing.assert_array_equal(found, t["rho_arcsec"] <= 2.0)
+
+
+# --------------------------------------- further readings of "best pairs"
+
+def _check_pick(res, ref, n_a, n_b, kind):
+    exp = oracle.pick(ref, n_a, n_b, kind)
+    assert exp["near_tie_b"].size == 0 and exp["near_tie_a"].size == 0
+    rows = res.pick(kind)
+    np.testing.assert_array_equal(_host(rows.a_row), exp["a_row"])
+    np.testing.assert_array_equal(_host(rows.b_row), exp["b_row"])
+    if exp["sep"].size:
+        assert np.max(np.abs(_host(rows.sep) - exp["sep"])) <= SEP_TOL
+    return exp["a_row"].size
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", ["best_b", "mutual"])
+def test_pick_c1_c2(xm, c1, c2_small, prec, kind):
+    for d, ref in (c1, c2_small):
+        for a_order in (1, 2):  # the sorted order keeps a row -> slot map
+            _, res = run(xm, d, prec, a_order=a_order)
+            assert _check_pick(res, ref, d["a_lon"].size, d["b_lon"].size, kind) > 100
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pick_near_ties_decided_in_float64(xm, prec):
+    """B sources between two A sources, closer to one by 1e-6 to 1e-5 arcsec:
+    inside the float32 error band, so the choice is made in float64."""
+    half = 0.5 / 3600.0
+    a_lon, a_lat, b_lon, b_lat = [], [], [], []
+    for k, delta in enumerate([1e-6, -1e-6, 3e-6, -5e-6, 1e-5, -2e-5, 4e-5, -8e-5]):
+        lon0, lat0 = 20.0 + 0.01 * k, -30.0 + 0.02 * k
+        a_lon += [lon0 - half / np.cos(np.radians(lat0)), lon0 + half / np.cos(np.radians(lat0))]
+        a_lat += [lat0, lat0]
+        b_lon.append(lon0 + delta / 3600.0 / np.cos(np.radians(lat0)))
+        b_lat.append(lat0)
+    d = dict(a_lon=np.array(a_lon), a_lat=np.array(a_lat), b_lon=np.array(b_lon),
+             b_lat=np.array(b_lat), a_frame=0, b_frame=0, region=dict(shape=0, a=1.0))
+    ref = oracle_ref(d)
+    assert ref["a_row"].size == 16  # every B lies in both regions
+    _, res = run(xm, d, prec)
+    for kind in ("best_b", "mutual"):
+        _check_pick(res, ref, d["a_lon"].size, d["b_lon"].size, kind)
+
+
+def test_pick_needs_the_selections(xm, c1):
+    d, _ = c1
+    _, res = run(xm, d, "fp32", selection=xm.SEL_BEST)
+    with pytest.raises(xm.XMError, match="EINVAL"):
+        res.pick("best_b")
+    _, res = run(xm, d, "fp32", selection=xm.SEL_ALL)
+    res.pick("best_b")
+    with pytest.raises(xm.XMError, match="EINVAL"):
+        res.pick("mutual")
