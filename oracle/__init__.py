@@ -220,6 +220,29 @@ def pick(pairs, n_a, n_b, kind, tau=1e-9):
             "near_tie_b": pb["near_tie"], "near_tie_a": near_a}
 
 
+def match_values(a_keys, b_keys):
+    """The Exact Value functional case (paper §2.1): A_i and B_j match when
+    their key columns hold the same value. Integer keys compare as integers,
+    float64 keys as numbers (-0 equals +0; NaN equals nothing). The plain
+    definition: B rows grouped by value, each A key looked up. Returns int64
+    ``a_row``, ``b_row`` in ascending (a_row, b_row) and ``sep`` (0: the
+    values are equal)."""
+    a_list = np.asarray(a_keys).tolist()
+    b_list = np.asarray(b_keys).tolist()
+    rows_of = {}
+    for j, v in enumerate(b_list):
+        if v == v:  # NaN equals nothing
+            rows_of.setdefault(v, []).append(j)
+    a_out, b_out = [], []
+    for i, v in enumerate(a_list):
+        if v == v:
+            for j in rows_of.get(v, ()):
+                a_out.append(i)
+                b_out.append(j)
+    a_row = np.array(a_out, np.int64)
+    return {"a_row": a_row, "b_row": np.array(b_out, np.int64), "sep": np.zeros(a_row.size)}
+
+
 def selected_pairs(pairs, n_a, selection, tau=1e-9):
     """The pair set after match selection ("all" or "best")."""
     if selection == "all":

@@ -465,3 +465,38 @@ def test_mutual_best_is_symmetric_and_inside_both_bests():
     both = [(a, b) for a, b in zip(ab["a_row"].tolist(), ab["b_row"].tolist())
             if best_a[a] == b and best_b[b] == a]
     assert set(both) == got
+
+
+# ------------------------------------------------ Exact Value functional case
+
+def test_match_values_equals_all_pairs_comparison():
+    """Brute force over every (i, j) on small integer keys with repeats on
+    both sides (paper §2.1, Exact Value case)."""
+    g = synth.rng(31)
+    a = g.integers(-20, 20, 300)
+    b = g.integers(-20, 20, 200)
+    r = oracle.match_values(a, b)
+    ii, jj = np.nonzero(a[:, None] == b[None, :])
+    np.testing.assert_array_equal(r["a_row"], ii)
+    np.testing.assert_array_equal(r["b_row"], jj)
+    assert np.all(r["sep"] == 0)
+    # best (lowest B row per A) is the argmin of the all-pairs list
+    bb = oracle.best(r, a.size)
+    for i in range(a.size):
+        js = np.nonzero(b == a[i])[0]
+        assert bb["best_b"][i] == (js[0] if js.size else -1)
+
+
+def test_match_values_floats_zero_and_nan():
+    a = np.array([0.0, -0.0, np.nan, 1.5, 2.0**60, -np.inf])
+    b = np.array([-0.0, np.nan, 1.5, 1.5000000000000002, 2.0**60 + 0.0, -np.inf, 0.0])
+    r = oracle.match_values(a, b)
+    pairs = set(zip(r["a_row"].tolist(), r["b_row"].tolist()))
+    assert pairs == {(0, 0), (0, 6), (1, 0), (1, 6), (3, 2), (4, 4), (5, 5)}
+
+
+def test_match_values_large_int64_keys_compare_exactly():
+    big = np.array([2**62 + 1, 2**62 + 2, -(2**63), 2**63 - 1], np.int64)
+    r = oracle.match_values(big, big[::-1].copy())
+    np.testing.assert_array_equal(r["a_row"], [0, 1, 2, 3])
+    np.testing.assert_array_equal(r["b_row"], [3, 2, 1, 0])
