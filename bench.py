@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--c3-scale", type=float, default=1.0, help="0 skips the all-sky C3 leg")
     p.add_argument("--c4-requests", type=int, default=4096, help="0 skips the batched C4 leg")
     p.add_argument("--c4-b", type=int, default=100_000_000, help="resident B of the C4 leg")
+    p.add_argument("--values-scale", type=float, default=1.0,
+                   help="0 skips the Exact Value leg (A 5e7 x B 2e8 int64 keys at 1)")
     return p.parse_args()
 
 
@@ -416,6 +418,8 @@ def run_ours(args):
         line["c3"] = c3_leg(args, xm, torch)
     if world == 1 and args.c4_requests > 0:
         line["c4"] = c4_leg(args, xm, torch)
+    if world == 1 and args.values_scale > 0:
+        line["exact_value"] = values_leg(args, xm, torch)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = serving_leg(args, xm, torch)
     elif world > 1:
@@ -500,6 +504,52 @@ def c3_leg(args, xm, torch):
                                       "achieved": ach, "peak": peak, "unit": "GB/s",
                                       "frac": ach / peak, "peak_source": "of measured"}
         out[name] = entry
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------- Exact Value case leg
+
+def values_leg(args, xm, torch):
+    """The Exact Value functional case: int64 keys, A = 5e7 and B = 2e8 at
+    scale 1 (repeats on the B side). A step sorts B's keys, finds every A key
+    and writes all pairs and the best pairs; the dominant kernel (the sort
+    pass) against the HBM roofline."""
+    from paper_1611_08494_gb300 import synth_gpu
+
+    n_a, n_b = int(5e7 * args.values_scale), int(2e8 * args.values_scale)
+    d = synth_gpu.values(n_a=n_a, n_b=n_b)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(4):
+        if k == 3:
+            xm.reset_stats()
+            xm.prof_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = xm.ValueResult(d["a_keys"], d["b_keys"], selection=xm.SEL_ALL | xm.SEL_BEST)
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ms.append(e0.elapsed_time(e1))
+        pairs = int(res.n_pairs)
+        del res
+    prof = xm.prof_all()
+    xm.prof_enable(False)
+    peak = load_peaks().get("hbm_gbs", 6800.0)
+    out = {"workload": f"exact value: int64 keys, A={n_a} (60 % present in B), B={n_b} "
+                       "(10 % repeats)", "pairs": pairs, "ms": statistics.median(ms),
+           "a_per_s": n_a / (statistics.median(ms) / 1e3),
+           "kernels_ms": {k: round(v[0], 3) for k, v in
+                          sorted(prof.items(), key=lambda kv: -kv[1][0])[:6]}}
+    sw = prof.get("k_onesweep")
+    if sw:
+        alg = 24.0 * n_b  # key and row read and written per pass
+        ach = alg / (sw[0] / sw[1] * 1e-3) / 1e9
+        out["roofline"] = {"kernel": "k_onesweep", "bound": "hbm", "algorithmic_bytes": alg,
+                           "ms_per_launch": sw[0] / sw[1], "achieved": ach, "peak": peak,
+                           "unit": "GB/s", "frac": ach / peak, "peak_source": "of measured"}
     del d
     torch.cuda.empty_cache()
     return out

@@ -280,6 +280,24 @@ XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int
                                  int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
                                  int64_t* n_rows, void* stream);
 
+/* ---- the Exact Value functional case (paper §2.1) ------------------------ */
+
+typedef enum { XM_KEY_INT64 = 0, XM_KEY_FLOAT64 = 1 } xm_key_type;
+
+/* Matches A_i with B_j when their key columns (one per catalogue, n_a and
+ * n_b values of key_type, host or device by on_device) hold the same value:
+ * integers compare as integers, float64 as numbers (-0 equals +0, NaN
+ * equals nothing). The result has the layout of xm_match: pairs in ascending
+ * A row then B row with sep_arcsec 0, member counts, and for XM_SEL_BEST the
+ * lowest matching B row (sep 0; -1 / NaN when none), so xm_join applies; it
+ * holds no positions (xm_pick_pairs refuses it). B keys are sorted once
+ * (stable radix sort over the key bits that differ), A keys found by binary
+ * search. Synchronises `stream` twice. Errors: XM_EINVAL, XM_ENOMEM, XM_ECUDA,
+ * XM_ETIMEOUT. */
+XM_API xm_status xm_match_values(const void* a_keys, int64_t n_a, const void* b_keys, int64_t n_b,
+                                 int32_t key_type, int32_t on_device, int32_t selection,
+                                 void* stream, xm_result** out);
+
 /* ---- further readings of "best pairs" (paper §2.2) ----------------------- */
 
 /* The paper keeps "all" matches or only the "best pairs" without saying
@@ -297,7 +315,8 @@ typedef enum { XM_PICK_BEST_B = 1, XM_PICK_MUTUAL = 2 } xm_pick;
  * is the float64 one. `result` must come from xm_match on `index` with the
  * ALL selection (and BEST for XM_PICK_MUTUAL). Synchronises `stream` once.
  * Errors: XM_EINVAL (selection missing, another index), XM_EUNSUPPORTED
- * (views of batch results), XM_ENOMEM, XM_ECUDA, XM_ETIMEOUT. */
+ * (results without positions: views of batch results, xm_match_values),
+ * XM_ENOMEM, XM_ECUDA, XM_ETIMEOUT. */
 XM_API xm_status xm_pick_pairs(const xm_index* index, const xm_result* result, int32_t pick,
                                void* stream, xm_rows** out);
 

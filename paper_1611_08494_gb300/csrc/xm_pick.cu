@@ -147,7 +147,9 @@ extern "C" xm_status xm_pick_pairs(const xm_index* X, const xm_result* R, int32_
         return set_error(XM_EINVAL, "xm_pick_pairs: the result holds no ALL selection");
     if (pick == XM_PICK_MUTUAL && !(R->selection & XM_SEL_BEST))
         return set_error(XM_EINVAL, "xm_pick_pairs: MUTUAL needs the BEST selection too");
-    if (!R->acold) return set_error(XM_EUNSUPPORTED, "xm_pick_pairs: not for views of batch results");
+    if (!R->acold)
+        return set_error(XM_EUNSUPPORTED, "xm_pick_pairs: the result holds no positions (batch view "
+                                          "or exact-value match)");
     if (R->n_b != X->n) return set_error(XM_EINVAL, "xm_pick_pairs: the result is of another index");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = R->n_pairs, nB = R->n_b;

@@ -1,0 +1,232 @@
+// xm_values.cu -- the Exact Value functional case (paper §2.1): A_i and B_j
+// match when their key columns hold the same value. The result has the
+// layout of a positional match (pairs in ascending A row then B row, member
+// counts, the best pair = the lowest B row), so the joins of §2.2 apply
+// unchanged.
+//
+//   k_val_key     keys to order-preserving unsigned codes (int64: sign bit
+//                 flipped; float64: IEEE total order with -0 folded into +0;
+//                 NaN -> all ones, above every number, never looked up), row
+//                 payloads, and the AND / OR of all B codes (bits that never
+//                 differ need no sort pass)
+//   radix sort    stable, so equal keys keep ascending B rows (xm_sort.cu)
+//   k_val_probe   per A: the run of equal B codes by binary search; count,
+//                 best B row, first sorted position
+//   prefix sum    pair offsets
+//   k_val_emit    the pairs of each A row
+#include <math.h>
+
+#include <new>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr uint64_t kNaNCode = ~0ull;
+
+__device__ __forceinline__ uint64_t key_code(const void* keys, int64_t i, int32_t type) {
+    if (type == XM_KEY_INT64) return (uint64_t)((const int64_t*)keys)[i] ^ 0x8000000000000000ull;
+    double v = ((const double*)keys)[i];
+    uint64_t u = (uint64_t)__double_as_longlong(v);
+    if ((u & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) return kNaNCode;  // NaN
+    if ((u << 1) == 0) u = 0;  // -0 is +0
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void k_val_key(const void* __restrict__ keys, int64_t n, int32_t type,
+                          uint64_t* __restrict__ codes, uint32_t* __restrict__ rows,
+                          unsigned long long* __restrict__ and_or) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t c = ~0ull, o = 0;
+    if (i < n) {
+        c = key_code(keys, i, type);
+        codes[i] = c;
+        rows[i] = (uint32_t)i;
+        o = c;
+    }
+    // block-wide AND / OR, one atomic pair per warp
+    for (int s = 16; s > 0; s >>= 1) {
+        c &= __shfl_xor_sync(0xffffffffu, c, s);
+        o |= __shfl_xor_sync(0xffffffffu, o, s);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAnd(&and_or[0], (unsigned long long)c);
+        atomicOr(&and_or[1], (unsigned long long)o);
+    }
+}
+
+// First position in sorted[0, n) whose code is >= c (or > c when upper).
+__device__ __forceinline__ int64_t bound(const uint64_t* __restrict__ sorted, int64_t n, uint64_t c,
+                                         bool upper) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        const uint64_t v = __ldg(&sorted[mid]);
+        if (upper ? v <= c : v < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_val_probe(const void* __restrict__ a_keys, int64_t n_a, int32_t type,
+                            const uint64_t* __restrict__ sorted, const uint32_t* __restrict__ rows,
+                            int64_t n_b, int32_t* __restrict__ count, int64_t* __restrict__ first,
+                            int64_t* __restrict__ best_b, double* __restrict__ best_sep) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_a) return;
+    const uint64_t c = key_code(a_keys, i, type);
+    int64_t lo = 0, hi = 0;
+    if (!(type == XM_KEY_FLOAT64 && c == kNaNCode)) {  // (the int64 maximum has that code too)
+        lo = bound(sorted, n_b, c, false);
+        hi = lo < n_b && __ldg(&sorted[lo]) == c ? bound(sorted, n_b, c, true) : lo;
+    }
+    const int64_t m = hi - lo;
+    count[i] = (int32_t)(m < 2147483647 ? m : 2147483647);
+    first[i] = lo;
+    if (best_b) {
+        best_b[i] = m > 0 ? (int64_t)rows[lo] : -1;
+        best_sep[i] = m > 0 ? 0.0 : NAN;
+    }
+}
+
+__global__ void k_val_emit(const int32_t* __restrict__ count, const int64_t* __restrict__ first,
+                           const int64_t* __restrict__ pair_off, const uint32_t* __restrict__ rows,
+                           int64_t n_a, int64_t* __restrict__ pa, int64_t* __restrict__ pb,
+                           double* __restrict__ ps) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_a) return;
+    const int32_t c = count[i];
+    const int64_t o = pair_off[i], f = first[i];
+    for (int32_t k = 0; k < c; k++) {
+        pa[o + k] = i;
+        pb[o + k] = rows[f + k];
+        ps[o + k] = 0.0;
+    }
+}
+
+unsigned grid_of(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+int top_bit(uint64_t x) {
+    int b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+
+}  // namespace
+}  // namespace xm
+
+using namespace xm;
+
+extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void* b_keys,
+                                     int64_t n_b, int32_t key_type, int32_t on_device,
+                                     int32_t selection, void* stream, xm_result** out) {
+    if (!out) return set_error(XM_EINVAL, "xm_match_values: out is NULL");
+    *out = nullptr;
+    if (n_a < 0 || n_b < 0 || n_a > 2147483647LL || n_b > 2147483647LL ||
+        (n_a > 0 && !a_keys) || (n_b > 0 && !b_keys))
+        return set_error(XM_EINVAL, "xm_match_values: bad key columns");
+    if (key_type != XM_KEY_INT64 && key_type != XM_KEY_FLOAT64)
+        return set_error(XM_EINVAL, "xm_match_values: bad key type %d", key_type);
+    if (selection < 1 || selection > 3)
+        return set_error(XM_EINVAL, "xm_match_values: bad selection %d", selection);
+    cudaStream_t s = (cudaStream_t)stream;
+    xm_result* R = new (std::nothrow) xm_result();
+    if (!R) return set_error(XM_ENOMEM, "xm_match_values: host allocation");
+    cudaGetDevice(&R->device);
+    R->selection = selection;
+    R->precision = XM_PREC_FP64;
+    R->shape = -1;
+    R->n_a = n_a;
+    R->n_b = n_b;
+    const int64_t na1 = n_a > 0 ? n_a : 1, nb1 = n_b > 0 ? n_b : 1;
+    const bool want_best = (selection & XM_SEL_BEST) != 0;
+    R->count = (int32_t*)dev_alloc(na1 * sizeof(int32_t), s);
+    R->pair_off = (int64_t*)dev_alloc(na1 * sizeof(int64_t), s);
+    if (want_best) {
+        R->best_b = (int64_t*)dev_alloc(na1 * (sizeof(int64_t) + sizeof(double)), s);
+        R->best_sep = R->best_b ? (double*)(R->best_b + na1) : nullptr;
+    }
+    // temporaries: host key copies, codes and rows (and sort scratch), first
+    // positions, totals and the error word
+    void* d_a = nullptr;
+    void* d_b = nullptr;
+    uint64_t* codes = (uint64_t*)dev_alloc(2 * nb1 * sizeof(uint64_t), s);
+    uint32_t* rows = (uint32_t*)dev_alloc(2 * nb1 * sizeof(uint32_t), s);
+    int64_t* first = (int64_t*)dev_alloc(na1 * sizeof(int64_t), s);
+    unsigned long long* small = (unsigned long long*)dev_alloc(4 * sizeof(unsigned long long), s);
+    auto body = [&]() -> xm_status {
+        if (!R->count || !R->pair_off || (want_best && !R->best_b) || !codes || !rows || !first ||
+            !small)
+            return set_error(XM_ENOMEM, "xm_match_values: work buffers");
+        cudaError_t e;
+        const void* ak = a_keys;
+        const void* bk = b_keys;
+        if (!on_device) {
+            d_a = dev_alloc(na1 * 8, s);
+            d_b = dev_alloc(nb1 * 8, s);
+            if (!d_a || !d_b) return set_error(XM_ENOMEM, "xm_match_values: key copies");
+            e = n_a ? cudaMemcpyAsync(d_a, a_keys, n_a * 8, cudaMemcpyHostToDevice, s) : cudaSuccess;
+            if (e == cudaSuccess && n_b)
+                e = cudaMemcpyAsync(d_b, b_keys, n_b * 8, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "xm_match_values: key copies");
+            ak = d_a;
+            bk = d_b;
+        }
+        // small: [0] AND of codes, [1] OR, [2] pair total, [3] error bits
+        const unsigned long long init[4] = {~0ull, 0ull, 0ull, 0ull};
+        e = cudaMemcpyAsync(small, init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_match_values: init");
+        int32_t* err = (int32_t*)(small + 3);
+        if (n_b > 0) {
+            XM_LAUNCH("k_val_key", grid_of(n_b), kBlock, 0, s, k_val_key, bk, n_b, key_type, codes,
+                      rows, small);
+        }
+        unsigned long long h_ao[2] = {~0ull, 0ull};
+        e = cudaMemcpyAsync(h_ao, small, sizeof(h_ao), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_match_values sync");
+        // bits where the codes differ: the sort covers only those
+        const int end_bit = top_bit(h_ao[0] ^ h_ao[1]);
+        if (n_b > 1 && end_bit > 0) {
+            xm_status r = radix_sort_u64(codes, rows, codes + nb1, rows + nb1, n_b, 0, end_bit, err, s);
+            if (r != XM_OK) return r;
+        }
+        if (n_a > 0)
+            XM_LAUNCH("k_val_probe", grid_of(n_a), kBlock, 0, s, k_val_probe, ak, n_a, key_type,
+                      codes, rows, n_b, R->count, first, R->best_b, R->best_sep);
+        xm_status r = exclusive_scan_i32(R->count, R->pair_off, n_a, (int64_t*)(small + 2), err, s);
+        if (r != XM_OK) return r;
+        unsigned long long h[2] = {0, 0};
+        e = cudaMemcpyAsync(h, small + 2, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_match_values sync");
+        if ((int32_t)h[1] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_match_values: look-back timed out");
+        R->n_pairs = (selection & XM_SEL_ALL) ? (int64_t)h[0] : 0;
+        if (selection & XM_SEL_ALL) {
+            const int64_t np = R->n_pairs > 0 ? R->n_pairs : 1;
+            R->a_row = (int64_t*)dev_alloc(np * (2 * sizeof(int64_t) + sizeof(double)), s);
+            if (!R->a_row) return set_error(XM_ENOMEM, "xm_match_values: %lld pairs", (long long)R->n_pairs);
+            R->b_row = R->a_row + np;
+            R->sep = (double*)(R->b_row + np);
+            if (n_a > 0)
+                XM_LAUNCH("k_val_emit", grid_of(n_a), kBlock, 0, s, k_val_emit, R->count, first,
+                          R->pair_off, rows, n_a, R->a_row, R->b_row, R->sep);
+        }
+        return XM_OK;
+    };
+    const xm_status st = body();
+    dev_free(d_a, s);
+    dev_free(d_b, s);
+    dev_free(codes, s);
+    dev_free(rows, s);
+    dev_free(first, s);
+    dev_free(small, s);
+    if (st != XM_OK) {
+        xm_result_free(R);
+        return st;
+    }
+    *out = R;
+    return XM_OK;
+}

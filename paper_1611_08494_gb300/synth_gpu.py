@@ -281,3 +281,21 @@ def c4(seed=1004, n_b=100_000_000, n_req=4096, a_lo=100, a_hi=1_000_000, device=
                              cap=(c_lon, c_lat, rad), offset_sigma=0.3 * size,
                              max_size=30.0 if per_source else size))
     return dict(name="c4", b_lon=b_lon, b_lat=b_lat, b_frame=EQ, requests=requests)
+
+
+def values(seed=1008, n_a=50_000_000, n_b=200_000_000, device="cuda"):
+    """Exact Value case (paper §2.1): int64 key columns. B holds n_b keys: 90 %
+    distinct ids and 10 % repeats of them (so some keys appear twice or more);
+    A holds n_a keys, 60 % drawn from B's keys (with replacement), 40 %
+    fresh ids that match nothing. Device tensors."""
+    g = generator(seed, device)
+    n_distinct = int(n_b * 0.9)
+    ids = unique_ids(n_distinct + n_a, seed, device)
+    b_ids = ids[:n_distinct]
+    rep = b_ids[torch.randint(0, n_distinct, (n_b - n_distinct,), generator=g, device=device)]
+    b = torch.cat([b_ids, rep])[_permute(g, n_b)].contiguous()
+    n_hit = int(n_a * 0.6)
+    hit = b[torch.randint(0, n_b, (n_hit,), generator=g, device=device)]
+    fresh = ids[n_distinct:n_distinct + (n_a - n_hit)]
+    a = torch.cat([hit, fresh])[_permute(g, n_a)].contiguous()
+    return dict(a_keys=a, b_keys=b)

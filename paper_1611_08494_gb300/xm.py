@@ -107,6 +107,9 @@ xm_join_noalloc = _sig("xm_join_noalloc", _i32, _p, _i32, _i32, _p, _p, _p, _i64
                        ctypes.POINTER(_i64), _p)
 xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
 xm_pick_pairs = _sig("xm_pick_pairs", _i32, _p, _p, _i32, _p, ctypes.POINTER(_p))
+xm_match_values = _sig("xm_match_values", _i32, _p, _i64, _p, _i64, _i32, _i32, _i32, _p,
+                       ctypes.POINTER(_p))
+KEY_INT64, KEY_FLOAT64 = 0, 1
 PICKS = {"best_b": 1, "mutual": 2}
 
 
@@ -294,6 +297,37 @@ class Result:
         if h:
             xm_result_free(h)
             self.handle = None
+
+
+class ValueResult(Result):
+    """The Exact Value case: A and B rows whose key columns hold the same value.
+    ``xm_match_values``. Same views and joins as ``Result``."""
+
+    def __init__(self, a_keys, b_keys, selection=SEL_ALL | SEL_BEST, stream=None):
+        keep = []
+        ak, bk = a_keys, b_keys
+        if isinstance(ak, np.ndarray) or isinstance(bk, np.ndarray):
+            ak, bk = np.ascontiguousarray(ak), np.ascontiguousarray(bk)
+            on_dev = 0
+            pa, pb = ak.ctypes.data, bk.ctypes.data
+            dt = ak.dtype
+        else:
+            ak, bk = ak.contiguous(), bk.contiguous()
+            on_dev = int(ak.is_cuda)
+            pa, pb = ak.data_ptr(), bk.data_ptr()
+            dt = {torch.int64: np.dtype(np.int64), torch.float64: np.dtype(np.float64)}[ak.dtype]
+        keep += [ak, bk]
+        kt = KEY_INT64 if dt == np.int64 else KEY_FLOAT64
+        h = _p()
+        check(xm_match_values(pa, len(ak), pb, len(bk), kt, on_dev, int(selection),
+                              _stream_handle(stream), ctypes.byref(h)), "xm_match_values")
+        self.handle = h.value
+        self.index = None
+        v = ResultView()
+        check(xm_result_get(self.handle, ctypes.byref(v)), "xm_result_get")
+        self.view = v
+        self.n_pairs, self.n_a, self.n_b = v.n_pairs, v.n_a, v.n_b
+        self._keep = keep
 
 
 class Rows:
