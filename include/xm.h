@@ -291,8 +291,8 @@ typedef enum { XM_KEY_INT64 = 0, XM_KEY_FLOAT64 = 1 } xm_key_type;
  * A row then B row with sep_arcsec 0, member counts, and for XM_SEL_BEST the
  * lowest matching B row (sep 0; -1 / NaN when none), so xm_join applies; it
  * holds no positions (xm_pick_pairs refuses it). B keys are sorted once
- * (stable radix sort over the key bits that differ), A keys found by binary
- * search. Synchronises `stream` twice. Errors: XM_EINVAL, XM_ENOMEM, XM_ECUDA,
+ * (stable radix sort over the key bits that differ) and bucketed; each A key
+ * is searched inside one bucket. Synchronises `stream` twice. Errors: XM_EINVAL, XM_ENOMEM, XM_ECUDA,
  * XM_ETIMEOUT. */
 XM_API xm_status xm_match_values(const void* a_keys, int64_t n_a, const void* b_keys, int64_t n_b,
                                  int32_t key_type, int32_t on_device, int32_t selection,

@@ -10,8 +10,10 @@
 //                 payloads, and the AND / OR of all B codes (bits that never
 //                 differ need no sort pass)
 //   radix sort    stable, so equal keys keep ascending B rows (xm_sort.cu)
-//   k_val_probe   per A: the run of equal B codes by binary search; count,
-//                 best B row, first sorted position
+//   k_val_lut     a bucket table over the sorted codes (one bucket per two
+//                 to four keys; long runs of entries by k_val_runs)
+//   k_val_probe   per A: the run of equal B codes, searched inside one
+//                 bucket; count, best B row, first sorted position
 //   prefix sum    pair offsets
 //   k_val_emit    the pairs of each A row
 #include <math.h>
@@ -35,32 +37,95 @@ __device__ __forceinline__ uint64_t key_code(const void* keys, int64_t i, int32_
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// Grid-stride over B (a few blocks per SM), so the AND / OR of all codes
+// costs one pair of atomics per block.
 __global__ void k_val_key(const void* __restrict__ keys, int64_t n, int32_t type,
                           uint64_t* __restrict__ codes, uint32_t* __restrict__ rows,
                           unsigned long long* __restrict__ and_or) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint64_t c = ~0ull, o = 0;
-    if (i < n) {
-        c = key_code(keys, i, type);
+    __shared__ unsigned long long s_and, s_or;
+    if (threadIdx.x == 0) {
+        s_and = ~0ull;
+        s_or = 0ull;
+    }
+    __syncthreads();
+    uint64_t c_and = ~0ull, c_or = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = key_code(keys, i, type);
         codes[i] = c;
         rows[i] = (uint32_t)i;
-        o = c;
+        c_and &= c;
+        c_or |= c;
     }
-    // block-wide AND / OR, one atomic pair per warp
     for (int s = 16; s > 0; s >>= 1) {
-        c &= __shfl_xor_sync(0xffffffffu, c, s);
-        o |= __shfl_xor_sync(0xffffffffu, o, s);
+        c_and &= __shfl_xor_sync(0xffffffffu, c_and, s);
+        c_or |= __shfl_xor_sync(0xffffffffu, c_or, s);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAnd(&and_or[0], (unsigned long long)c);
-        atomicOr(&and_or[1], (unsigned long long)o);
+        atomicAnd(&s_and, (unsigned long long)c_and);
+        atomicOr(&s_or, (unsigned long long)c_or);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAnd(&and_or[0], s_and);
+        atomicOr(&and_or[1], s_or);
     }
 }
 
-// First position in sorted[0, n) whose code is >= c (or > c when upper).
-__device__ __forceinline__ int64_t bound(const uint64_t* __restrict__ sorted, int64_t n, uint64_t c,
-                                         bool upper) {
-    int64_t lo = 0, hi = n;
+// Bucket table over the sorted codes: the codes share every bit above
+// end_bit; bucket(c) = low end_bit bits of c >> shift, and lut[k] is the
+// first sorted position whose bucket reaches k (lut[nb] = n). Runs of
+// entries longer than kRunInline go to a list filled by k_val_runs.
+struct ValLut {
+    uint64_t prefix, mask;  // common high bits, mask of the low end_bit bits
+    uint32_t shift, nb;     // bucket shift, buckets
+    uint32_t* lut;
+};
+
+struct ValRun {
+    int64_t first;
+    uint32_t count, value;
+};
+
+constexpr int64_t kRunInline = 32;
+
+__device__ __forceinline__ uint32_t val_bucket(const ValLut& V, uint64_t c) {
+    return (uint32_t)((c & V.mask) >> V.shift);
+}
+
+__global__ void k_val_lut(const uint64_t* __restrict__ sorted, int64_t n, ValLut V,
+                          ValRun* __restrict__ runs, unsigned long long* __restrict__ n_runs,
+                          long long run_cap, int32_t* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = val_bucket(V, sorted[i]);
+    const int64_t pb = i == 0 ? -1 : (int64_t)val_bucket(V, sorted[i - 1]);
+    auto run = [&](int64_t first, int64_t count, uint32_t value) {
+        if (count <= 0) return;
+        if (count <= kRunInline) {
+            for (int64_t k = 0; k < count; k++) V.lut[first + k] = value;
+        } else {
+            const unsigned long long g = atomicAdd(n_runs, 1ull);
+            if ((long long)g < run_cap) runs[g] = ValRun{first, (uint32_t)count, value};
+            else atomicOr(err, kErrOverflow);
+        }
+    };
+    run(pb + 1, b - pb, (uint32_t)i);
+    if (i == n - 1) run(b + 1, (int64_t)V.nb - b, (uint32_t)n);
+}
+
+__global__ void k_val_runs(const ValRun* __restrict__ runs, const unsigned long long* n_runs,
+                           long long run_cap, uint32_t* __restrict__ lut) {
+    const long long nr = min((long long)*n_runs, run_cap);
+    for (long long r = blockIdx.x; r < nr; r += gridDim.x) {
+        const ValRun R = runs[r];
+        for (uint32_t k = threadIdx.x; k < R.count; k += blockDim.x) lut[R.first + k] = R.value;
+    }
+}
+
+// First position in sorted[lo, hi) whose code is >= c (or > c when upper).
+__device__ __forceinline__ int64_t bound(const uint64_t* __restrict__ sorted, int64_t lo, int64_t hi,
+                                         uint64_t c, bool upper) {
     while (lo < hi) {
         const int64_t mid = lo + ((hi - lo) >> 1);
         const uint64_t v = __ldg(&sorted[mid]);
@@ -72,15 +137,19 @@ __device__ __forceinline__ int64_t bound(const uint64_t* __restrict__ sorted, in
 
 __global__ void k_val_probe(const void* __restrict__ a_keys, int64_t n_a, int32_t type,
                             const uint64_t* __restrict__ sorted, const uint32_t* __restrict__ rows,
-                            int64_t n_b, int32_t* __restrict__ count, int64_t* __restrict__ first,
-                            int64_t* __restrict__ best_b, double* __restrict__ best_sep) {
+                            int64_t n_b, ValLut V, int32_t* __restrict__ count,
+                            int64_t* __restrict__ first, int64_t* __restrict__ best_b,
+                            double* __restrict__ best_sep) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_a) return;
     const uint64_t c = key_code(a_keys, i, type);
     int64_t lo = 0, hi = 0;
-    if (!(type == XM_KEY_FLOAT64 && c == kNaNCode)) {  // (the int64 maximum has that code too)
-        lo = bound(sorted, n_b, c, false);
-        hi = lo < n_b && __ldg(&sorted[lo]) == c ? bound(sorted, n_b, c, true) : lo;
+    // (NaN never matches; the int64 maximum has the same code and does)
+    if (n_b > 0 && !(type == XM_KEY_FLOAT64 && c == kNaNCode) && (c & ~V.mask) == V.prefix) {
+        const uint32_t b = val_bucket(V, c);
+        const int64_t b0 = __ldg(&V.lut[b]), b1 = __ldg(&V.lut[b + 1]);
+        lo = bound(sorted, b0, b1, c, false);
+        hi = lo < b1 && __ldg(&sorted[lo]) == c ? bound(sorted, lo, b1, c, true) : lo;
     }
     const int64_t m = hi - lo;
     count[i] = (int32_t)(m < 2147483647 ? m : 2147483647);
@@ -156,6 +225,8 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
     uint32_t* rows = (uint32_t*)dev_alloc(2 * nb1 * sizeof(uint32_t), s);
     int64_t* first = (int64_t*)dev_alloc(na1 * sizeof(int64_t), s);
     unsigned long long* small = (unsigned long long*)dev_alloc(4 * sizeof(unsigned long long), s);
+    uint32_t* lut = nullptr;
+    ValRun* runs = nullptr;
     auto body = [&]() -> xm_status {
         if (!R->count || !R->pair_off || (want_best && !R->best_b) || !codes || !rows || !first ||
             !small)
@@ -180,8 +251,9 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
         if (e != cudaSuccess) return cuda_fail(e, "xm_match_values: init");
         int32_t* err = (int32_t*)(small + 3);
         if (n_b > 0) {
-            XM_LAUNCH("k_val_key", grid_of(n_b), kBlock, 0, s, k_val_key, bk, n_b, key_type, codes,
-                      rows, small);
+            const unsigned gk = grid_of(n_b) < 8 * 152 ? grid_of(n_b) : 8 * 152;
+            XM_LAUNCH("k_val_key", gk, kBlock, 0, s, k_val_key, bk, n_b, key_type, codes, rows,
+                      small);
         }
         unsigned long long h_ao[2] = {~0ull, 0ull};
         e = cudaMemcpyAsync(h_ao, small, sizeof(h_ao), cudaMemcpyDeviceToHost, s);
@@ -193,9 +265,31 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
             xm_status r = radix_sort_u64(codes, rows, codes + nb1, rows + nb1, n_b, 0, end_bit, err, s);
             if (r != XM_OK) return r;
         }
+        // bucket table: about one bucket per 2-4 keys over the differing bits
+        ValLut V{};
+        V.mask = end_bit >= 64 ? ~0ull : ((1ull << end_bit) - 1);
+        V.prefix = h_ao[0] & ~V.mask;
+        int lg = top_bit((uint64_t)nb1) - 2;
+        lg = lg < 1 ? 1 : (lg > 28 ? 28 : lg);
+        if (lg > end_bit) lg = end_bit > 0 ? end_bit : 0;
+        V.shift = (uint32_t)(end_bit - lg);
+        V.nb = 1u << lg;
+        lut = (uint32_t*)dev_alloc(((size_t)V.nb + 1) * sizeof(uint32_t), s);
+        const long long run_cap = (long long)(V.nb + 1) / (kRunInline + 1) + 16;
+        runs = (ValRun*)dev_alloc(run_cap * sizeof(ValRun) + 16, s);
+        if (!lut || !runs) return set_error(XM_ENOMEM, "xm_match_values: bucket table");
+        V.lut = lut;
+        unsigned long long* n_runs = (unsigned long long*)(runs + run_cap);
+        e = cudaMemsetAsync(n_runs, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_match_values: memset");
+        if (n_b > 0) {
+            XM_LAUNCH("k_val_lut", grid_of(n_b), kBlock, 0, s, k_val_lut, codes, n_b, V, runs,
+                      n_runs, run_cap, err);
+            XM_LAUNCH("k_val_runs", 4 * 152, kBlock, 0, s, k_val_runs, runs, n_runs, run_cap, lut);
+        }
         if (n_a > 0)
             XM_LAUNCH("k_val_probe", grid_of(n_a), kBlock, 0, s, k_val_probe, ak, n_a, key_type,
-                      codes, rows, n_b, R->count, first, R->best_b, R->best_sep);
+                      codes, rows, n_b, V, R->count, first, R->best_b, R->best_sep);
         xm_status r = exclusive_scan_i32(R->count, R->pair_off, n_a, (int64_t*)(small + 2), err, s);
         if (r != XM_OK) return r;
         unsigned long long h[2] = {0, 0};
@@ -203,6 +297,7 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "xm_match_values sync");
         if ((int32_t)h[1] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_match_values: look-back timed out");
+        if ((int32_t)h[1] & kErrOverflow) return set_error(XM_ECUDA, "xm_match_values: run list overflow");
         R->n_pairs = (selection & XM_SEL_ALL) ? (int64_t)h[0] : 0;
         if (selection & XM_SEL_ALL) {
             const int64_t np = R->n_pairs > 0 ? R->n_pairs : 1;
@@ -223,6 +318,8 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
     dev_free(rows, s);
     dev_free(first, s);
     dev_free(small, s);
+    dev_free(lut, s);
+    dev_free(runs, s);
     if (st != XM_OK) {
         xm_result_free(R);
         return st;
