@@ -111,16 +111,15 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const int64_t warp_base = tile_base + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
     int32_t rank[kSortItems];
     // warp-striped: item k of lane l is element warp_base + 32 k + l, so the
-    // (k, lane) order is the input order and ranks are stable. All loads are
-    // issued before the ranking so they overlap.
+    // (k, lane) order is the input order and ranks are stable. All key loads
+    // are issued before the ranking so they overlap; the row payloads are
+    // read only when placed (fewer live registers).
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         const int64_t i = warp_base + 32 * k + lane;
         key[k] = i < n ? keys_in[i] : 0;
-        val[k] = i < n ? vals_in[i] : 0;
     }
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
@@ -210,7 +209,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
             const int32_t p = S.dstart[d] + S.wcount[warp][d] + rank[k];
             S.keys[p] = key[k];
-            S.vals[p] = val[k];
+            S.vals[p] = vals_in[warp_base + 32 * k + lane];
         }
     }
     __syncthreads();
