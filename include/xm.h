@@ -133,7 +133,10 @@ typedef struct {
 typedef struct {
     double zone_height_arcsec;
     int32_t build_fp64;
-    int32_t reserved;
+    int32_t deferred_check; /* 1: return without synchronising; invalid B positions (or a
+                               failed sort) are then reported by every xm_match or
+                               xm_match_batch on the index, which synchronise anyway. The
+                               columns must stay valid until `stream` has run the build. */
 } xm_index_opts;
 
 /* Order in which the scan visits the A sources (results do not depend on it):

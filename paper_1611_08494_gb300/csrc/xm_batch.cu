@@ -640,6 +640,7 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
     cudaEventRecord(ev1, s);
     // ---- one synchronisation: totals, flags, per-request counters and bounds
     std::vector<int64_t> h_small(kSmallWords + 2 * n + 1);
+    int32_t h_berr = 0;  // a deferred index build's error bits
     if (st == XM_OK) {
         e = cudaMemcpyAsync(h_small.data(), B.small, h_small.size() * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s);
@@ -648,8 +649,11 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
             e = cudaMemcpyAsync(out->bounds.data(), B.bounds, 4 * n * sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, s);
         }
+        if (e == cudaSuccess && X->build_err)
+            e = cudaMemcpyAsync(&h_berr, X->build_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "batch sync");
+        if (st == XM_OK && h_berr) st = index_build_status(h_berr);
     }
     float ms = 0.f;
     if (st == XM_OK && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) out->device_ms = ms;

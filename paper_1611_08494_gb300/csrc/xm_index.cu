@@ -288,6 +288,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     X->h_arcsec = 648000.0 / X->nz;
     X->h = kPi / X->nz;
     const bool fp64 = opts && opts->build_fp64;
+    const bool deferred = opts && opts->deferred_check;
     const int64_t nn = n > 0 ? n : 1;
 
     xm_status st = XM_OK;
@@ -398,12 +399,16 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         };
         st = body();
         if (st != XM_OK) break;
+        if (deferred) {  // the error word stays with the index, read by its first match
+            X->build_err = err;
+            err = nullptr;
+            break;
+        }
         e = cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { fail(cuda_fail(e, "xm_build_index sync")); break; }
-        if (h_err & kErrCoord) { fail(set_error(XM_EINVAL, "B: NaN/inf or |lat| > 90")); break; }
-        if (h_err & kErrTimeout) { fail(set_error(XM_ETIMEOUT, "index sort: look-back timed out")); break; }
-        if (h_err & kErrOverflow) { fail(set_error(XM_ECUDA, "index bucket tables: run list overflow")); break; }
+        const xm_status bs = index_build_status(h_err);
+        if (bs != XM_OK) { fail(bs); break; }
     } while (0);
 
     dev_free(d_lon, s);
@@ -421,6 +426,13 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     return XM_OK;
 }
 
+xm_status xm::index_build_status(int32_t bits) {
+    if (bits & kErrCoord) return set_error(XM_EINVAL, "B: NaN/inf or |lat| > 90");
+    if (bits & kErrTimeout) return set_error(XM_ETIMEOUT, "index sort: look-back timed out");
+    if (bits & kErrOverflow) return set_error(XM_ECUDA, "index bucket tables: run list overflow");
+    return XM_OK;
+}
+
 extern "C" xm_status xm_index_free(xm_index* X) {
     if (!X) return XM_OK;
     cudaStream_t s = nullptr;
@@ -431,6 +443,7 @@ extern "C" xm_status xm_index_free(xm_index* X) {
     dev_free(X->zone_start, s);
     dev_free(X->zones, s);
     dev_free(X->lut, s);
+    dev_free(X->build_err, s);
     delete X;
     return XM_OK;
 }

@@ -361,6 +361,10 @@ cudaError_t launch_end(const char* name, cudaStream_t s);
 xm_status cuda_fail(cudaError_t e, const char* what);
 xm_status set_error(xm_status s, const char* fmt, ...);
 
+// The error status of a deferred index build from its error bits (host
+// copy), XM_OK when clean.
+xm_status index_build_status(int32_t bits);
+
 // Device primitives (xm_sort.cu).
 // Stable LSD radix sort of (keys, vals) on key bits [begin_bit, end_bit).
 // Sorted data ends in (keys, vals); (tk, tv) are scratch of the same sizes.
@@ -421,6 +425,7 @@ struct xm_index {
     uint32_t* lut;
     int64_t lut_n;
     int64_t bytes;
+    int32_t* build_err;  // error bits of a build whose check was deferred (else NULL)
     xm::IndexGeom geom() const {
         return xm::IndexGeom{rec, pos, px, py, pz, zones, lut, nz, h, (float)h};
     }

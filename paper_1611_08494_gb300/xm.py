@@ -49,7 +49,7 @@ class Region(ctypes.Structure):
 
 
 class IndexOpts(ctypes.Structure):
-    _fields_ = [("zone_height_arcsec", _f64), ("build_fp64", _i32), ("reserved", _i32)]
+    _fields_ = [("zone_height_arcsec", _f64), ("build_fp64", _i32), ("deferred_check", _i32)]
 
 
 class MatchOpts(ctypes.Structure):
@@ -194,15 +194,16 @@ class Index:
     """Resident B index (paper §2.3). ``xm_build_index``."""
 
     def __init__(self, lon, lat, frame=EQ, ids=None, zone_height_arcsec=0.0, build_fp64=False,
-                 stream=None):
+                 deferred_check=False, stream=None):
         cols, keep = columns(lon, lat, frame, ids)
-        opts = IndexOpts(float(zone_height_arcsec), int(bool(build_fp64)), 0)
+        opts = IndexOpts(float(zone_height_arcsec), int(bool(build_fp64)), int(bool(deferred_check)))
         h = _p()
         check(xm_build_index(ctypes.byref(cols), ctypes.byref(opts), _stream_handle(stream),
                              ctypes.byref(h)), "xm_build_index")
         self.handle = h.value
         self.n = cols.n
         self.frame = frame
+        self._keep = keep  # the build may still be reading them (deferred_check)
 
     def info(self):
         n, z, hb = _i64(), _i64(), _i64()

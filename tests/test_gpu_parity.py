@@ -416,3 +416,21 @@ def test_pick_needs_the_selections(xm, c1):
     res.pick("best_b")
     with pytest.raises(xm.XMError, match="EINVAL"):
         res.pick("mutual")
+
+
+def test_deferred_index_check(xm):
+    """A build with the check deferred returns at once; invalid B positions
+    then fail the match (and the batch) that uses the index."""
+    good = _cuda([10.0, 11.0, 12.0])
+    lat_bad = _cuda([0.0, np.nan, 0.0])
+    idx = xm.Index(good, lat_bad, deferred_check=True)
+    with pytest.raises(xm.XMError, match="EINVAL.*B:"):
+        xm.Result(idx, good, _cuda([0.0, 0.0, 0.0]), shape=0, a=1.0)
+    with pytest.raises(xm.XMError, match="EINVAL"):
+        xm.Batch(idx, [dict(lon=good, lat=_cuda([0.0, 0.0, 0.0]), a=1.0)])
+    # a clean deferred build matches like a checked one
+    d = synth.c1()
+    ref = oracle_ref(d)
+    idx = xm.Index(_cuda(d["b_lon"]), _cuda(d["b_lat"]), deferred_check=True)
+    res = xm.Result(idx, _cuda(d["a_lon"]), _cuda(d["a_lat"]), **d["region"])
+    check_pairs(res, ref)
