@@ -247,9 +247,11 @@ XM_API xm_status xm_result_get(const xm_result* result, xm_result_view* view);
  * (a_row, b_row, sep_arcsec); a missing side is -1 / NaN. A source counts as
  * matched when it appears in the selected pairs. Row order: every row that
  * carries an A source in ascending (a_row, b_row), then the rows of unmatched
- * B sources in ascending b_row. Synchronises `stream` once.
+ * B sources in ascending b_row. Does not synchronise: the rows are written on
+ * `stream` into room for the most rows the join can have, and the first
+ * xm_rows_get reads the row count (one synchronisation of that stream).
  * Errors: XM_EINVAL (selection not in the result, bad join type), XM_ENOMEM,
- * XM_ECUDA. */
+ * XM_ECUDA; XM_ETIMEOUT from xm_rows_get. */
 XM_API xm_status xm_join(const xm_result* result, int32_t selection, int32_t join_type,
                          void* stream, xm_rows** out);
 XM_API xm_status xm_rows_free(xm_rows* rows);

@@ -910,9 +910,10 @@ extern "C" xm_status xm_batch_join(const xm_batch* X, int64_t r, void* stream, x
     if (st == XM_OK) st = exclusive_scan_i32(view.count, rel, view.n_a, nullptr, err, s);
     view.pair_off = rel;
     if (st == XM_OK) st = xm_join(&view, X->join_sel[r], X->join_type[r], stream, out);
-    if (st == XM_OK) {  // xm_join synchronised the stream: the scan's error bits are final
+    if (st == XM_OK) {  // the offsets' scan error bits
         int32_t h_err = 0;
-        e = cudaMemcpy(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "xm_batch_join");
         else if (h_err & kErrTimeout) st = set_error(XM_ETIMEOUT, "xm_batch_join: scan look-back timed out");
         if (st != XM_OK) {

@@ -452,4 +452,10 @@ struct xm_rows {
     int64_t n, n_unmatched_a, n_unmatched_b;
     int64_t *a_row, *b_row;
     double* sep;
+    // a join whose counts are still on the device: [0] A-side rows,
+    // [1] unmatched B, [2] unmatched A, [4] error bits; read (one
+    // synchronisation of `stream`) by the first xm_rows_get
+    int64_t* pending;
+    cudaStream_t stream;
+    int32_t with_un_b;
 };

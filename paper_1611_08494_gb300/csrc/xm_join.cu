@@ -12,6 +12,7 @@
 // B counts per 32-row word and their prefix sum, then two writers.
 #include <math.h>
 
+#include <mutex>
 #include <new>
 
 #include "xm_internal.cuh"
@@ -109,11 +110,13 @@ __global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __r
     os[o] = ps[p];
 }
 
+// B-only rows after the A-side rows: base_ptr (device) holds their count.
 __global__ void k_write_b(const uint32_t* __restrict__ bits, const int64_t* __restrict__ word_off,
-                          int64_t nB, int64_t base, int64_t* __restrict__ oa,
+                          int64_t nB, const int64_t* __restrict__ base_ptr, int64_t* __restrict__ oa,
                           int64_t* __restrict__ ob, double* __restrict__ os) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nB) return;
+    const int64_t base = *base_ptr;
     int64_t w = j >> 5;
     uint32_t un = ~bits[w] & word_valid(w, nB);
     uint32_t bit = 1u << (j & 31);
@@ -254,7 +257,8 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
                                                  (int)with_pairs, (int)with_un_a, 0, a_row, b_row,
                                                  sep);
     if (with_un_b && nB > 0)
-        k_write_b<<<grid_for(nB), kBlock, 0, s>>>(S->bits, S->word_off, nB, total_a, a_row, b_row, sep);
+        k_write_b<<<grid_for(nB), kBlock, 0, s>>>(S->bits, S->word_off, nB, &S->small[0], a_row,
+                                                 b_row, sep);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "xm_join_noalloc launch");
     return XM_OK;
@@ -264,8 +268,28 @@ using namespace xm;
 
 static void free_rows(xm_rows* J) {
     if (!J) return;
-    dev_free(J->a_row, nullptr);
+    dev_free(J->a_row, J->pending ? J->stream : nullptr);
+    dev_free(J->pending, J->pending ? J->stream : nullptr);
     delete J;
+}
+
+// Reads the counts of a join launched without synchronising (once).
+static std::mutex g_rows_mu;
+
+static xm_status resolve_rows(xm_rows* J) {
+    std::lock_guard<std::mutex> g(g_rows_mu);
+    if (!J->pending) return XM_OK;
+    int64_t h[5];
+    cudaError_t e = cudaMemcpyAsync(h, J->pending, sizeof(h), cudaMemcpyDeviceToHost, J->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(J->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "xm_rows_get sync");
+    if ((int32_t)h[4] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_join: scan look-back timed out");
+    J->n_unmatched_a = h[2];
+    J->n_unmatched_b = h[1];
+    J->n = h[0] + (J->with_un_b ? h[1] : 0);
+    dev_free(J->pending, J->stream);
+    J->pending = nullptr;
+    return XM_OK;
 }
 
 extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join_type,
@@ -297,7 +321,12 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
     int64_t* row_off = (int64_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int64_t), s);
     int32_t* wcount = (int32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int32_t), s);
     int64_t* word_off = (int64_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int64_t), s);
-    int64_t* small = (int64_t*)dev_alloc(5 * sizeof(int64_t), s);  // [4]: error bits
+    // counts read later by xm_rows_get: [0] A-side rows, [1] unmatched B,
+    // [2] unmatched A, [4] error bits
+    int64_t* small = (int64_t*)dev_alloc(5 * sizeof(int64_t), s);
+    J->pending = small;
+    J->stream = s;
+    J->with_un_b = with_un_b;
     auto body = [&]() -> xm_status {
         if (!bits || !rows || !row_off || !wcount || !word_off || !small)
             return set_error(XM_ENOMEM, "xm_join: work buffers");
@@ -322,18 +351,13 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
                       nwords, nB, wcount);
         r = exclusive_scan_i32(wcount, word_off, nwords, small + 1, err, s);
         if (r != XM_OK) return r;
-        int64_t h[5];
-        e = cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "xm_join sync");
-        if ((int32_t)h[4] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_join: scan look-back timed out");
-        const int64_t total_a = h[0], un_b = h[1];
-        J->n_unmatched_a = h[2];
-        J->n_unmatched_b = un_b;
-        J->n = total_a + (with_un_b ? un_b : 0);
-        int64_t nr = J->n > 0 ? J->n : 1;
+        // rows are written at device-side offsets into room for the most
+        // rows the join can have; the count is read by xm_rows_get
+        const int64_t a_side = (with_pairs ? (sel_all ? R->n_pairs : nA) : 0) + (with_un_a ? nA : 0);
+        const int64_t bound = a_side + (with_un_b ? nB : 0);
+        int64_t nr = bound > 0 ? bound : 1;
         J->a_row = (int64_t*)dev_alloc(nr * (2 * sizeof(int64_t) + sizeof(double)), s);
-        if (!J->a_row) return set_error(XM_ENOMEM, "xm_join: %lld rows", (long long)J->n);
+        if (!J->a_row) return set_error(XM_ENOMEM, "xm_join: %lld rows", (long long)bound);
         J->b_row = J->a_row + nr;
         J->sep = (double*)(J->b_row + nr);
         const int pairs_apart = sel_all && with_pairs && R->n_pairs > 0 && R->a_row;
@@ -347,7 +371,7 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
                       (int)with_pairs, (int)with_un_a, pairs_apart, J->a_row, J->b_row, J->sep);
         if (with_un_b && nB > 0)
             XM_LAUNCH("k_write_b", grid_for(nB), kBlock, 0, s, k_write_b, bits, word_off, nB,
-                      total_a, J->a_row, J->b_row, J->sep);
+                      small + 0, J->a_row, J->b_row, J->sep);
         return XM_OK;
     };
     xm_status st = body();
@@ -356,9 +380,8 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
     dev_free(row_off, s);
     dev_free(wcount, s);
     dev_free(word_off, s);
-    dev_free(small, s);
     if (st != XM_OK) {
-        free_rows(J);
+        free_rows(J);  // (frees the counts too)
         return st;
     }
     *out = J;
@@ -372,6 +395,8 @@ extern "C" xm_status xm_rows_free(xm_rows* J) {
 
 extern "C" xm_status xm_rows_get(const xm_rows* J, xm_rows_view* v) {
     if (!J || !v) return set_error(XM_EINVAL, "xm_rows_get: NULL argument");
+    const xm_status st = resolve_rows(const_cast<xm_rows*>(J));
+    if (st != XM_OK) return st;
     v->n = J->n;
     v->a_row = J->a_row;
     v->b_row = J->b_row;

@@ -286,8 +286,6 @@ class Result:
         v = RowsView()
         check(xm_rows_get(rows.handle, ctypes.byref(v)), "xm_rows_get")
         rows.view = v
-        rows.n = v.n
-        rows.n_unmatched_a, rows.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
         return rows
 
     def join(self, join_type: str, selection=SEL_ALL, stream=None) -> "Rows":
@@ -332,7 +330,9 @@ class ValueResult(Result):
 
 
 class Rows:
-    """Rows of one join type (paper §2.2). ``xm_join``."""
+    """Rows of one join type (paper §2.2). ``xm_join``. The join runs
+    without a host synchronisation; the first access to the counts or the
+    rows reads them (``xm_rows_get``)."""
 
     def __init__(self, result: Result, join_type: str, selection=SEL_ALL, stream=None):
         h = _p()
@@ -340,11 +340,31 @@ class Rows:
                       ctypes.byref(h)), "xm_join")
         self.handle = h.value
         self.result = result
-        v = RowsView()
-        check(xm_rows_get(self.handle, ctypes.byref(v)), "xm_rows_get")
-        self.view = v
-        self.n = v.n
-        self.n_unmatched_a, self.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
+        self._view = None
+
+    @property
+    def view(self):
+        if self._view is None:
+            v = RowsView()
+            check(xm_rows_get(self.handle, ctypes.byref(v)), "xm_rows_get")
+            self._view = v
+        return self._view
+
+    @view.setter
+    def view(self, v):
+        self._view = v
+
+    @property
+    def n(self):
+        return self.view.n
+
+    @property
+    def n_unmatched_a(self):
+        return self.view.n_unmatched_a
+
+    @property
+    def n_unmatched_b(self):
+        return self.view.n_unmatched_b
 
     @property
     def a_row(self):
@@ -493,8 +513,6 @@ class Batch:
         v = RowsView()
         check(xm_rows_get(rows.handle, ctypes.byref(v)), "xm_rows_get")
         rows.view = v
-        rows.n = v.n
-        rows.n_unmatched_a, rows.n_unmatched_b = v.n_unmatched_a, v.n_unmatched_b
         return rows
 
     def __del__(self):
