@@ -547,7 +547,7 @@ def values_leg(args, xm, torch):
                           sorted(prof.items(), key=lambda kv: -kv[1][0])[:6]}}
     sw = prof.get("k_onesweep")
     if sw:
-        alg = 24.0 * n_b  # key and row read and written per pass
+        alg = 24.0 * xm.stats()["sort_key_passes"] / sw[1]  # key and row, read and written
         ach = alg / (sw[0] / sw[1] * 1e-3) / 1e9
         out["roofline"] = {"kernel": "k_onesweep", "bound": "hbm", "algorithmic_bytes": alg,
                            "ms_per_launch": sw[0] / sw[1], "achieved": ach, "peak": peak,
@@ -705,22 +705,18 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "_source": "fallback"}
 
 
-def sort_passes(zone_height_arcsec):
-    """Digit passes of the (zone, RA) sort: bits 8 .. 32 + bits(nz - 1)."""
-    nz = int(np.ceil(648000.0 / zone_height_arcsec - 1e-9))
-    return (32 + int(nz - 1).bit_length() - 8 + 7) // 8
-
-
 def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, zone_h):
-    """Bytes the method must move per launch of a kernel:
-    k_onesweep   per key and pass 8 B key + 4 B row, read and written (B and A
-                 sorts, the same number of passes each);
+    """Bytes the method must move per launch of a kernel (averaged over the
+    launches, so achieved = all bytes / all kernel time):
+    k_onesweep   per key and pass 8 B key + 4 B row, read and written, over
+                 the passes that ran (the library counts keys x passes; an
+                 index sort planned to fewer passes launches the rest empty);
     k_scan_fp32_count  per A 16 B position + 24 B region columns + 16 B best
                  row, per candidate 12 B (offsets + RA key);
     k_gather_b   per B 16 B position read + 16 B record + 16 B position
                  written."""
     if kernel == "k_onesweep":
-        return steps * sort_passes(zone_h) * 24 * (n_b + n_a) / launches
+        return 24.0 * st["sort_key_passes"] / launches
     if kernel == "k_scan_fp32_count":
         return n_a * (16 + 24 + 16) + st["candidates"] / steps * 12
     if kernel == "k_gather_b":

@@ -166,6 +166,7 @@ typedef struct {
     uint64_t members;      /* (A, B) memberships found */
     uint64_t tie_resolved; /* A sources whose best pair was decided in FP64 */
     uint64_t kernel_launches;
+    uint64_t sort_key_passes; /* keys moved by radix-sort passes (keys x passes) */
 } xm_stats;
 
 /* ---- status and configuration ------------------------------------------ */

@@ -8,7 +8,9 @@
 //                 (once per device and zone count, then copied)
 //   k_ingest_b    per source, input order: validity, fixed-point position,
 //                 sort key; exact position kept by row
-//   radix sort    (xm_sort.cu)
+//   index sort    (xm_sort.cu) on a plan k_ingest_b narrows: the zone range
+//                 and the RA bits that vary, so a catalogue of a small sky
+//                 area sorts in fewer passes
 //   k_zone_start  first sorted source of each zone (binary search)
 //   k_zone_rows   rows of each zone, size of its RA bucket table (one to two
 //                 buckets per source); prefix sum; k_zone_lut the offsets
@@ -54,25 +56,66 @@ __global__ void k_zone_geom(int32_t nz, ZoneInfo* __restrict__ zones) {
     zones[z] = Z;
 }
 
-__global__ void k_ingest_b(const double* __restrict__ lon, const double* __restrict__ lat,
-                           int64_t n, int32_t nz, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ vals, double2* __restrict__ pos,
-                           double* __restrict__ px, double* __restrict__ py,
-                           double* __restrict__ pz, int32_t* err) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double lo = lon[i], la = lat[i];
-    if (!coord_ok(lo, la)) {
-        atomicOr(err, kErrCoord);
-        lo = 0.0;
-        la = 0.0;
+// Narrows the sort plan to a block's keys: warp reductions, one lane per warp
+// through shared memory, then an atomic only where the block widens what the
+// plan already holds (a stale read costs one redundant atomic, never a miss).
+__device__ __forceinline__ void plan_accumulate(bool has, uint32_t z, uint32_t ra,
+                                                SortPlan* plan) {
+    __shared__ uint32_t red[4][kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t zlo = __reduce_min_sync(0xFFFFFFFFu, has ? z : 0xFFFFFFFFu);
+    const uint32_t zhi = __reduce_max_sync(0xFFFFFFFFu, has ? z : 0u);
+    const uint32_t rand_ = __reduce_and_sync(0xFFFFFFFFu, has ? ra : 0xFFFFFFFFu);
+    const uint32_t ror = __reduce_or_sync(0xFFFFFFFFu, has ? ra : 0u);
+    if (lane == 0) {
+        red[0][warp] = zlo;
+        red[1][warp] = zhi;
+        red[2][warp] = rand_;
+        red[3][warp] = ror;
     }
-    lo = lon_mod360(lo);
-    const PosKey k = pos_key(lo, la, nz);
-    keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
-    vals[i] = (uint32_t)i;
-    pos[i] = make_double2(lo, la);
-    if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = red[0][0], b = red[1][0], c = red[2][0], d = red[3][0];
+        for (int w = 1; w < kBlock / 32; w++) {
+            a = min(a, red[0][w]);
+            b = max(b, red[1][w]);
+            c &= red[2][w];
+            d |= red[3][w];
+        }
+        const volatile SortPlan* vp = plan;
+        if (a < vp->zmin) atomicMin(&plan->zmin, a);
+        if (b > vp->zmax) atomicMax(&plan->zmax, b);
+        if (~c & vp->ra_and) atomicAnd(&plan->ra_and, c);
+        if (d & ~vp->ra_or) atomicOr(&plan->ra_or, d);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_ingest_b(
+    const double* __restrict__ lon, const double* __restrict__ lat, int64_t n, int32_t nz,
+    uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, double2* __restrict__ pos,
+    double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz, SortPlan* plan,
+    int32_t* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = i < n;
+    uint32_t z = 0, ra = 0;
+    if (has) {
+        double lo = lon[i], la = lat[i];
+        if (!coord_ok(lo, la)) {
+            atomicOr(err, kErrCoord);
+            lo = 0.0;
+            la = 0.0;
+        }
+        lo = lon_mod360(lo);
+        const PosKey k = pos_key(lo, la, nz);
+        z = (uint32_t)k.z;
+        const uint32_t rk = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
+        ra = rk >> kSortBeginBit;
+        keys[i] = ((uint64_t)z << 32) | rk;
+        vals[i] = (uint32_t)i;
+        pos[i] = make_double2(lo, la);
+        if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
+    }
+    plan_accumulate(has, z, ra, plan);
 }
 
 // The index record of a source at (lon, lat): float32 offsets in the tangent
@@ -94,10 +137,22 @@ __device__ __forceinline__ BRec make_brec(double lon, double lat, int32_t row, i
     return r;
 }
 
-__global__ void k_zone_start(const uint64_t* __restrict__ keys, int64_t n, int32_t nz,
-                             int64_t* __restrict__ zone_start) {
+// The sorted keys and rows of an index build: where the plan's passes left
+// them.
+struct Sorted {
+    const uint64_t* k0;
+    const uint32_t* v0;
+    const uint64_t* k1;
+    const uint32_t* v1;
+    const SortPlan* plan;
+    __device__ __forceinline__ const uint64_t* keys() const { return sorted_in_scratch(plan) ? k1 : k0; }
+    __device__ __forceinline__ const uint32_t* vals() const { return sorted_in_scratch(plan) ? v1 : v0; }
+};
+
+__global__ void k_zone_start(Sorted S, int64_t n, int32_t nz, int64_t* __restrict__ zone_start) {
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z > nz) return;
+    const uint64_t* __restrict__ keys = S.keys();
     const uint64_t target = (uint64_t)z << 32;
     int64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -108,11 +163,11 @@ __global__ void k_zone_start(const uint64_t* __restrict__ keys, int64_t n, int32
     zone_start[z] = lo;
 }
 
-__global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start,
-                            const uint64_t* __restrict__ keys, ZoneInfo* __restrict__ zones,
-                            int32_t* __restrict__ lut_cnt) {
+__global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, Sorted S,
+                            ZoneInfo* __restrict__ zones, int32_t* __restrict__ lut_cnt) {
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
+    const uint64_t* __restrict__ keys = S.keys();
     ZoneInfo& Z = zones[z];
     Z.start = zone_start[z];
     Z.end = zone_start[z + 1];
@@ -166,14 +221,15 @@ constexpr uint32_t kGapInline = 32;  // longest run written by the finding threa
 // row's bucket up to its own; the zone's last row also writes the entries
 // after its bucket (the value: the zone's row count). Runs longer than
 // kGapInline go to a list for k_gap_fill.
-__global__ void k_gather_b(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                           int64_t n, const double2* __restrict__ pos, int32_t nz, float h_f,
+__global__ void k_gather_b(Sorted S, int64_t n, const double2* __restrict__ pos, int32_t nz, float h_f,
                            const ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut,
                            BRec* __restrict__ rec, LutGap* __restrict__ gaps,
                            unsigned long long* __restrict__ n_gaps, long long gap_cap,
                            int32_t* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const uint64_t* __restrict__ keys = S.keys();
+    const uint32_t* __restrict__ vals = S.vals();
     const uint64_t key = keys[i];
     const ZoneInfo& Z = zones[key >> 32];
     const uint32_t row = vals[i];
@@ -297,6 +353,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     uint64_t *keys = nullptr, *tk = nullptr;
     uint32_t *vals = nullptr, *tv = nullptr;
     int32_t* err = nullptr;
+    SortPlan* plan = nullptr;
     int32_t* lut_cnt = nullptr;
     int64_t* lut_off = nullptr;
     LutGap* gaps = nullptr;
@@ -346,6 +403,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
         vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
         err = (int32_t*)dev_alloc(sizeof(int32_t), s);
+        plan = (SortPlan*)dev_alloc(sizeof(SortPlan), s);
         lut_cnt = (int32_t*)dev_alloc(X->nz * sizeof(int32_t), s);
         lut_off = (int64_t*)dev_alloc(X->nz * sizeof(int64_t), s);
         // bucket tables: a zone of m rows has at most max(2, 2m) + 1 entries
@@ -356,7 +414,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         gap_cap = X->lut_n / (kGapInline + 1) + 2 * (int64_t)X->nz + 16;
         gaps = (LutGap*)dev_alloc(gap_cap * sizeof(LutGap) + 16, s);
         n_gaps = gaps ? (unsigned long long*)(gaps + gap_cap) : nullptr;
-        if (!keys || !vals || !err || !lut_cnt || !lut_off || !X->lut || !gaps) {
+        if (!keys || !vals || !err || !plan || !lut_cnt || !lut_off || !X->lut || !gaps) {
             fail(set_error(XM_ENOMEM, "index build buffers"));
             break;
         }
@@ -372,25 +430,27 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             const unsigned gz = (unsigned)((X->nz + kBlock) / kBlock);
             xm_status rg = zone_geometry(X->nz, X->zones, s);
             if (rg != XM_OK) return rg;
+            xm_status r = sort_plan_init(plan, s);
+            if (r != XM_OK) return r;
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
                 XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz, keys, vals,
-                          X->pos, X->px, X->py, X->pz, err);
-                xm_status r = radix_sort_u64(keys, vals, tk, tv, n, kSortBeginBit,
-                                             32 + bits_for(X->nz - 1), err, s);
-                if (r != XM_OK) return r;
+                          X->pos, X->px, X->py, X->pz, plan, err);
             }
-            XM_LAUNCH("k_zone_start", gz, kBlock, 0, s, k_zone_start, keys, n, X->nz,
-                      X->zone_start);
-            XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, keys,
-                      X->zones,
-                      lut_cnt);
-            xm_status r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, err, s);
+            // the virtual key: zone offset above the RA bits that vary
+            const int max_passes = (bits_for(X->nz - 1) + 32 - kSortBeginBit + 7) / 8;
+            r = index_sort(keys, vals, tk, tv, n, plan, max_passes, err, s);
+            if (r != XM_OK) return r;
+            const Sorted S{keys, vals, tk, tv, plan};
+            XM_LAUNCH("k_zone_start", gz, kBlock, 0, s, k_zone_start, S, n, X->nz, X->zone_start);
+            XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, S,
+                      X->zones, lut_cnt);
+            r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, err, s);
             if (r != XM_OK) return r;
             XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->lut);
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, keys, vals, n, X->pos, X->nz,
+                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, S, n, X->pos, X->nz,
                           G.h_f, X->zones, X->lut, X->rec, gaps, n_gaps, gap_cap, err);
                 XM_LAUNCH("k_gap_fill", 4 * 152, kBlock, 0, s, k_gap_fill, gaps, n_gaps, gap_cap,
                           X->lut);
@@ -415,6 +475,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     dev_free(keys, s);
     dev_free(vals, s);
     dev_free(err, s);
+    dev_free(plan, s);
     dev_free(lut_cnt, s);
     dev_free(lut_off, s);
     dev_free(gaps, s);

@@ -377,6 +377,29 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
 // before capturing a stream that sorts).
 void radix_sort_prepare();
 
+// The index sort's plan, decided on the device from the keys themselves:
+// the keys (zone << 32 | RA key) are sorted on the virtual key
+// ((zone - zmin) << rb) | (RA key >> 8 & (2^rb - 1)), where the RA bits
+// above rb are the same in every key, so its order is the key order and it
+// needs only `active` 8-bit passes (trailing passes are skipped).
+struct SortPlan {
+    uint32_t zmin, zmax;      // zone range (atomicMin / atomicMax)
+    uint32_t ra_and, ra_or;   // AND / OR of the 24-bit RA fields
+    uint32_t rb, active;      // RA bits kept, passes needed
+};
+
+// Sets a plan to the empty ranges the key kernel narrows.
+xm_status sort_plan_init(SortPlan* plan, cudaStream_t s);
+
+// Sorts (keys, vals) of an index build by the plan's virtual key with up to
+// `max_passes` launches (each does nothing past plan->active). The sorted
+// data ends in (keys, vals) when plan->active is even, else in (tk, tv);
+// sorted_in_scratch() tells which on the device.
+xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
+                     SortPlan* plan, int max_passes, int32_t* err, cudaStream_t s);
+
+__device__ __forceinline__ bool sorted_in_scratch(const SortPlan* plan) { return plan->active & 1; }
+
 // Sort keys file sources by zone, then by RA to 2^-24 of a turn (0.08
 // arcsec): the low 8 bits of the RA key are dropped, so the sort starts at
 // bit 8. Search windows are widened by one such quantum.

@@ -46,6 +46,57 @@ __global__ void __launch_bounds__(kSortThreads) k_all_hist(const uint64_t* __res
     }
 }
 
+// The virtual key of an index key under a plan.
+__device__ __forceinline__ uint64_t plan_key(const SortPlan& P, uint64_t key) {
+    const uint32_t z = (uint32_t)(key >> 32);
+    const uint32_t ra = (uint32_t)key >> kSortBeginBit;
+    const uint32_t rmask = P.rb >= 32 ? 0xFFFFFFFFu : ((1u << P.rb) - 1u);
+    return ((uint64_t)(z - P.zmin) << P.rb) | (ra & rmask);
+}
+
+// Histograms of the plan's virtual-key digits, as k_all_hist.
+__global__ void __launch_bounds__(kSortThreads) k_plan_hist(const uint64_t* __restrict__ keys,
+                                                            int64_t n, const SortPlan* plan,
+                                                            int passes,
+                                                            unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t h[8][kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const SortPlan P = *plan;
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const uint64_t k = plan_key(P, keys[i]);
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&hist[i], (unsigned long long)v);
+    }
+}
+
+__global__ void k_plan_init(SortPlan* plan) {
+    *plan = SortPlan{0xFFFFFFFFu, 0u, 0xFFFFFFFFu, 0u, 0u, 0u};
+}
+
+// The plan from the accumulated ranges: bits of the zone offset and of the
+// varying RA bits, passes needed (none for no keys).
+__global__ void k_plan_finish(SortPlan* plan) {
+    SortPlan P = *plan;
+    if (P.zmin > P.zmax) {
+        P.rb = 0;
+        P.active = 0;
+        *plan = P;
+        return;
+    }
+    const uint32_t ra_diff = P.ra_and ^ P.ra_or;
+    P.rb = ra_diff ? 32 - __clz(ra_diff) : 0;
+    const uint32_t zd = P.zmax - P.zmin;
+    const uint32_t zb = zd ? 32 - __clz(zd) : 0;
+    P.active = (P.rb + zb + 7) / 8;
+    *plan = P;
+}
+
 // Look-back status word of one (tile, digit): flag in the top two bits,
 // count (or inclusive prefix) below.
 constexpr uint64_t kStAgg = 1ull << 62;   // tile's own count is available
@@ -85,11 +136,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
     int shift, const unsigned long long* __restrict__ hist, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    int32_t* err) {
+    int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats) {
+    // with a plan: the digit of pass `pass` of the virtual key, and nothing
+    // to do past the passes the plan needs (uniform over the grid)
+    SortPlan P{};
+    const bool planned = plan != nullptr;
+    if (planned) {
+        P = *plan;
+        if (pass >= (int)P.active) return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) S.tile = (int)atomicAdd(tile_counter, 1u);
+    if (threadIdx.x == 0) {
+        S.tile = (int)atomicAdd(tile_counter, 1u);
+        if (S.tile == 0 && stats) atomicAdd(&stats[5], (unsigned long long)n);  // keys this pass
+    }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
     if (threadIdx.x < 32) {  // exclusive scan of the pass histogram (256 digits)
         int64_t v[8], sum = 0;
@@ -127,7 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
         rank[k] = -1;
         if (valid) {
-            const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
+            const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
             const uint32_t peers = __match_any_sync(vmask, d);
             const int32_t before = S.wcount[warp][d];
             rank[k] = before + __popc(peers & lt_mask);
@@ -206,7 +268,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         if (rank[k] >= 0) {
-            const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFF;
+            const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
             const int32_t p = S.dstart[d] + S.wcount[warp][d] + rank[k];
             S.keys[p] = key[k];
             S.vals[p] = vals_in[warp_base + 32 * k + lane];
@@ -217,7 +279,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     if (valid_n > kSortTile) valid_n = kSortTile;
     for (int p = threadIdx.x; p < valid_n; p += kSortThreads) {
         const uint64_t kk = S.keys[p];
-        const uint32_t d = (uint32_t)(kk >> shift) & 0xFF;
+        const uint32_t d = (uint32_t)((planned ? plan_key(P, kk) : kk) >> shift) & 0xFF;
         const int64_t g = S.gstart[d] + (p - S.dstart[d]);
         keys_out[g] = kk;
         vals_out[g] = S.vals[p];
@@ -459,6 +521,54 @@ void radix_sort_prepare() {
     done[dev] = true;
 }
 
+xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
+    XM_LAUNCH("k_plan_init", 1, 1, 0, s, k_plan_init, plan);
+    return XM_OK;
+}
+
+xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
+                     SortPlan* plan, int max_passes, int32_t* err, cudaStream_t s) {
+    if (max_passes < 1 || max_passes > 8) return set_error(XM_EINVAL, "index sort: passes");
+    XM_LAUNCH("k_plan_finish", 1, 1, 0, s, k_plan_finish, plan);
+    if (n <= 1) return XM_OK;  // (one key: the plan needs no pass)
+    const int passes = max_passes;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const size_t st_words = (size_t)ntiles * kRadix;
+    const size_t bytes = passes * (kRadix * sizeof(unsigned long long) + st_words * sizeof(uint64_t) +
+                                   sizeof(uint64_t)) + 16;
+    unsigned char* work = (unsigned char*)dev_alloc(bytes, s);
+    if (!work) return set_error(XM_ENOMEM, "index sort of %lld keys", (long long)n);
+    unsigned long long* hist = (unsigned long long*)work;
+    uint64_t* status = (uint64_t*)(hist + passes * kRadix);
+    unsigned int* counters = (unsigned int*)(status + passes * st_words);
+    const size_t smem = sizeof(OnesweepSmem);
+    radix_sort_prepare();
+    xm_status st = XM_OK;
+    cudaError_t e = cudaMemsetAsync(work, 0, bytes, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "index sort memset");
+    if (st == XM_OK) {
+        const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
+        launch_begin("k_plan_hist", s);
+        k_plan_hist<<<hg, kSortThreads, 0, s>>>(keys, n, plan, passes, hist);
+        e = launch_end("k_plan_hist", s);
+        if (e != cudaSuccess) st = cuda_fail(e, "k_plan_hist");
+    }
+    uint64_t *ki = keys, *ko = tk;
+    uint32_t *vi = vals, *vo = tv;
+    for (int p = 0; p < passes && st == XM_OK; p++) {
+        launch_begin("k_onesweep", s);
+        k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, s>>>(
+            ki, vi, n, 8 * p, hist + p * kRadix, status + p * st_words, counters + p, ko, vo, err,
+            plan, p, device_stats());
+        e = launch_end("k_onesweep", s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
+        uint64_t* t = ki; ki = ko; ko = t;
+        uint32_t* u = vi; vi = vo; vo = u;
+    }
+    dev_free(work, s);
+    return st;
+}
+
 xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
                          int begin_bit, int end_bit, int32_t* err, cudaStream_t s) {
     if (n <= 1 || end_bit <= begin_bit) return XM_OK;
@@ -492,7 +602,7 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
         launch_begin("k_onesweep", s);
         k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, s>>>(
             ki, vi, n, begin_bit + 8 * p, hist + p * kRadix, status + p * st_words, counters + p,
-            ko, vo, err);
+            ko, vo, err, (const SortPlan*)nullptr, p, device_stats());
         e = launch_end("k_onesweep", s);
         if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;

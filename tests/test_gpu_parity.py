@@ -434,3 +434,56 @@ def test_deferred_index_check(xm):
     idx = xm.Index(_cuda(d["b_lon"]), _cuda(d["b_lat"]), deferred_check=True)
     res = xm.Result(idx, _cuda(d["a_lon"]), _cuda(d["a_lat"]), **d["region"])
     check_pairs(res, ref)
+
+
+# ------------------------------------------------- planned index sort
+
+PLAN_CASES = {  # centre lon, lat, half-widths in lon and lat (deg), most passes
+    "patch": (150.0, 30.0, 0.3, 0.3, 4),
+    "seam": (0.0, -20.0, 0.3, 0.3, 5),
+    "two_zones": (77.0, 0.0, 0.5, 1.5e-3, 4),
+    "pole": (None, 90.0, None, 0.05, 5),
+}
+
+
+@pytest.mark.parametrize("case", ["identical"] + list(PLAN_CASES))
+def test_index_sort_plan(xm, case):
+    """The index sort skips digit passes over key bits that no B source
+    varies (zone range, RA bits above their spread); the index must be the
+    one a full sort gives, so the matches equal the oracle's, and the passes
+    counted are whole passes over B."""
+    g = synth.rng(900 + len(case))
+    n_b = 300_001  # 74 sort tiles, the last one ragged
+    if case == "identical":
+        b_lon, b_lat = np.full(n_b, 123.456), np.full(n_b, -7.5)
+        # on the point, 1.9 arcsec and 2.1 arcsec away (radius 2 arcsec)
+        a_lon = np.array([123.456, 123.456, 123.456])
+        a_lat = np.array([-7.5, -7.5 + 1.9 / 3600, -7.5 - 2.1 / 3600])
+        max_passes = 0
+    else:
+        c_lon, c_lat, w_lon, w_lat, max_passes = PLAN_CASES[case]
+        if c_lon is None:  # a cap around the pole, every RA
+            b_lon = g.uniform(0, 360, n_b)
+            b_lat = c_lat - g.uniform(0, w_lat, n_b)
+        else:
+            b_lon = np.mod(c_lon + g.uniform(-w_lon, w_lon, n_b), 360.0)
+            b_lat = c_lat + g.uniform(-w_lat, w_lat, n_b)
+        a_lon = np.mod(b_lon[::100] + g.normal(0, 3e-4, b_lon[::100].size), 360.0)
+        a_lat = b_lat[::100].copy()
+    d = dict(a_lon=a_lon, a_lat=a_lat, b_lon=b_lon, b_lat=b_lat, a_frame=0, b_frame=0,
+             region=dict(shape=0, a=2.0))
+    ref = oracle_ref(d)
+    for prec in PRECS:
+        xm.reset_stats()
+        idx = xm.Index(_cuda(b_lon), _cuda(b_lat), zone_height_arcsec=12.0,
+                       build_fp64=prec == "fp64")
+        keys = xm.stats()["sort_key_passes"]  # the index sort's alone
+        assert keys % n_b == 0 and keys // n_b <= max_passes
+        res = xm.Result(idx, _cuda(a_lon), _cuda(a_lat), precision=_prec(xm, prec), shape=0,
+                        a=2.0, selection=xm.SEL_ALL | xm.SEL_BEST)
+        check_pairs(res, ref)
+        if case == "identical":
+            # every B source is a member of the first two; best: lowest B row
+            assert list(_host(res.best_b)) == [0, 0, -1]
+        else:
+            check_best(res, ref, a_lon.size)
