@@ -65,6 +65,7 @@ def _load():
     lib.or_result_nborder.argtypes = [ctypes.c_void_p]
     lib.or_result_copy.argtypes = [ctypes.c_void_p, pi64, pi64, pd]
     lib.or_result_copy_border.argtypes = [ctypes.c_void_p, pi64, pi64, pd]
+    lib.or_result_copy_dist.argtypes = [ctypes.c_void_p, pd]
     lib.or_result_free.argtypes = [ctypes.c_void_p]
     lib.or_to_equatorial.restype = i32
     lib.or_to_equatorial.argtypes = [i64, pd, pd, i32, pd, pd]
@@ -120,9 +121,10 @@ def match(a_lon, a_lat, b_lon, b_lat, *, shape=CIRCLE, a=1.0, b=None, pa=0.0,
           pa_zero_deg=0.0, pa_dir=1, a_frame=EQ, b_frame=EQ, subset=None, mode="grid",
           nthreads=None, tau=1e-9):
     """All members of each A source (paper §2.1). Returns a dict with int64
-    ``a_row``, ``b_row``, float64 ``sep`` (arcsec) in ascending (a_row, b_row)
-    and the borderline candidates ``border_a``, ``border_b``, ``border_margin``
-    (decision margin below ``tau``)."""
+    ``a_row``, ``b_row``, float64 ``sep`` (arcsec) and ``dist`` (normalised
+    distance: the region scale that reaches the pair, at most 1 for members)
+    in ascending (a_row, b_row), and the borderline candidates ``border_a``,
+    ``border_b``, ``border_margin`` (decision margin below ``tau``)."""
     lib = _load()
     a_lon, a_lat, b_lon, b_lat = _f64(a_lon), _f64(a_lat), _f64(b_lon), _f64(b_lat)
     a_col = None if a_col is None else _f64(a_col)
@@ -147,10 +149,12 @@ def match(a_lon, a_lat, b_lon, b_lat, *, shape=CIRCLE, a=1.0, b=None, pa=0.0,
         n = lib.or_result_npairs(res)
         nb = lib.or_result_nborder(res)
         out = {"a_row": np.empty(n, np.int64), "b_row": np.empty(n, np.int64),
-               "sep": np.empty(n, np.float64), "border_a": np.empty(nb, np.int64),
+               "sep": np.empty(n, np.float64), "dist": np.empty(n, np.float64),
+               "border_a": np.empty(nb, np.int64),
                "border_b": np.empty(nb, np.int64), "border_margin": np.empty(nb, np.float64)}
         lib.or_result_copy(res, _ptr(out["a_row"], ctypes.c_int64),
                            _ptr(out["b_row"], ctypes.c_int64), _ptr(out["sep"]))
+        lib.or_result_copy_dist(res, _ptr(out["dist"]))
         lib.or_result_copy_border(res, _ptr(out["border_a"], ctypes.c_int64),
                                   _ptr(out["border_b"], ctypes.c_int64),
                                   _ptr(out["border_margin"]))
@@ -218,6 +222,40 @@ def pick(pairs, n_a, n_b, kind, tau=1e-9):
     order = np.lexsort((b[keep], a[keep]))
     return {"a_row": a[keep][order], "b_row": b[keep][order], "sep": sep[keep][order],
             "near_tie_b": pb["near_tie"], "near_tie_a": near_a}
+
+
+def best_normalised(pairs, n_a, tau=1e-9):
+    """Best pair of every A source by normalised distance (how deep inside
+    the region the B source lies) instead of angular separation, the third
+    reading of paper §2.2's "best pairs": the member of smallest ``dist``,
+    ties to the lowest B row. Returns ``best_b``, ``best_dist`` (NaN when
+    none) and ``near_tie`` as ``best`` does."""
+    r = best({"a_row": pairs["a_row"], "b_row": pairs["b_row"], "sep": pairs["dist"]}, n_a, tau)
+    return {"best_b": r["best_b"], "best_dist": r["best_sep"], "near_tie": r["near_tie"]}
+
+
+def concentric(pairs, n_a, scales, tau=1e-9):
+    """Concentric regions (paper §3, ClumpPopulator): copies of each A
+    source's region about the same centre with the same orientation, sizes
+    multiplied by ``scales`` (increasing, in (0, 1]: the matched region is
+    the outermost). A member lies inside copy k when its normalised distance
+    is at most scales[k]. Returns per pair ``level``, the first copy that
+    holds it (len(scales) when only the matched region does), per A and copy
+    ``n_within`` (int32 [n_a, K], members inside copy k), and ``border``, the
+    pair indices whose distance is within tau (relative) of a scale."""
+    sc = np.asarray(scales, np.float64)
+    if sc.ndim != 1 or sc.size == 0 or np.any(~np.isfinite(sc)) or np.any(sc <= 0) \
+            or np.any(sc > 1) or np.any(np.diff(sc) <= 0):
+        raise OracleError("scales must increase within (0, 1]")
+    d = pairs["dist"]
+    # copies that do not hold the pair: those before the first that does
+    level = np.sum(~(d[:, None] <= sc[None, :]), axis=1).astype(np.int32)
+    within = np.zeros((n_a, sc.size), np.int32)
+    for k in range(sc.size):
+        np.add.at(within[:, k], pairs["a_row"][d <= sc[k]], 1)
+    near = np.nonzero(np.any(np.abs(d[:, None] / sc[None, :] - 1.0) < tau, axis=1))[0] \
+        if d.size else np.empty(0, np.int64)
+    return {"level": level, "n_within": within, "border": near.astype(np.int64)}
 
 
 def match_values(a_keys, b_keys):

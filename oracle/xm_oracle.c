@@ -31,7 +31,14 @@
  *      (azimuthal-equidistant frame centred on A_i);
  *   5. circle: rho <= r; ellipse: (X/a)^2 + (Y/b)^2 <= 1;
  *      rectangle: |X| <= a and |Y| <= b (a, b half-sides); closed boundary;
- *   6. the separation is reported in arcsec.
+ *   6. the separation is reported in arcsec;
+ *   7. with every pair also its normalised distance: the factor by which the
+ *      region must be scaled about A_i to reach B_j -- rho/r for a circle,
+ *      sqrt((X/a)^2 + (Y/b)^2) for an ellipse, max(|X|/a, |Y|/b) for a
+ *      rectangle -- so B_j is a member when it is at most 1. It orders the
+ *      members by how deep inside the region they lie (the "best" pair by
+ *      normalised distance) and places them among concentric scaled copies
+ *      of the region (paper §3, ClumpPopulator).
  * A region with a zero size has no interior and matches nothing.
  *
  * Two ways of finding the candidates, with identical results:
@@ -208,15 +215,16 @@ static int make_region(const region_spec* rs, int64_t i, a_src* s) {
 /* Membership of one candidate: returns 1 if inside; rho (radians) and the
  * decision margin are returned through the pointers. */
 static int test_pair(int shape, const a_src* A, const double pb[3], double* rho_out,
-                     double* margin_out) {
+                     double* margin_out, double* dist_out) {
     double x = pb[0] * A->e[0] + pb[1] * A->e[1] + pb[2] * A->e[2];
     double y = pb[0] * A->n[0] + pb[1] * A->n[1] + pb[2] * A->n[2];
     double z = pb[0] * A->p[0] + pb[1] * A->p[1] + pb[2] * A->p[2];
     double rho = atan2(hypot(x, y), z);
     *rho_out = rho;
-    if (A->empty) { *margin_out = INFINITY; return 0; }
+    if (A->empty) { *margin_out = INFINITY; *dist_out = INFINITY; return 0; }
     if (shape == OR_CIRCLE) {
         *margin_out = fabs(rho / A->a - 1.0);
+        *dist_out = rho / A->a;
         return rho <= A->a;
     }
     double phi = atan2(x, y);
@@ -225,10 +233,12 @@ static int test_pair(int shape, const a_src* A, const double pb[3], double* rho_
     if (shape == OR_ELLIPSE) {
         double q = (X / A->a) * (X / A->a) + (Y / A->b) * (Y / A->b);
         *margin_out = fabs(q - 1.0);
+        *dist_out = sqrt(q);
         return q <= 1.0;
     }
     double m = fmax(fabs(X) / A->a, fabs(Y) / A->b);
     *margin_out = fabs(m - 1.0);
+    *dist_out = m;
     return m <= 1.0;
 }
 
@@ -237,6 +247,7 @@ static int test_pair(int shape, const a_src* A, const double pb[3], double* rho_
 typedef struct {
     int64_t *a, *b;
     double* sep;
+    double* dist;
     int64_t n, cap;
     int64_t *ba, *bb;
     double* bm;
@@ -244,7 +255,7 @@ typedef struct {
     int oom;
 } pairbuf;
 
-static void pb_push(pairbuf* P, int64_t a, int64_t b, double sep) {
+static void pb_push(pairbuf* P, int64_t a, int64_t b, double sep, double dist) {
     if (P->n == P->cap) {
         int64_t c = P->cap ? 2 * P->cap : 1024;
         int64_t* na = realloc(P->a, c * sizeof(int64_t));
@@ -253,10 +264,12 @@ static void pb_push(pairbuf* P, int64_t a, int64_t b, double sep) {
         if (nb) P->b = nb;
         double* ns = realloc(P->sep, c * sizeof(double));
         if (ns) P->sep = ns;
-        if (!na || !nb || !ns) { P->oom = 1; return; }
+        double* nd = realloc(P->dist, c * sizeof(double));
+        if (nd) P->dist = nd;
+        if (!na || !nb || !ns || !nd) { P->oom = 1; return; }
         P->cap = c;
     }
-    P->a[P->n] = a; P->b[P->n] = b; P->sep[P->n] = sep; P->n++;
+    P->a[P->n] = a; P->b[P->n] = b; P->sep[P->n] = sep; P->dist[P->n] = dist; P->n++;
 }
 
 static void pb_border(pairbuf* P, int64_t a, int64_t b, double m) {
@@ -277,7 +290,7 @@ static void pb_border(pairbuf* P, int64_t a, int64_t b, double m) {
 typedef struct or_result {
     int64_t n, nb;
     int64_t *a, *b, *ba, *bb;
-    double *sep, *bm;
+    double *sep, *dist, *bm;
 } or_result;
 
 /* --------------------------------------------------------------- matcher -- */
@@ -302,7 +315,7 @@ static uint64_t vox_key(int64_t ix, int64_t iy, int64_t iz) {
     return (uint64_t)ix | ((uint64_t)iy << 21) | ((uint64_t)iz << 42);
 }
 
-typedef struct { int64_t b; double sep, margin; } member;
+typedef struct { int64_t b; double sep, margin, dist; } member;
 
 static int member_cmp(const void* x, const void* y) {
     const member* u = x;
@@ -337,8 +350,8 @@ static int64_t lower_key(const vox_entry* v, int64_t n, uint64_t key) {
 
 static void consider(worker* w, const a_src* A, int64_t arow, int64_t j, member** mem,
                      int64_t* nm, int64_t* cm) {
-    double rho, margin;
-    int in = test_pair(w->shape, A, w->pB + 3 * j, &rho, &margin);
+    double rho, margin, dist;
+    int in = test_pair(w->shape, A, w->pB + 3 * j, &rho, &margin, &dist);
     if (margin < w->tau) pb_border(&w->out, arow, j, margin);
     if (!in) return;
     if (*nm == *cm) {
@@ -351,6 +364,7 @@ static void consider(worker* w, const a_src* A, int64_t arow, int64_t j, member*
     (*mem)[*nm].b = j;
     (*mem)[*nm].sep = rho / ARCSEC;
     (*mem)[*nm].margin = margin;
+    (*mem)[*nm].dist = dist;
     (*nm)++;
 }
 
@@ -379,7 +393,7 @@ static void* run_worker(void* arg) {
         }
         /* members of one A in ascending B row (canonical order) */
         qsort(mem, nm, sizeof(member), member_cmp);
-        for (int64_t k = 0; k < nm; k++) pb_push(&w->out, arow, mem[k].b, mem[k].sep);
+        for (int64_t k = 0; k < nm; k++) pb_push(&w->out, arow, mem[k].b, mem[k].sep, mem[k].dist);
     }
     free(mem);
     return NULL;
@@ -553,10 +567,11 @@ or_result* or_match(int64_t nA, const double* a_lon, const double* a_lat, int a_
         R->a = malloc((total ? total : 1) * sizeof(int64_t));
         R->b = malloc((total ? total : 1) * sizeof(int64_t));
         R->sep = malloc((total ? total : 1) * sizeof(double));
+        R->dist = malloc((total ? total : 1) * sizeof(double));
         R->ba = malloc((totalb ? totalb : 1) * sizeof(int64_t));
         R->bb = malloc((totalb ? totalb : 1) * sizeof(int64_t));
         R->bm = malloc((totalb ? totalb : 1) * sizeof(double));
-        oom = !R->a || !R->b || !R->sep || !R->ba || !R->bb || !R->bm;
+        oom = !R->a || !R->b || !R->sep || !R->dist || !R->ba || !R->bb || !R->bm;
     }
     if (R && !oom) {
         /* threads own contiguous, ascending slices of the selected A */
@@ -564,6 +579,7 @@ or_result* or_match(int64_t nA, const double* a_lon, const double* a_lat, int a_
             memcpy(R->a + R->n, W[t].out.a, W[t].out.n * sizeof(int64_t));
             memcpy(R->b + R->n, W[t].out.b, W[t].out.n * sizeof(int64_t));
             memcpy(R->sep + R->n, W[t].out.sep, W[t].out.n * sizeof(double));
+            memcpy(R->dist + R->n, W[t].out.dist, W[t].out.n * sizeof(double));
             R->n += W[t].out.n;
             memcpy(R->ba + R->nb, W[t].out.ba, W[t].out.nb * sizeof(int64_t));
             memcpy(R->bb + R->nb, W[t].out.bb, W[t].out.nb * sizeof(int64_t));
@@ -572,12 +588,15 @@ or_result* or_match(int64_t nA, const double* a_lon, const double* a_lat, int a_
         }
     }
     for (int t = 0; t < nthreads; t++) {
-        free(W[t].out.a); free(W[t].out.b); free(W[t].out.sep);
+        free(W[t].out.a); free(W[t].out.b); free(W[t].out.sep); free(W[t].out.dist);
         free(W[t].out.ba); free(W[t].out.bb); free(W[t].out.bm);
     }
     free(W); free(vox); free(A); free(a_rows); free(pB);
     if (!R || oom) {
-        if (R) { free(R->a); free(R->b); free(R->sep); free(R->ba); free(R->bb); free(R->bm); free(R); }
+        if (R) {
+            free(R->a); free(R->b); free(R->sep); free(R->dist);
+            free(R->ba); free(R->bb); free(R->bm); free(R);
+        }
         *status = OR_ENOMEM;
         return NULL;
     }
@@ -593,6 +612,10 @@ void or_result_copy(const or_result* R, int64_t* a, int64_t* b, double* sep) {
     memcpy(sep, R->sep, R->n * sizeof(double));
 }
 
+void or_result_copy_dist(const or_result* R, double* dist) {
+    memcpy(dist, R->dist, R->n * sizeof(double));
+}
+
 void or_result_copy_border(const or_result* R, int64_t* a, int64_t* b, double* margin) {
     memcpy(a, R->ba, R->nb * sizeof(int64_t));
     memcpy(b, R->bb, R->nb * sizeof(int64_t));
@@ -601,7 +624,7 @@ void or_result_copy_border(const or_result* R, int64_t* a, int64_t* b, double* m
 
 void or_result_free(or_result* R) {
     if (!R) return;
-    free(R->a); free(R->b); free(R->sep); free(R->ba); free(R->bb); free(R->bm);
+    free(R->a); free(R->b); free(R->sep); free(R->dist); free(R->ba); free(R->bb); free(R->bm);
     free(R);
 }
 

@@ -500,3 +500,104 @@ def test_match_values_large_int64_keys_compare_exactly():
     r = oracle.match_values(big, big[::-1].copy())
     np.testing.assert_array_equal(r["a_row"], [0, 1, 2, 3])
     np.testing.assert_array_equal(r["b_row"], [3, 2, 1, 0])
+
+
+# ------------------------------------------- normalised distance (§2.2, §3)
+
+@pytest.mark.parametrize("lat0", [0.0, 37.0, -89.99, 89.995])
+def test_normalised_distance_of_scaled_ellipse_points(lat0):
+    """A point at t (a cos u, b sin u) in the region frame lies on the
+    boundary of the ellipse scaled by t, whatever u: its normalised distance
+    is t."""
+    a, b, pa = 20.0, 6.0, 30.0
+    t = np.array([0.05, 0.3, 0.61, 0.97, 0.9999])
+    u = np.radians(np.array([0.0, 17.0, 90.0, 133.0, 200.0, 271.0, 333.0]))
+    tt, uu = np.meshgrid(t, u, indexing="ij")
+    xy = np.stack([(tt * a * np.cos(uu)).ravel(), (tt * b * np.sin(uu)).ravel()], 1)
+    lon, lat = _region_points(123.0, lat0, pa, xy)
+    r = oracle.match([123.0], [lat0], lon, lat, shape=oracle.ELLIPSE, a=a, b=b, pa=pa)
+    assert r["b_row"].size == xy.shape[0]
+    np.testing.assert_allclose(r["dist"], tt.ravel()[r["b_row"]], rtol=1e-9)
+
+
+@pytest.mark.parametrize("lat0", [0.0, -60.0, 89.999])
+def test_normalised_distance_of_rectangle_edges(lat0):
+    """Points on the edges of the rectangle scaled by t (t a, w t b) and
+    (w t a, t b) with |w| <= 1 have normalised distance t."""
+    a, b, pa = 15.0, 4.0, 110.0
+    pts, want = [], []
+    for t in (0.2, 0.5, 0.93):
+        for w in (-1.0, -0.4, 0.0, 0.7, 1.0):
+            pts += [[t * a, w * t * b], [-t * a, w * t * b], [w * t * a, t * b], [w * t * a, -t * b]]
+            want += [t] * 4
+    lon, lat = _region_points(300.0, lat0, pa, np.array(pts))
+    r = oracle.match([300.0], [lat0], lon, lat, shape=oracle.RECT, a=a, b=b, pa=pa)
+    assert r["b_row"].size == len(pts)
+    np.testing.assert_allclose(r["dist"], np.array(want)[r["b_row"]], rtol=1e-9)
+
+
+def test_normalised_distance_of_circles_is_separation_over_radius():
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(11)
+    r = oracle.match(a_lon, a_lat, b_lon, b_lat, a_col=cols["a_col"])
+    assert r["a_row"].size > 50
+    np.testing.assert_allclose(r["dist"], r["sep"] / cols["a_col"][r["a_row"]], rtol=1e-12)
+    assert np.all(r["dist"] <= 1.0)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_normalised_distance_scales_inversely_with_region_size(shape):
+    """Scaling every region by s divides each pair's normalised distance by
+    s; the members of the smaller regions are the pairs with dist <= 1/s."""
+    a_lon, a_lat, b_lon, b_lat, cols = _random_mixed(12)
+    kw = dict(shape=shape, a_col=cols["a_col"], b_col=cols["b_col"], pa_col=cols["pa_col"])
+    big = oracle.match(a_lon, a_lat, b_lon, b_lat, size_scale=1.5, **kw)
+    base = oracle.match(a_lon, a_lat, b_lon, b_lat, **kw)
+    key_big = big["a_row"] * 10**6 + big["b_row"]
+    key = base["a_row"] * 10**6 + base["b_row"]
+    inside = big["dist"] * 1.5 <= 1.0
+    np.testing.assert_array_equal(np.sort(key_big[inside]), np.sort(key))
+    np.testing.assert_allclose(big["dist"][np.isin(key_big, key)] * 1.5, base["dist"], rtol=1e-12)
+
+
+def test_best_normalised_hand_example():
+    """Ellipse 20 x 2 arcsec, major axis north: B0 10 arcsec along the major
+    axis (dist 0.5), B1 1.5 arcsec across it (dist 0.75). By separation the
+    best is B1, by normalised distance B0."""
+    lon, lat = _region_points(50.0, 10.0, 0.0, np.array([[10.0, 0.0], [0.0, 1.5]]))
+    r = oracle.match([50.0], [10.0], lon, lat, shape=oracle.ELLIPSE, a=20.0, b=2.0, pa=0.0)
+    np.testing.assert_allclose(r["dist"], [0.5, 0.75], rtol=1e-9)
+    assert oracle.best(r, 1)["best_b"][0] == 1
+    bn = oracle.best_normalised(r, 1)
+    assert bn["best_b"][0] == 0 and bn["best_dist"][0] == pytest.approx(0.5, rel=1e-9)
+
+
+def test_best_normalised_equals_best_for_fixed_circles(c1_result):
+    d, r = c1_result
+    n_a = d["a_lon"].size
+    np.testing.assert_array_equal(oracle.best_normalised(r, n_a)["best_b"],
+                                  oracle.best(r, n_a)["best_b"])
+
+
+def test_concentric_levels_from_construction():
+    """Points at known normalised distances t inside an ellipse: the level is
+    the first scale >= t, the counts are cumulative over the scales."""
+    a, b, pa = 30.0, 12.0, 75.0
+    t = np.array([0.1, 0.29, 0.31, 0.55, 0.65, 0.88, 0.95, 0.999, 0.2])
+    u = np.radians(np.arange(t.size) * 41.0)
+    xy = np.stack([t * a * np.cos(u), t * b * np.sin(u)], 1)
+    lon, lat = _region_points(210.0, -33.0, pa, xy)
+    r = oracle.match([210.0], [-33.0], lon, lat, shape=oracle.ELLIPSE, a=a, b=b, pa=pa)
+    scales = [0.3, 0.6, 0.9]
+    c = oracle.concentric(r, 1, scales)
+    np.testing.assert_array_equal(c["level"], np.array([0, 0, 1, 1, 2, 2, 3, 3, 0])[r["b_row"]])
+    np.testing.assert_array_equal(c["n_within"][0], [3, 5, 7])
+    assert c["border"].size == 0
+    # one scale of 1: every member is at level 0
+    assert np.all(oracle.concentric(r, 1, [1.0])["level"] == 0)
+
+
+@pytest.mark.parametrize("bad", [[], [0.5, 0.5], [0.6, 0.3], [0.0, 0.5], [0.5, 1.2], [np.nan]])
+def test_concentric_rejects_bad_scales(bad):
+    r = oracle.match([1.0], [1.0], [1.0], [1.0], a=1.0)
+    with pytest.raises(oracle.OracleError):
+        oracle.concentric(r, 1, bad)
