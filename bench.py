@@ -363,13 +363,18 @@ def run_ours(args):
             dist.barrier()
         return ms, st, prof, res, rows, bytes_out
 
-    # float32 + float64 recheck (the product path)
+    # float32 + float64 recheck (the product path), uninstrumented
     with Clocks(local) as clk:
-        ms, st, prof, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup,
-                                           profile=True, clocks=clk)
+        ms, st, _, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup, clocks=clk)
     total_ms = max_over_ranks(sum(ms), world, "cuda")
     value = weak_scaling_value(n_a, args.steps, world, total_ms)
     launches = st["kernel_launches"]
+
+    # the same steps again with an event pair around every launch: per-kernel
+    # times for the shares and the roofline (the events cost a little time,
+    # so these steps are not the ones the value comes from)
+    prof_steps = max(10, args.steps // 4)
+    ms_p, st_p, prof, _, _, _ = timed(xm.PREC_FP32, False, prof_steps, 1, profile=True)
 
     # all-float64 path
     ms64, _, _, _, _, _ = timed(xm.PREC_FP64, True, max(3, args.steps // 2), 1)
@@ -386,7 +391,7 @@ def run_ours(args):
     v_e2e = n_a * len(ms_e2e) / (sum(ms_e2e) / 1e3)
 
     # roofline of the dominant kernel
-    roof = roofline(prof, st, args.steps, n_a, n_b, zone_h, total_ms)
+    roof = roofline(prof, st_p, prof_steps, n_a, n_b, zone_h, sum(ms_p))
 
     # further readings of "best pairs" over the C2 pair list (index resident)
     picks = pick_leg(xm, torch, step, stream)
@@ -411,8 +416,9 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk.summary(),
         "picks": picks,
-        "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in
+        "kernels_ms_per_step": {k: round(v[0] / prof_steps, 4) for k, v in
                                 sorted(prof.items(), key=lambda kv: -kv[1][0])[:16]},
+        "profiled_ms_per_step": sum(ms_p) / prof_steps,
         "stats_per_step": {k: v // args.steps for k, v in st.items()},
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peaks.get("_source")},
     }
@@ -433,7 +439,8 @@ def run_ours(args):
 
 def pick_leg(xm, torch, step, stream):
     """Best pair per B source and mutual best pairs over one C2 result:
-    device time of xm_pick_pairs (median of 10) and pairs per second."""
+    device time of xm_pick_pairs (median of 10) and pairs per second; the
+    same for the normalised distances and concentric levels."""
     idx, res, _, _ = step(xm.PREC_FP32, False)
     out = {"pairs_in": int(res.n_pairs)}
     for kind in ("best_b", "mutual"):
@@ -447,6 +454,20 @@ def pick_leg(xm, torch, step, stream):
             if k:
                 ms.append(e0.elapsed_time(e1))
         out[kind] = {"ms": statistics.median(ms), "rows": int(rows.n),
+                     "pairs_per_s": res.n_pairs / (statistics.median(ms) / 1e3)}
+    # normalised distance of every pair, best pair by it, and three concentric
+    # copies of each ellipse (xm_levels_compute)
+    ms = []
+    for k in range(11):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lv = res.levels([0.25, 0.5, 0.75])
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ms.append(e0.elapsed_time(e1))
+        del lv
+    out["levels"] = {"scales": [0.25, 0.5, 0.75], "ms": statistics.median(ms),
                      "pairs_per_s": res.n_pairs / (statistics.median(ms) / 1e3)}
     return out
 
@@ -467,9 +488,9 @@ def c3_leg(args, xm, torch):
     peak = load_peaks().get("hbm_gbs", 6800.0)
     for prec, fp64_index, name in ((xm.PREC_FP32, False, "fp32_recheck"), (xm.PREC_FP64, True, "fp64")):
         t_build, t_match = [], []
-        for k in range(4):
+        for k in range(5):  # a warm-up, three timed passes, one profiled
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            if k == 3:
+            if k == 4:
                 xm.reset_stats()
                 xm.prof_enable(True)
                 nvtx_push(f"c3_{name}")
@@ -481,9 +502,9 @@ def c3_leg(args, xm, torch):
                             selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
             e2.record(stream)
             e2.synchronize()
-            if k == 3:
+            if k == 4:
                 nvtx_pop()
-            if k >= 1:
+            if 1 <= k <= 3:
                 t_build.append(e0.elapsed_time(e1))
                 t_match.append(e1.elapsed_time(e2))
             pairs = int(res.n_pairs)
@@ -524,8 +545,8 @@ def values_leg(args, xm, torch):
     d = synth_gpu.values(n_a=n_a, n_b=n_b)
     stream = torch.cuda.current_stream()
     ms = []
-    for k in range(4):
-        if k == 3:
+    for k in range(5):  # a warm-up, three timed passes, one profiled
+        if k == 4:
             xm.reset_stats()
             xm.prof_enable(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -533,7 +554,7 @@ def values_leg(args, xm, torch):
         res = xm.ValueResult(d["a_keys"], d["b_keys"], selection=xm.SEL_ALL | xm.SEL_BEST)
         e1.record(stream)
         e1.synchronize()
-        if k:
+        if 1 <= k <= 3:
             ms.append(e0.elapsed_time(e1))
         pairs = int(res.n_pairs)
         del res

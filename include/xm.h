@@ -326,6 +326,52 @@ typedef enum { XM_PICK_BEST_B = 1, XM_PICK_MUTUAL = 2 } xm_pick;
 XM_API xm_status xm_pick_pairs(const xm_index* index, const xm_result* result, int32_t pick,
                                void* stream, xm_rows** out);
 
+/* ---- normalised distance and concentric regions (paper §2.2, §3) ----- */
+
+/* The normalised distance of a pair is the factor by which A's region must be
+ * scaled about A's position (same orientation) to reach B: rho / r for a
+ * circle, sqrt((X/a)^2 + (Y/b)^2) for an ellipse, max(|X|/a, |Y|/b) for a
+ * rectangle, with (X, Y) B's coordinates in A's region frame; members have it
+ * at most 1. Over it:
+ *   - the best pair of every A source by normalised distance (the member
+ *     lying deepest inside the region; ties to the lowest B row), a third
+ *     reading of the paper's "best pairs" (§2.2);
+ *   - concentric regions (§3, ClumpPopulator): copies of each region scaled
+ *     by n_scales factors s_0 < s_1 < ... in (0, 1], the matched region being
+ *     the outermost. A pair's level is the first copy that holds it
+ *     (dist <= s_k), n_scales when only the matched region does. */
+typedef struct xm_levels xm_levels;
+
+/* Computes, in float64 from the exact positions, the normalised distance of
+ * every pair of `result` (which must come from xm_match on `index` with the
+ * ALL selection), the best pair by it, and, when n_scales > 0, the level of
+ * every pair and per A source the number of members inside each copy.
+ * `scales` is a host array of n_scales (0..64) strictly increasing values in
+ * (0, 1]. Does not synchronise: the arrays are written on `stream`.
+ * Errors: XM_EINVAL (selection missing, another index, bad scales),
+ * XM_EUNSUPPORTED (results without positions: views of batch results,
+ * xm_match_values), XM_ENOMEM, XM_ECUDA. */
+XM_API xm_status xm_levels_compute(const xm_index* index, const xm_result* result,
+                                   const double* scales, int32_t n_scales, void* stream,
+                                   xm_levels** out);
+XM_API xm_status xm_levels_free(xm_levels* levels);
+
+/* Device arrays of a levels result (valid until xm_levels_free):
+ *  dist[n_pairs]                 normalised distance of each pair of the result
+ *  best_b_row[n_a] (-1 = none), best_dist[n_a] (NaN = none)
+ *  level[n_pairs] (int32, 0..n_scales), n_within[n_a * n_scales] (int32,
+ *  row-major by A: members with dist <= s_k); NULL when n_scales == 0. */
+typedef struct {
+    int64_t n_pairs, n_a;
+    int32_t n_scales;
+    const double* dist;
+    const int64_t* best_b_row;
+    const double* best_dist;
+    const int32_t* level;
+    const int32_t* n_within;
+} xm_levels_view;
+XM_API xm_status xm_levels_get(const xm_levels* levels, xm_levels_view* view);
+
 /* ---- batches of requests (one launch of the persistent scan) --------- */
 
 /* One cross-match request of a batch: an A catalogue, its region (§2.1), the

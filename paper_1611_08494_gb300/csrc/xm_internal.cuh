@@ -329,6 +329,38 @@ __device__ __forceinline__ bool test64(const A64& A, int shape, double px, doubl
     return k * fmax(fabs(X) / A.a, fabs(Y) / A.b) <= 1.0;
 }
 
+// Float64 normalised distance of B in A's region: the factor by which the
+// region must be scaled about A to reach B (rho / r for a circle,
+// sqrt((X/a)^2 + (Y/b)^2) for an ellipse, max(|X|/a, |Y|/b) for a
+// rectangle, X and Y the region-frame coordinates as in test64), at most 1
+// for members. Infinite for an empty region.
+__device__ __forceinline__ double norm64(const A64& A, int shape, double px, double py,
+                                         double pz) {
+    double w = px * A.ca + py * A.sa;
+    double x = py * A.ca - px * A.sa;
+    double y = pz * A.cd - A.sd * w;
+    double z = A.cd * w + pz * A.sd;
+    double s2 = x * x + y * y;
+    double s = sqrt(s2);
+    double rho, k;
+    if (z > 0.0 && s2 < 1e-4) {
+        k = rho_over_s(s2);
+        rho = s * k;
+    } else {
+        rho = atan2(s, z);
+        k = s > 0.0 ? rho / s : 1.0;
+    }
+    if (A.a == 0.0 || A.b == 0.0) return INFINITY;
+    if (shape == XM_CIRCLE) return rho / A.a;
+    double X = x * A.st + y * A.ct;
+    double Y = x * A.ct - y * A.st;
+    if (shape == XM_ELLIPSE) {
+        double u = X / A.a, v = Y / A.b;
+        return k * sqrt(u * u + v * v);
+    }
+    return k * fmax(fabs(X) / A.a, fabs(Y) / A.b);
+}
+
 // Float64 unit vector of a position given in degrees.
 __device__ __forceinline__ void unit64_deg(double lon, double lat, double* px, double* py,
                                            double* pz) {

@@ -1,0 +1,218 @@
+// xm_levels.cu -- the normalised distance of every pair of an "all" result:
+// the best pair of each A source by it (a reading of the "best pairs" of
+// §2.2) and the levels of concentric scaled regions (§3, ClumpPopulator).
+//
+//   k_lvl_a64     per A source: float64 sines and cosines of its position and
+//                 orientation, once (the pairs of a source share them)
+//   k_lvl_pair    per pair: float64 normalised distance from the exact
+//                 positions, its level among the scales, the count of its
+//                 copy, the smallest distance of its A source
+//   k_lvl_best    per pair at that smallest distance: the lowest B row
+//   k_lvl_finish  per A source: counts made cumulative over the copies, the
+//                 best pair written out
+//
+// Every decision (dist <= s_k, the smallest distance) is taken in float64 on
+// the same values, so the levels and best pairs are the float64 ones.
+#include <math.h>
+
+#include <new>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+
+constexpr int kMaxScales = 64;
+
+struct Scales {
+    double s[kMaxScales];
+    int32_t k;
+};
+
+}  // namespace xm
+
+struct xm_levels {
+    int64_t n_pairs = 0, n_a = 0;
+    int32_t n_scales = 0;
+    double* dist = nullptr;  // one allocation: dist, best_dist, best_b, level, n_within
+    double* best_dist = nullptr;
+    int64_t* best_b = nullptr;
+    int32_t* level = nullptr;
+    int32_t* n_within = nullptr;
+    cudaStream_t stream = nullptr;  // the arrays are written, and freed, in its order
+};
+
+namespace xm {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+
+__global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, A64* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = make_a64(acold[i]);
+}
+
+__global__ void k_lvl_pair(IndexGeom G, const A64* __restrict__ a64,
+                           const int32_t* __restrict__ a_slot, int shape,
+                           const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
+                           int64_t n, Scales S, double* __restrict__ dist,
+                           int32_t* __restrict__ level, int32_t* __restrict__ within,
+                           unsigned long long* __restrict__ mind) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t a = pa[p];
+    const A64& A = a64[a_slot ? a_slot[a] : a];
+    const int32_t row = (int32_t)pb[p];
+    double px, py, pz;
+    if (G.px) {
+        px = G.px[row];
+        py = G.py[row];
+        pz = G.pz[row];
+    } else {
+        const double2 q = G.pos[row];
+        unit64_deg(q.x, q.y, &px, &py, &pz);
+    }
+    const double d = norm64(A, shape, px, py, pz);
+    dist[p] = d;
+    atomicMin(&mind[a], (unsigned long long)dbits(d));  // d >= 0: bit order is value order
+    if (S.k > 0) {
+        int32_t k = 0;  // copies that do not hold the pair
+        while (k < S.k && !(d <= S.s[k])) k++;
+        level[p] = k;
+        if (k < S.k) atomicAdd(&within[a * S.k + k], 1);
+    }
+}
+
+__global__ void k_lvl_best(const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
+                           int64_t n, const double* __restrict__ dist,
+                           const unsigned long long* __restrict__ mind,
+                           unsigned long long* __restrict__ best) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t a = pa[p];
+    if (dbits(dist[p]) == (uint64_t)mind[a]) atomicMin(&best[a], (unsigned long long)pb[p]);
+}
+
+__global__ void k_lvl_finish(int64_t n_a, int32_t k, const unsigned long long* __restrict__ mind,
+                             const unsigned long long* __restrict__ best,
+                             int32_t* __restrict__ within, int64_t* __restrict__ best_b,
+                             double* __restrict__ best_dist) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_a) return;
+    const bool has = best[a] != ~0ull;
+    best_b[a] = has ? (int64_t)best[a] : -1;
+    best_dist[a] = has ? __longlong_as_double((long long)mind[a]) : (double)NAN;
+    int32_t run = 0;
+    for (int32_t j = 0; j < k; j++) {
+        run += within[a * k + j];
+        within[a * k + j] = run;
+    }
+}
+
+unsigned grid_of(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+}  // namespace
+}  // namespace xm
+
+using namespace xm;
+
+extern "C" xm_status xm_levels_compute(const xm_index* X, const xm_result* R, const double* scales,
+                                       int32_t n_scales, void* stream, xm_levels** out) {
+    if (!out) return set_error(XM_EINVAL, "xm_levels_compute: out is NULL");
+    *out = nullptr;
+    if (!X || !R) return set_error(XM_EINVAL, "xm_levels_compute: NULL argument");
+    if (n_scales < 0 || n_scales > kMaxScales)
+        return set_error(XM_EINVAL, "xm_levels_compute: %d scales (0..%d)", n_scales, kMaxScales);
+    if (n_scales > 0 && !scales) return set_error(XM_EINVAL, "xm_levels_compute: scales is NULL");
+    Scales S{};
+    S.k = n_scales;
+    for (int32_t j = 0; j < n_scales; j++) {
+        const double v = scales[j];
+        if (!(v > 0.0 && v <= 1.0) || (j > 0 && !(v > scales[j - 1])))
+            return set_error(XM_EINVAL, "xm_levels_compute: scales must increase within (0, 1]");
+        S.s[j] = v;
+    }
+    if (!(R->selection & XM_SEL_ALL))
+        return set_error(XM_EINVAL, "xm_levels_compute: the result holds no ALL selection");
+    if (!R->acold)
+        return set_error(XM_EUNSUPPORTED, "xm_levels_compute: the result holds no positions "
+                                          "(batch view or exact-value match)");
+    if (R->n_b != X->n) return set_error(XM_EINVAL, "xm_levels_compute: the result is of another index");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = R->n_pairs, nA = R->n_a;
+    xm_levels* L = new (std::nothrow) xm_levels();
+    if (!L) return set_error(XM_ENOMEM, "xm_levels_compute: host allocation");
+    L->n_pairs = n;
+    L->n_a = nA;
+    L->n_scales = n_scales;
+    L->stream = s;
+    const int64_t n1 = n > 0 ? n : 1, a1 = nA > 0 ? nA : 1;
+    const int64_t nw = n_scales > 0 ? nA * n_scales : 0;
+    // dist, best_dist (f64), best_b (i64), level (i32, padded to 8 B), n_within (i32)
+    const size_t lvl_bytes = n_scales > 0 ? ((size_t)n1 * sizeof(int32_t) + 7) / 8 * 8 : 0;
+    const size_t bytes = (size_t)n1 * sizeof(double) + (size_t)a1 * (sizeof(double) + sizeof(int64_t)) +
+                         lvl_bytes + (size_t)(nw > 0 ? nw : 0) * sizeof(int32_t);
+    unsigned char* base = (unsigned char*)dev_alloc(bytes, s);
+    A64* a64 = (A64*)dev_alloc((size_t)a1 * sizeof(A64), s);
+    unsigned long long* w = (unsigned long long*)dev_alloc(2 * (size_t)a1 * sizeof(unsigned long long), s);
+    auto body = [&]() -> xm_status {
+        if (!base || !a64 || !w) return set_error(XM_ENOMEM, "xm_levels_compute: %lld pairs", (long long)n);
+        L->dist = (double*)base;
+        L->best_dist = L->dist + n1;
+        L->best_b = (int64_t*)(L->best_dist + a1);
+        unsigned char* tail = (unsigned char*)(L->best_b + a1);
+        if (n_scales > 0) {
+            L->level = (int32_t*)tail;
+            L->n_within = (int32_t*)(tail + lvl_bytes);
+        }
+        unsigned long long *mind = w, *best = w + a1;
+        cudaError_t e = cudaMemsetAsync(w, 0xFF, 2 * (size_t)a1 * sizeof(unsigned long long), s);
+        if (e == cudaSuccess && nw > 0) e = cudaMemsetAsync(L->n_within, 0, nw * sizeof(int32_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "xm_levels_compute: memset");
+        if (nA > 0)  // A descriptions are stored by slot; the slots are a permutation of the rows
+            XM_LAUNCH("k_lvl_a64", grid_of(nA), kBlock, 0, s, k_lvl_a64, R->acold, nA, a64);
+        if (n > 0) {
+            const IndexGeom G = X->geom();
+            XM_LAUNCH("k_lvl_pair", grid_of(n), kBlock, 0, s, k_lvl_pair, G, a64, R->a_slot,
+                      R->shape, R->a_row, R->b_row, n, S, L->dist, L->level, L->n_within, mind);
+            XM_LAUNCH("k_lvl_best", grid_of(n), kBlock, 0, s, k_lvl_best, R->a_row, R->b_row, n,
+                      L->dist, mind, best);
+        }
+        if (nA > 0)
+            XM_LAUNCH("k_lvl_finish", grid_of(nA), kBlock, 0, s, k_lvl_finish, nA, n_scales, mind,
+                      best, L->n_within, L->best_b, L->best_dist);
+        return XM_OK;
+    };
+    const xm_status st = body();
+    dev_free(a64, s);
+    dev_free(w, s);
+    if (st != XM_OK) {
+        dev_free(base, s);
+        delete L;
+        return st;
+    }
+    *out = L;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_levels_free(xm_levels* L) {
+    if (!L) return XM_OK;
+    dev_free(L->dist, L->stream);
+    delete L;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_levels_get(const xm_levels* L, xm_levels_view* v) {
+    if (!L || !v) return set_error(XM_EINVAL, "xm_levels_get: NULL argument");
+    v->n_pairs = L->n_pairs;
+    v->n_a = L->n_a;
+    v->n_scales = L->n_scales;
+    v->dist = L->dist;
+    v->best_b_row = L->best_b;
+    v->best_dist = L->best_dist;
+    v->level = L->level;
+    v->n_within = L->n_within;
+    return XM_OK;
+}

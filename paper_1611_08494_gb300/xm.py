@@ -61,6 +61,11 @@ class ResultView(ctypes.Structure):
                 ("sep_arcsec", _p), ("count", _p), ("best_b_row", _p), ("best_sep_arcsec", _p)]
 
 
+class LevelsView(ctypes.Structure):
+    _fields_ = [("n_pairs", _i64), ("n_a", _i64), ("n_scales", _i32), ("dist", _p),
+                ("best_b_row", _p), ("best_dist", _p), ("level", _p), ("n_within", _p)]
+
+
 class RowsView(ctypes.Structure):
     _fields_ = [("n", _i64), ("a_row", _p), ("b_row", _p), ("sep_arcsec", _p),
                 ("n_unmatched_a", _i64), ("n_unmatched_b", _i64)]
@@ -110,6 +115,10 @@ xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
 xm_pick_pairs = _sig("xm_pick_pairs", _i32, _p, _p, _i32, _p, ctypes.POINTER(_p))
 xm_match_values = _sig("xm_match_values", _i32, _p, _i64, _p, _i64, _i32, _i32, _i32, _p,
                        ctypes.POINTER(_p))
+xm_levels_compute = _sig("xm_levels_compute", _i32, _p, _p, ctypes.POINTER(_f64), _i32, _p,
+                         ctypes.POINTER(_p))
+xm_levels_free = _sig("xm_levels_free", _i32, _p)
+xm_levels_get = _sig("xm_levels_get", _i32, _p, ctypes.POINTER(LevelsView))
 KEY_INT64, KEY_FLOAT64 = 0, 1
 PICKS = {"best_b": 1, "mutual": 2}
 
@@ -292,6 +301,12 @@ class Result:
     def join(self, join_type: str, selection=SEL_ALL, stream=None) -> "Rows":
         return Rows(self, join_type, selection, stream)
 
+    def levels(self, scales=(), stream=None) -> "Levels":
+        """Normalised distance of every pair, the best pair per A source by
+        it, and the levels of concentric copies of the regions scaled by
+        ``scales`` (increasing, in (0, 1]). ``xm_levels_compute``."""
+        return Levels(self, scales, stream)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:
@@ -328,6 +343,54 @@ class ValueResult(Result):
         self.view = v
         self.n_pairs, self.n_a, self.n_b = v.n_pairs, v.n_a, v.n_b
         self._keep = keep
+
+
+class Levels:
+    """Normalised distances and concentric levels of a result (paper §2.2,
+    §3). ``xm_levels_compute``; device tensors as views."""
+
+    def __init__(self, result: Result, scales=(), stream=None):
+        sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).reshape(-1))
+        h = _p()
+        ptr = sc.ctypes.data_as(ctypes.POINTER(_f64)) if sc.size else None
+        check(xm_levels_compute(result.index.handle if result.index else None, result.handle, ptr,
+                                int(sc.size), _stream_handle(stream), ctypes.byref(h)),
+              "xm_levels_compute")
+        self.handle = h.value
+        self.result = result
+        v = LevelsView()
+        check(xm_levels_get(self.handle, ctypes.byref(v)), "xm_levels_get")
+        self.view = v
+        self.n_pairs, self.n_a, self.n_scales = v.n_pairs, v.n_a, v.n_scales
+
+    @property
+    def dist(self):
+        return _tensor(self.view.dist, self.n_pairs, "<f8", self)
+
+    @property
+    def best_b(self):
+        return _tensor(self.view.best_b_row, self.n_a, "<i8", self)
+
+    @property
+    def best_dist(self):
+        return _tensor(self.view.best_dist, self.n_a, "<f8", self)
+
+    @property
+    def level(self):
+        return _tensor(self.view.level, self.n_pairs if self.n_scales else 0, "<i4", self)
+
+    @property
+    def n_within(self):
+        """int32 [n_a, n_scales]: members inside each copy."""
+        t = _tensor(self.view.n_within, self.n_a * self.n_scales if self.n_scales else 0, "<i4",
+                    self)
+        return t.view(self.n_a, self.n_scales) if self.n_scales else t
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            xm_levels_free(h)
+            self.handle = None
 
 
 class Rows:
