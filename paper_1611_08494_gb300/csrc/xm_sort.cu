@@ -4,14 +4,15 @@
 // catalogue to a cell; here the assignment is realised by sorting sources on
 // a (zone, RA) key. The sort is a stable least-significant-digit radix sort
 // with 8-bit digits: one kernel counts the digits of every pass at once
-// (they do not depend on the order of the keys), then one kernel per pass in
-// the single-kernel Onesweep form: tiles of 4096 keys take ids in launch
-// order, rank their keys stably with warp-level match (lanes with equal
-// digits), publish their per-digit counts, add the counts of earlier tiles by
-// a decoupled look-back (bounded, see kSpinLimit), and scatter through shared
-// memory so stores of one digit are contiguous.
+// (they do not depend on the order of the keys) and turns the counts into
+// output offsets, then one kernel per pass in the single-kernel Onesweep
+// form: tiles of 4096 keys take ids in launch order, rank their keys stably
+// per warp (lanes with equal digits found by one vote per digit bit), publish
+// their per-digit counts, add the counts of earlier tiles by a decoupled
+// look-back (bounded, see kSpinLimit), and scatter through shared memory so
+// stores of one digit are contiguous.
 // Prefix sums are reduce-then-scan over tiles of 4096 elements, applied
-// recursively to the tile sums.
+// recursively to the tile sums, or a single chained pass.
 #include <mutex>
 
 #include "xm_internal.cuh"
@@ -26,26 +27,6 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
 
-// Digit histograms of every pass at once (they do not depend on the order of
-// the keys): hist[p * 256 + d] counts keys whose digit p is d.
-__global__ void __launch_bounds__(kSortThreads) k_all_hist(const uint64_t* __restrict__ keys,
-                                                           int64_t n, int begin_bit, int passes,
-                                                           unsigned long long* __restrict__ hist) {
-    __shared__ uint32_t h[8][kRadix];
-    for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kSortThreads) {
-        const uint64_t k = keys[i] >> begin_bit;
-        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
-        const uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(&hist[i], (unsigned long long)v);
-    }
-}
-
 // The virtual key of an index key under a plan.
 __device__ __forceinline__ uint64_t plan_key(const SortPlan& P, uint64_t key) {
     const uint32_t z = (uint32_t)(key >> 32);
@@ -54,24 +35,53 @@ __device__ __forceinline__ uint64_t plan_key(const SortPlan& P, uint64_t key) {
     return ((uint64_t)(z - P.zmin) << P.rb) | (ra & rmask);
 }
 
-// Histograms of the plan's virtual-key digits, as k_all_hist.
-__global__ void __launch_bounds__(kSortThreads) k_plan_hist(const uint64_t* __restrict__ keys,
-                                                            int64_t n, const SortPlan* plan,
-                                                            int passes,
-                                                            unsigned long long* __restrict__ hist) {
+// Digit histograms of every pass at once (they do not depend on the order of
+// the keys): hist[p * 256 + d] counts keys whose digit p is d; the digits are
+// those of key >> begin_bit, or of the plan's virtual key. The last block to
+// finish turns every pass's counts into exclusive offsets (the first output
+// slot of each digit), so the passes need not scan them.
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t* __restrict__ keys,
+                                                             int64_t n, int begin_bit,
+                                                             const SortPlan* plan, int passes,
+                                                             unsigned long long* hist,
+                                                             unsigned int* done) {
     __shared__ uint32_t h[8][kRadix];
+    __shared__ bool last;
     for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const SortPlan P = *plan;
+    SortPlan P{};
+    if (plan) P = *plan;
     for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * kSortThreads) {
-        const uint64_t k = plan_key(P, keys[i]);
+        const uint64_t k = plan ? plan_key(P, keys[i]) : keys[i] >> begin_bit;
         for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
         const uint32_t v = (&h[0][0])[i];
         if (v) atomicAdd(&hist[i], (unsigned long long)v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < passes) {  // one warp per pass: exclusive scan of its 256 counts
+        unsigned long long* row = hist + warp * kRadix;
+        unsigned long long v[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { v[j] = __ldcg(row + lane * 8 + j); sum += v[j]; }
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        unsigned long long run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { row[lane * 8 + j] = run; run += v[j]; }
     }
 }
 
@@ -120,8 +130,8 @@ struct OnesweepSmem {
     uint32_t vals[kSortTile];
     int32_t wcount[kWarps][kRadix];  // per-warp digit counts, then warp offsets
     int32_t dstart[kRadix];          // tile-local start of each digit
-    int64_t gstart[kRadix];          // global start of each digit for this tile
-    int64_t pass_off[kRadix];        // first output slot of each digit in the pass
+    int64_t gstart[kRadix];          // global start of each digit for this tile, less its
+                                     // tile-local start (output slot = gstart[d] + p)
     int tile;
 };
 
@@ -132,9 +142,9 @@ struct OnesweepSmem {
 // an inclusive prefix, then scatter through shared memory. A walk that finds
 // no progress for kSpinLimit polls flags a timeout and carries on, so no
 // block can wait forever; the caller turns the flag into XM_ETIMEOUT.
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
-    int shift, const unsigned long long* __restrict__ hist, uint64_t* status,
+    int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
     int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats) {
     // with a plan: the digit of pass `pass` of the virtual key, and nothing
@@ -153,20 +163,6 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         if (S.tile == 0 && stats) atomicAdd(&stats[5], (unsigned long long)n);  // keys this pass
     }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
-    if (threadIdx.x < 32) {  // exclusive scan of the pass histogram (256 digits)
-        int64_t v[8], sum = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j++) { v[j] = (int64_t)hist[lane * 8 + j]; sum += v[j]; }
-        int64_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int64_t run = incl - sum;
-#pragma unroll
-        for (int j = 0; j < 8; j++) { S.pass_off[lane * 8 + j] = run; run += v[j]; }
-    }
     __syncthreads();
     const int tile = S.tile;
     const int64_t tile_base = (int64_t)tile * kSortTile;
@@ -186,16 +182,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         const bool valid = warp_base + 32 * k + lane < n;
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        rank[k] = -1;
-        if (valid) {
-            const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
-            const uint32_t peers = __match_any_sync(vmask, d);
-            const int32_t before = S.wcount[warp][d];
-            rank[k] = before + __popc(peers & lt_mask);
-            __syncwarp(vmask);
-            if ((peers & lt_mask) == 0) S.wcount[warp][d] = before + __popc(peers);
+        const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
+        // lanes holding the same digit: one vote per digit bit (the
+        // multisplit form), cheaper than a match instruction
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const uint32_t vote = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? vote : ~vote;
         }
+        // every lane reads its digit's count, then the first lane of each
+        // digit adds the digit's lanes (no per-digit synchronisation, which
+        // would run the digits' lanes one group after another)
+        const int32_t before = valid ? S.wcount[warp][d] : 0;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0) S.wcount[warp][d] = before + __popc(peers);
+        rank[k] = valid ? before + __popc(peers & lt_mask) : -1;
         __syncwarp();
     }
     __syncthreads();
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             }
             st_relaxed(my, kStInc | (uint64_t)(prefix + run));
         }
-        S.gstart[d] = S.pass_off[d] + prefix;
+        S.gstart[d] = (int64_t)offs[d] + prefix;
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the 256 tile counts by one warp
@@ -265,6 +267,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         for (int j = 0; j < 8; j++) { S.dstart[lane * 8 + j] = run; run += v[j]; }
     }
     __syncthreads();
+    if (threadIdx.x < kRadix) S.gstart[threadIdx.x] -= S.dstart[threadIdx.x];
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         if (rank[k] >= 0) {
@@ -277,12 +280,16 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     __syncthreads();
     int64_t valid_n = n - tile_base;
     if (valid_n > kSortTile) valid_n = kSortTile;
-    for (int p = threadIdx.x; p < valid_n; p += kSortThreads) {
-        const uint64_t kk = S.keys[p];
-        const uint32_t d = (uint32_t)((planned ? plan_key(P, kk) : kk) >> shift) & 0xFF;
-        const int64_t g = S.gstart[d] + (p - S.dstart[d]);
-        keys_out[g] = kk;
-        vals_out[g] = S.vals[p];
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        const int p = threadIdx.x + j * kSortThreads;
+        if (p < valid_n) {
+            const uint64_t kk = S.keys[p];
+            const uint32_t d = (uint32_t)((planned ? plan_key(P, kk) : kk) >> shift) & 0xFF;
+            const int64_t g = S.gstart[d] + p;
+            keys_out[g] = kk;
+            vals_out[g] = S.vals[p];
+        }
     }
 }
 
@@ -548,10 +555,11 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
     if (e != cudaSuccess) st = cuda_fail(e, "index sort memset");
     if (st == XM_OK) {
         const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
-        launch_begin("k_plan_hist", s);
-        k_plan_hist<<<hg, kSortThreads, 0, s>>>(keys, n, plan, passes, hist);
-        e = launch_end("k_plan_hist", s);
-        if (e != cudaSuccess) st = cuda_fail(e, "k_plan_hist");
+        launch_begin("k_digit_hist", s);
+        // (counters + passes: a spare word of the zeroed work area)
+        k_digit_hist<<<hg, kSortThreads, 0, s>>>(keys, n, 0, plan, passes, hist, counters + passes);
+        e = launch_end("k_digit_hist", s);
+        if (e != cudaSuccess) st = cuda_fail(e, "k_digit_hist");
     }
     uint64_t *ki = keys, *ko = tk;
     uint32_t *vi = vals, *vo = tv;
@@ -575,7 +583,8 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     const int passes = (end_bit - begin_bit + 7) / 8;
     if (passes > 8) return set_error(XM_EINVAL, "radix sort: more than 64 key bits");
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    // per pass: 256 histogram counters, ntiles x 256 status words, 1 counter
+    // per pass: 256 histogram counters (then offsets), ntiles x 256 status
+    // words, a tile counter; plus the histogram kernel's completion counter
     const size_t st_words = (size_t)ntiles * kRadix;
     const size_t bytes = passes * (kRadix * sizeof(unsigned long long) + st_words * sizeof(uint64_t) +
                                    sizeof(uint64_t)) + 16;
@@ -593,10 +602,11 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     uint32_t *vi = vals, *vo = tv;
     if (st == XM_OK) {
         const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
-        launch_begin("k_all_hist", s);
-        k_all_hist<<<hg, kSortThreads, 0, s>>>(keys, n, begin_bit, passes, hist);
-        e = launch_end("k_all_hist", s);
-        if (e != cudaSuccess) st = cuda_fail(e, "k_all_hist");
+        launch_begin("k_digit_hist", s);
+        k_digit_hist<<<hg, kSortThreads, 0, s>>>(keys, n, begin_bit, (const SortPlan*)nullptr,
+                                                 passes, hist, counters + passes);
+        e = launch_end("k_digit_hist", s);
+        if (e != cudaSuccess) st = cuda_fail(e, "k_digit_hist");
     }
     for (int p = 0; p < passes && st == XM_OK; p++) {
         launch_begin("k_onesweep", s);
