@@ -142,7 +142,8 @@ struct OnesweepSmem {
 // an inclusive prefix, then scatter through shared memory. A walk that finds
 // no progress for kSpinLimit polls flags a timeout and carries on, so no
 // block can wait forever; the caller turns the flag into XM_ETIMEOUT.
-__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
     int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -523,9 +524,28 @@ void radix_sort_prepare() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> g(mu);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_onesweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(OnesweepSmem));
+    cudaFuncSetAttribute(k_onesweep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(OnesweepSmem));
     done[dev] = true;
+}
+
+// One pass. Large sorts run three tiles per SM (registers capped at 40, a
+// few spilled): more tiles in flight hide more of each tile's latency
+// chain. Sorts of a few waves keep two (no spills, shorter tiles).
+constexpr int64_t kThreeBlockTiles = 2048;
+
+void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* ki,
+                   const uint32_t* vi, int64_t n, int shift, const unsigned long long* offs,
+                   uint64_t* status, unsigned int* counter, uint64_t* ko, uint32_t* vo,
+                   int32_t* err, const SortPlan* plan, int pass) {
+    if (ntiles >= kThreeBlockTiles)
+        k_onesweep<3><<<(unsigned)ntiles, kSortThreads, smem, s>>>(
+            ki, vi, n, shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
+    else
+        k_onesweep<2><<<(unsigned)ntiles, kSortThreads, smem, s>>>(
+            ki, vi, n, shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
 }
 
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
@@ -565,9 +585,8 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
     uint32_t *vi = vals, *vo = tv;
     for (int p = 0; p < passes && st == XM_OK; p++) {
         launch_begin("k_onesweep", s);
-        k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, s>>>(
-            ki, vi, n, 8 * p, hist + p * kRadix, status + p * st_words, counters + p, ko, vo, err,
-            plan, p, device_stats());
+        onesweep_pass(ntiles, smem, s, ki, vi, n, 8 * p, hist + p * kRadix, status + p * st_words,
+                      counters + p, ko, vo, err, plan, p);
         e = launch_end("k_onesweep", s);
         if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;
@@ -610,9 +629,8 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     }
     for (int p = 0; p < passes && st == XM_OK; p++) {
         launch_begin("k_onesweep", s);
-        k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, s>>>(
-            ki, vi, n, begin_bit + 8 * p, hist + p * kRadix, status + p * st_words, counters + p,
-            ko, vo, err, (const SortPlan*)nullptr, p, device_stats());
+        onesweep_pass(ntiles, smem, s, ki, vi, n, begin_bit + 8 * p, hist + p * kRadix,
+                      status + p * st_words, counters + p, ko, vo, err, nullptr, p);
         e = launch_end("k_onesweep", s);
         if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;
