@@ -373,8 +373,9 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
 
 // Single-pass exclusive scan: tiles take ids in launch order, scan their
 // 4096 elements in blocked order, publish their sum, and add the sums of
-// earlier tiles by a decoupled look-back (bounded like the sort's; a timeout
-// sets kErrTimeout in *err). The last tile writes the total.
+// earlier tiles by a decoupled look-back in which one warp reads 32
+// predecessors' words per step (bounded like the sort's; a timeout sets
+// kErrTimeout in *err). The last tile writes the total.
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_chained(
     const T* __restrict__ in, int64_t n, int64_t* __restrict__ out, int64_t* __restrict__ total,
@@ -409,34 +410,44 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chained(
         if (w < warp) woff += warp_tot[w];
         all += warp_tot[w];
     }
-    if (threadIdx.x == 0) {
+    if (warp == 0) {  // publish, then look back 32 tiles per step
         uint64_t* my = status + tile;
         int64_t prefix = 0;
         if (tile == 0) {
-            st_relaxed(my, kStInc | (uint64_t)all);
+            if (lane == 0) st_relaxed(my, kStInc | (uint64_t)all);
         } else {
-            st_relaxed(my, kStAgg | (uint64_t)all);
-            int64_t t = tile - 1;
+            if (lane == 0) st_relaxed(my, kStAgg | (uint64_t)all);
+            int64_t top = tile - 1;  // lane j reads tile top - j (before tile 0: an inclusive 0)
             int spins = 0;
-            while (t >= 0) {
-                const uint64_t w = ld_relaxed(status + t);
+            while (true) {
+                const int64_t j = top - lane;
+                const uint64_t w = j >= 0 ? ld_relaxed(status + j) : kStInc;
                 const uint64_t flag = w & ~kStMask;
-                if (flag == 0) {
+                const uint32_t inc = __ballot_sync(0xffffffffu, flag == kStInc);
+                const uint32_t unready = __ballot_sync(0xffffffffu, flag == 0);
+                const int first = inc ? __ffs(inc) - 1 : 31;  // words needed: lanes 0..first
+                const uint32_t need = first == 31 ? 0xffffffffu : ((1u << (first + 1)) - 1u);
+                if (unready & need) {
                     if (++spins > kSpinLimit) {
-                        atomicOr(err, kErrTimeout);
+                        if (lane == 0) atomicOr(err, kErrTimeout);
                         break;
                     }
                     __nanosleep(64);
                     continue;
                 }
-                prefix += (int64_t)(w & kStMask);
-                if (flag == kStInc) break;
-                t--;
+                int64_t v = lane <= first ? (int64_t)(w & kStMask) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                prefix += v;
+                if (inc) break;
+                top -= 32;
             }
-            st_relaxed(my, kStInc | (uint64_t)(prefix + all));
+            if (lane == 0) st_relaxed(my, kStInc | (uint64_t)(prefix + all));
         }
-        tile_prefix = prefix;
-        if (total && (tile + 1) * kScanTile >= n) *total = prefix + all;
+        if (lane == 0) {
+            tile_prefix = prefix;
+            if (total && (tile + 1) * kScanTile >= n) *total = prefix + all;
+        }
     }
     __syncthreads();
     int64_t run = tile_prefix + woff + incl - sum;
