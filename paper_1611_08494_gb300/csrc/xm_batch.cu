@@ -84,6 +84,7 @@ __device__ __forceinline__ void batch_position(const BatchConst& C, const ReqDev
 
 __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
                                uint32_t* __restrict__ vals, int32_t* err, int32_t* bad_req) {
+    pdl_wait();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= C.total) return;
     const int32_t r = find_req(C.off, C.n_req, g);
@@ -112,6 +113,7 @@ __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
 __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
                              APrep* __restrict__ out, ACold* __restrict__ cold,
                              int32_t* __restrict__ lrow) {
+    pdl_wait();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= C.total) return;
     const int64_t g = vals ? (int64_t)vals[s] : s;
@@ -142,6 +144,7 @@ __device__ __forceinline__ bool jt_un_b(int t) {
 // A-side rows of each batch row's join, and unmatched A sources per request.
 __global__ void k_batch_rows_a(BatchConst C, const int32_t* __restrict__ count,
                                int32_t* __restrict__ rows, unsigned long long* __restrict__ req_un_a) {
+    pdl_wait();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= C.total) return;
     const int32_t r = find_req(C.off, C.n_req, g);
@@ -167,6 +170,7 @@ __global__ void k_batch_write_a(BatchConst C, const int32_t* __restrict__ count,
                                 const int64_t* __restrict__ row_off, long long row_cap,
                                 int64_t* __restrict__ oa, int64_t* __restrict__ ob,
                                 double* __restrict__ os) {
+    pdl_wait();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= C.total) return;
     const int32_t r = find_req(C.off, C.n_req, g);
@@ -216,6 +220,7 @@ __global__ void k_batch_matched_b(BatchConst C, const int32_t* __restrict__ coun
                                   const int64_t* __restrict__ best_b, uint64_t* __restrict__ table,
                                   uint64_t mask, unsigned long long* __restrict__ req_mb,
                                   int32_t* err) {
+    pdl_wait();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= C.total) return;
     const int32_t r = find_req(C.off, C.n_req, g);
@@ -251,6 +256,7 @@ __global__ void k_batch_matched_b(BatchConst C, const int32_t* __restrict__ coun
 __global__ void k_req_bounds(BatchConst C, const int64_t* __restrict__ pair_off,
                              const int64_t* __restrict__ row_off, const int64_t* totals,
                              int64_t* __restrict__ out) {
+    pdl_wait();
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= C.n_req) return;
     const int64_t b = C.off[r], e = C.off[r + 1];

@@ -34,6 +34,7 @@ namespace {
 constexpr int kBlock = 256;
 
 __global__ void k_zone_geom(int32_t nz, ZoneInfo* __restrict__ zones) {
+    pdl_wait();
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
     const double h = kPi / nz;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_ingest_b(
     uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, double2* __restrict__ pos,
     double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz, SortPlan* plan,
     int32_t* err) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool has = i < n;
     uint32_t z = 0, ra = 0;
@@ -150,6 +152,7 @@ struct Sorted {
 };
 
 __global__ void k_zone_start(Sorted S, int64_t n, int32_t nz, int64_t* __restrict__ zone_start) {
+    pdl_wait();
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z > nz) return;
     const uint64_t* __restrict__ keys = S.keys();
@@ -165,6 +168,7 @@ __global__ void k_zone_start(Sorted S, int64_t n, int32_t nz, int64_t* __restric
 
 __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, Sorted S,
                             ZoneInfo* __restrict__ zones, int32_t* __restrict__ lut_cnt) {
+    pdl_wait();
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
     const uint64_t* __restrict__ keys = S.keys();
@@ -191,6 +195,7 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, 
 
 __global__ void k_zone_lut(int32_t nz, const int64_t* __restrict__ lut_off,
                            ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut) {
+    pdl_wait();
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
     const int64_t base = lut_off[z];
@@ -226,6 +231,7 @@ __global__ void k_gather_b(Sorted S, int64_t n, const double2* __restrict__ pos,
                            BRec* __restrict__ rec, LutGap* __restrict__ gaps,
                            unsigned long long* __restrict__ n_gaps, long long gap_cap,
                            int32_t* err) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t* __restrict__ keys = S.keys();
@@ -255,6 +261,7 @@ __global__ void k_gather_b(Sorted S, int64_t n, const double2* __restrict__ pos,
 // The long runs of the bucket tables, one block per run.
 __global__ void k_gap_fill(const LutGap* __restrict__ gaps, const unsigned long long* n_gaps,
                            long long gap_cap, uint32_t* __restrict__ lut) {
+    pdl_wait();
     const long long ng = min((long long)*n_gaps, gap_cap);
     for (long long g = blockIdx.x; g < ng; g += gridDim.x) {
         const LutGap G = gaps[g];

@@ -36,6 +36,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <utility>
+
 #include "xm.h"
 
 namespace xm {
@@ -382,11 +384,37 @@ void dev_free(void* p, cudaStream_t s);
 void launch_begin(const char* name, cudaStream_t s);
 cudaError_t launch_end(const char* name, cudaStream_t s);
 
+// Every kernel of the library starts with pdl_wait(), and launches go out
+// with programmatic dependent launch: a kernel may be scheduled while the one
+// before it in the stream drains, and waits there (before any global memory
+// access) until that grid has completed and its writes are visible. Without a
+// programmatic predecessor the wait returns at once. This removes most of the
+// gap between the many short dependent kernels of a call.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 #define XM_LAUNCH(name, grid, block, smem, stream, kernel, ...)             \
     do {                                                                    \
         ::xm::launch_begin(name, stream);                                   \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);         \
+        const cudaError_t _l = ::xm::launch_pdl(kernel, dim3(grid), dim3(block), (smem), \
+                                                (stream), __VA_ARGS__);     \
         cudaError_t _e = ::xm::launch_end(name, stream);                    \
+        if (_l != cudaSuccess) _e = _l;                                     \
         if (_e != cudaSuccess) return ::xm::cuda_fail(_e, name);            \
     } while (0)
 

@@ -25,6 +25,7 @@ constexpr int kBlock = 256;
 unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 __global__ void k_mark_b(const int64_t* __restrict__ b_row, int64_t n, uint32_t* __restrict__ bits) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t b = b_row[i];
@@ -35,6 +36,7 @@ __global__ void k_mark_b(const int64_t* __restrict__ b_row, int64_t n, uint32_t*
 __global__ void k_rows_a(const int32_t* __restrict__ count, int64_t nA, int sel_all,
                          int with_pairs, int with_un_a, int32_t* __restrict__ rows,
                          unsigned long long* __restrict__ n_un_a) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
     int32_t c = count[i];
@@ -54,6 +56,7 @@ __device__ __forceinline__ uint32_t word_valid(int64_t w, int64_t nB) {
 
 __global__ void k_word_unmatched(const uint32_t* __restrict__ bits, int64_t nwords, int64_t nB,
                                  int32_t* __restrict__ wcount) {
+    pdl_wait();
     int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwords) return;
     wcount[w] = __popc(~bits[w] & word_valid(w, nB));
@@ -67,6 +70,7 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
                           const int64_t* __restrict__ row_off, int64_t nA, int sel_all,
                           int with_pairs, int with_un_a, int pairs_apart, int64_t* __restrict__ oa,
                           int64_t* __restrict__ ob, double* __restrict__ os) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
     int32_t c = count[i];
@@ -101,6 +105,7 @@ __global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __r
                               const int64_t* __restrict__ row_off, int64_t n_pairs,
                               int64_t* __restrict__ oa, int64_t* __restrict__ ob,
                               double* __restrict__ os) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     const int64_t a = pa[p];
@@ -114,6 +119,7 @@ __global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __r
 __global__ void k_write_b(const uint32_t* __restrict__ bits, const int64_t* __restrict__ word_off,
                           int64_t nB, const int64_t* __restrict__ base_ptr, int64_t* __restrict__ oa,
                           int64_t* __restrict__ ob, double* __restrict__ os) {
+    pdl_wait();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nB) return;
     const int64_t base = *base_ptr;

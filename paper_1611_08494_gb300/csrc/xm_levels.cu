@@ -49,6 +49,7 @@ constexpr int kBlock = 256;
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
 
 __global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, A64* __restrict__ out) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = make_a64(acold[i]);
@@ -60,6 +61,7 @@ __global__ void k_lvl_pair(IndexGeom G, const A64* __restrict__ a64,
                            int64_t n, Scales S, double* __restrict__ dist,
                            int32_t* __restrict__ level, int32_t* __restrict__ within,
                            unsigned long long* __restrict__ mind) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t a = pa[p];
@@ -89,6 +91,7 @@ __global__ void k_lvl_best(const int64_t* __restrict__ pa, const int64_t* __rest
                            int64_t n, const double* __restrict__ dist,
                            const unsigned long long* __restrict__ mind,
                            unsigned long long* __restrict__ best) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t a = pa[p];
@@ -99,6 +102,7 @@ __global__ void k_lvl_finish(int64_t n_a, int32_t k, const unsigned long long* _
                              const unsigned long long* __restrict__ best,
                              int32_t* __restrict__ within, int64_t* __restrict__ best_b,
                              double* __restrict__ best_dist) {
+    pdl_wait();
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n_a) return;
     const bool has = best[a] != ~0ull;

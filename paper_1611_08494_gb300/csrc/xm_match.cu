@@ -74,6 +74,7 @@ struct Temps {
 // a_slot[row] = position of A row `row` in the sorted order.
 __global__ void k_slot_of_row(const uint32_t* __restrict__ vals, int64_t n,
                               int32_t* __restrict__ a_slot) {
+    pdl_wait();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) a_slot[vals[s]] = (int32_t)s;
 }

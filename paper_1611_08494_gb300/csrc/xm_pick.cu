@@ -30,6 +30,7 @@ __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_
 
 __global__ void k_pick_min(const int64_t* __restrict__ pb, const double* __restrict__ ps,
                            int64_t n, unsigned long long* __restrict__ minbits) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     atomicMin(&minbits[pb[p]], (unsigned long long)dbits(ps[p]));
@@ -38,6 +39,7 @@ __global__ void k_pick_min(const int64_t* __restrict__ pb, const double* __restr
 __global__ void k_pick_cont(const int64_t* __restrict__ pb, const double* __restrict__ ps,
                             int64_t n, const unsigned long long* __restrict__ minbits,
                             int32_t* __restrict__ ncont, unsigned long long* __restrict__ first) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t b = pb[p];
@@ -74,6 +76,7 @@ __global__ void k_pick_exact(IndexGeom G, const ACold* __restrict__ acold,
                              const unsigned long long* __restrict__ minbits,
                              const int32_t* __restrict__ ncont,
                              unsigned long long* __restrict__ min64) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t b = pb[p];
@@ -90,6 +93,7 @@ __global__ void k_pick_first(IndexGeom G, const ACold* __restrict__ acold,
                              const int32_t* __restrict__ ncont,
                              const unsigned long long* __restrict__ min64,
                              unsigned long long* __restrict__ first_exact) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t b = pb[p];
@@ -107,6 +111,7 @@ __global__ void k_pick_flag(const int64_t* __restrict__ pa, const int64_t* __res
                             const unsigned long long* __restrict__ first_exact,
                             const int64_t* __restrict__ best_b, int mutual,
                             int32_t* __restrict__ flag) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t b = pb[p];
@@ -121,6 +126,7 @@ __global__ void k_pick_write(const int64_t* __restrict__ pa, const int64_t* __re
                              const int32_t* __restrict__ flag, const int64_t* __restrict__ off,
                              int64_t* __restrict__ oa, int64_t* __restrict__ ob,
                              double* __restrict__ os) {
+    pdl_wait();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n || !flag[p]) return;
     const int64_t o = off[p];

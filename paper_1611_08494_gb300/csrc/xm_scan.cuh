@@ -108,6 +108,7 @@ __device__ __forceinline__ bool size_ok(double a, double b, double pa) {
 
 __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                            int32_t* err) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I.n) return;
     double lon, lat, gamma;
@@ -193,6 +194,7 @@ __device__ __forceinline__ void make_aprep(double lon, double lat, double gamma,
 // harmless).
 __global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __restrict__ out,
                          ACold* __restrict__ cold, int32_t* err) {
+    pdl_wait();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= I.n) return;
     const int64_t i = vals ? (int64_t)vals[s] : s;
@@ -459,6 +461,7 @@ struct ScanWarpSmem {
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char scan_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ScanWarpSmem& W = reinterpret_cast<ScanWarpSmem*>(scan_smem)[warp];
@@ -792,6 +795,7 @@ __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long
                         const int32_t* __restrict__ lrow, long long out_cap,
                         int64_t* __restrict__ out_a, int64_t* __restrict__ out_b,
                         double* __restrict__ out_sep) {
+    pdl_wait();
     const long long n = min((long long)*n_rec, cap);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -816,6 +820,7 @@ __global__ void __launch_bounds__(256) k_sort_small(const int32_t* __restrict__ 
                                                     int64_t nA, long long out_cap,
                                                     int64_t* __restrict__ out_b,
                                                     double* __restrict__ out_sep) {
+    pdl_wait();
     static_assert(kSmallSort == 16, "one row per half-warp");
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -861,6 +866,7 @@ constexpr int kWarpSortWarps = 4;
 __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
     const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off, int64_t nA,
     long long out_cap, int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+    pdl_wait();
     __shared__ int64_t sb[kWarpSortWarps][kWarpSort];
     __shared__ double ss[kWarpSortWarps][kWarpSort];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -902,6 +908,7 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ co
                                                   const int64_t* __restrict__ pair_off, int64_t nA,
                                                   long long out_cap, int64_t* __restrict__ out_b,
                                                   double* __restrict__ out_sep) {
+    pdl_wait();
     __shared__ int64_t kb[kSegMax];
     __shared__ double ks[kSegMax];
     __shared__ int32_t found[256];
@@ -962,6 +969,7 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ co
 // permute the segment through a scratch copy.
 __global__ void k_seg_keys(const int64_t* __restrict__ b, int64_t n, uint64_t* __restrict__ keys,
                            uint32_t* __restrict__ vals) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     keys[i] = (uint64_t)b[i];
@@ -971,6 +979,7 @@ __global__ void k_seg_keys(const int64_t* __restrict__ b, int64_t n, uint64_t* _
 __global__ void k_seg_permute(const uint32_t* __restrict__ vals, int64_t n,
                               const int64_t* __restrict__ b_in, const double* __restrict__ s_in,
                               int64_t* __restrict__ b_out, double* __restrict__ s_out) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     b_out[i] = b_in[vals[i]];

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t* __r
                                                              const SortPlan* plan, int passes,
                                                              unsigned long long* hist,
                                                              unsigned int* done) {
+    pdl_wait();
     __shared__ uint32_t h[8][kRadix];
     __shared__ bool last;
     for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
@@ -86,12 +87,14 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t* __r
 }
 
 __global__ void k_plan_init(SortPlan* plan) {
+    pdl_wait();
     *plan = SortPlan{0xFFFFFFFFu, 0u, 0xFFFFFFFFu, 0u, 0u, 0u};
 }
 
 // The plan from the accumulated ranges: bits of the zone offset and of the
 // varying RA bits, passes needed (none for no keys).
 __global__ void k_plan_finish(SortPlan* plan) {
+    pdl_wait();
     SortPlan P = *plan;
     if (P.zmin > P.zmax) {
         P.rb = 0;
@@ -148,6 +151,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
     int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
     int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats) {
+    pdl_wait();
     // with a plan: the digit of pass `pass` of the virtual key, and nothing
     // to do past the passes the plan needs (uniform over the grid)
     SortPlan P{};
@@ -317,6 +321,7 @@ __device__ __forceinline__ int64_t block_sum(int64_t v) {
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const T* __restrict__ in, int64_t n,
                                                             int64_t* __restrict__ sums) {
+    pdl_wait();
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t v = 0;
 #pragma unroll 4
@@ -335,6 +340,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
                                                             const int64_t* __restrict__ tile_offs,
                                                             int64_t* __restrict__ out,
                                                             int64_t* __restrict__ total) {
+    pdl_wait();
     __shared__ int64_t warp_tot[kScanThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
@@ -380,6 +386,7 @@ template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_chained(
     const T* __restrict__ in, int64_t n, int64_t* __restrict__ out, int64_t* __restrict__ total,
     uint64_t* status, unsigned int* tile_counter, int32_t* err) {
+    pdl_wait();
     __shared__ int64_t warp_tot[kScanThreads / 32];
     __shared__ int64_t tile_prefix;
     __shared__ unsigned int tile_s;
@@ -484,8 +491,8 @@ xm_status scan_impl(const T* in, int64_t* out, int64_t n, int64_t* total, int32_
     if (e != cudaSuccess) st = cuda_fail(e, "scan memset");
     if (st == XM_OK) {
         launch_begin("k_scan_chained", s);
-        k_scan_chained<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, total, status,
-                                                                     counter, err);
+        launch_pdl(k_scan_chained<T>, dim3((unsigned)ntiles), dim3(kScanThreads), 0, s, in, n, out,
+                   total, status, counter, err);
         e = launch_end("k_scan_chained", s);
         if (e != cudaSuccess) st = cuda_fail(e, "k_scan_chained");
     }
@@ -552,11 +559,11 @@ void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* 
                    uint64_t* status, unsigned int* counter, uint64_t* ko, uint32_t* vo,
                    int32_t* err, const SortPlan* plan, int pass) {
     if (ntiles >= kThreeBlockTiles)
-        k_onesweep<3><<<(unsigned)ntiles, kSortThreads, smem, s>>>(
-            ki, vi, n, shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
+        launch_pdl(k_onesweep<3>, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n,
+                   shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
     else
-        k_onesweep<2><<<(unsigned)ntiles, kSortThreads, smem, s>>>(
-            ki, vi, n, shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
+        launch_pdl(k_onesweep<2>, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n,
+                   shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
 }
 
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
@@ -588,7 +595,8 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
         const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
         launch_begin("k_digit_hist", s);
         // (counters + passes: a spare word of the zeroed work area)
-        k_digit_hist<<<hg, kSortThreads, 0, s>>>(keys, n, 0, plan, passes, hist, counters + passes);
+        launch_pdl(k_digit_hist, dim3(hg), dim3(kSortThreads), 0, s, keys, n, 0, plan, passes, hist,
+                   counters + passes);
         e = launch_end("k_digit_hist", s);
         if (e != cudaSuccess) st = cuda_fail(e, "k_digit_hist");
     }
@@ -633,8 +641,8 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     if (st == XM_OK) {
         const unsigned hg = (unsigned)(ntiles < 4 * 152 ? ntiles : 4 * 152);
         launch_begin("k_digit_hist", s);
-        k_digit_hist<<<hg, kSortThreads, 0, s>>>(keys, n, begin_bit, (const SortPlan*)nullptr,
-                                                 passes, hist, counters + passes);
+        launch_pdl(k_digit_hist, dim3(hg), dim3(kSortThreads), 0, s, keys, n, begin_bit,
+                   (const SortPlan*)nullptr, passes, hist, counters + passes);
         e = launch_end("k_digit_hist", s);
         if (e != cudaSuccess) st = cuda_fail(e, "k_digit_hist");
     }

@@ -42,6 +42,7 @@ __device__ __forceinline__ uint64_t key_code(const void* keys, int64_t i, int32_
 __global__ void k_val_key(const void* __restrict__ keys, int64_t n, int32_t type,
                           uint64_t* __restrict__ codes, uint32_t* __restrict__ rows,
                           unsigned long long* __restrict__ and_or) {
+    pdl_wait();
     __shared__ unsigned long long s_and, s_or;
     if (threadIdx.x == 0) {
         s_and = ~0ull;
@@ -96,6 +97,7 @@ __device__ __forceinline__ uint32_t val_bucket(const ValLut& V, uint64_t c) {
 __global__ void k_val_lut(const uint64_t* __restrict__ sorted, int64_t n, ValLut V,
                           ValRun* __restrict__ runs, unsigned long long* __restrict__ n_runs,
                           long long run_cap, int32_t* err) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = val_bucket(V, sorted[i]);
@@ -116,6 +118,7 @@ __global__ void k_val_lut(const uint64_t* __restrict__ sorted, int64_t n, ValLut
 
 __global__ void k_val_runs(const ValRun* __restrict__ runs, const unsigned long long* n_runs,
                            long long run_cap, uint32_t* __restrict__ lut) {
+    pdl_wait();
     const long long nr = min((long long)*n_runs, run_cap);
     for (long long r = blockIdx.x; r < nr; r += gridDim.x) {
         const ValRun R = runs[r];
@@ -140,6 +143,7 @@ __global__ void k_val_probe(const void* __restrict__ a_keys, int64_t n_a, int32_
                             int64_t n_b, ValLut V, int32_t* __restrict__ count,
                             int64_t* __restrict__ first, int64_t* __restrict__ best_b,
                             double* __restrict__ best_sep) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_a) return;
     const uint64_t c = key_code(a_keys, i, type);
@@ -164,6 +168,7 @@ __global__ void k_val_emit(const int32_t* __restrict__ count, const int64_t* __r
                            const int64_t* __restrict__ pair_off, const uint32_t* __restrict__ rows,
                            int64_t n_a, int64_t* __restrict__ pa, int64_t* __restrict__ pb,
                            double* __restrict__ ps) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_a) return;
     const int32_t c = count[i];
