@@ -131,6 +131,7 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
 struct OnesweepSmem {
     uint64_t keys[kSortTile];
     uint32_t vals[kSortTile];
+    uint8_t dig[kSortTile];          // digit of each placed key
     int32_t wcount[kWarps][kRadix];  // per-warp digit counts, then warp offsets
     int32_t dstart[kRadix];          // tile-local start of each digit
     int64_t gstart[kRadix];          // global start of each digit for this tile, less its
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
         const int32_t before = valid ? S.wcount[warp][d] : 0;
         __syncwarp();
         if (valid && (peers & lt_mask) == 0) S.wcount[warp][d] = before + __popc(peers);
-        rank[k] = valid ? before + __popc(peers & lt_mask) : -1;
+        // rank within the warp's keys of digit d (< 256), the digit above it
+        rank[k] = valid ? (int32_t)(d << 16) + before + __popc(peers & lt_mask) : -1;
         __syncwarp();
     }
     __syncthreads();
@@ -276,10 +278,11 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         if (rank[k] >= 0) {
-            const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
-            const int32_t p = S.dstart[d] + S.wcount[warp][d] + rank[k];
+            const uint32_t d = (uint32_t)rank[k] >> 16;
+            const int32_t p = S.dstart[d] + S.wcount[warp][d] + (rank[k] & 0xFFFF);
             S.keys[p] = key[k];
             S.vals[p] = vals_in[warp_base + 32 * k + lane];
+            S.dig[p] = (uint8_t)d;
         }
     }
     __syncthreads();
@@ -289,10 +292,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
     for (int j = 0; j < kSortItems; j++) {
         const int p = threadIdx.x + j * kSortThreads;
         if (p < valid_n) {
-            const uint64_t kk = S.keys[p];
-            const uint32_t d = (uint32_t)((planned ? plan_key(P, kk) : kk) >> shift) & 0xFF;
-            const int64_t g = S.gstart[d] + p;
-            keys_out[g] = kk;
+            const int64_t g = S.gstart[S.dig[p]] + p;
+            keys_out[g] = S.keys[p];
             vals_out[g] = S.vals[p];
         }
     }
