@@ -34,8 +34,14 @@ template <int PREC, int MODE>
 xm_status launch_scan_t(const char* name, const ScanArgs& a, int64_t n_units, cudaStream_t s) {
     prepare_kernels();
     const int64_t warps = (n_units + 31) / 32;
-    const unsigned g = (unsigned)((warps + kScanWarps - 1) / kScanWarps);
-    XM_LAUNCH(name, g, kScanThreads, kScanSmem, s, (k_scan<PREC, MODE>), a);
+    int64_t g = (warps + kScanWarps - 1) / kScanWarps;
+    if (a.queue) {  // persistent: at most the blocks that are resident at once
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g > 6LL * sms) g = 6LL * sms;
+    }
+    XM_LAUNCH(name, (unsigned)g, kScanThreads, kScanSmem, s, (k_scan<PREC, MODE>), a);
     return XM_OK;
 }
 
@@ -248,7 +254,7 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             R->acold = (ACold*)dev_alloc(nn * sizeof(ACold), s);
             ACold* cold = R->acold;
             int32_t* lists = T.get<int32_t>(3 * nn);
-            int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts
+            int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts, [4] chunk queue
             int64_t* total = T.get<int64_t>(2);
             unsigned long long* stats = device_stats();
             MemberRec* arena = want_all ? T.get<MemberRec>(arena_cap) : nullptr;
@@ -293,7 +299,11 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             a.list_n = small + 1;
             a.stats = stats;
             a.err = err;
-            xm_status r = launch_scan_any(prec, a, kModeCount, nA, s);
+            // the count pass runs persistent warps that take 32-source chunks
+            // from a queue, so chunks of large regions do not leave a tail
+            ScanArgs cq = a;
+            cq.queue = (unsigned int*)(small + 4);
+            xm_status r = launch_scan_any(prec, cq, kModeCount, nA, s);
             if (r != XM_OK) return r;
             r = exclusive_scan_i32(R->count, R->pair_off, nA, total, err, s);
             if (r != XM_OK) return r;
