@@ -93,6 +93,52 @@ static void keep_pool_cached() {
     done[dev] = true;
 }
 
+// Per host thread: a pinned staging area for small device -> host reads.
+namespace {
+constexpr size_t kStageBytes = 4096;
+struct Stage {
+    unsigned char* p = nullptr;
+    bool tried = false;
+    ~Stage() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local Stage t_stage;
+unsigned char* stage_area() {
+    if (!t_stage.tried) {
+        t_stage.tried = true;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocDefault) == cudaSuccess)
+            t_stage.p = (unsigned char*)p;
+        else
+            cudaGetLastError();  // no pinned memory: plain copies below
+    }
+    return t_stage.p;
+}
+}  // namespace
+
+cudaError_t HostReads::add(void* host_dst, const void* dev_src, size_t bytes) {
+    unsigned char* st = stage_area();
+    const size_t off = (used_ + 15) & ~size_t(15);
+    if (!st || n_ == 8 || off + bytes > kStageBytes)  // (blocks until the copy is done)
+        return cudaMemcpyAsync(host_dst, dev_src, bytes, cudaMemcpyDeviceToHost, s_);
+    const cudaError_t e = cudaMemcpyAsync(st + off, dev_src, bytes, cudaMemcpyDeviceToHost, s_);
+    if (e != cudaSuccess) return e;
+    items_[n_++] = Item{host_dst, off, bytes};
+    used_ = off + bytes;
+    return cudaSuccess;
+}
+
+cudaError_t HostReads::sync() {
+    const cudaError_t e = cudaStreamSynchronize(s_);
+    if (e != cudaSuccess) return e;
+    unsigned char* st = stage_area();
+    for (int i = 0; i < n_; i++) memcpy(items_[i].dst, st + items_[i].off, items_[i].bytes);
+    n_ = 0;
+    used_ = 0;
+    return cudaSuccess;
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 1;
     AllocHook h;

@@ -377,6 +377,27 @@ __device__ __forceinline__ void unit64_deg(double lon, double lat, double* px, d
 // ---------------------------------------------------------------- host side
 
 void* dev_alloc(size_t bytes, cudaStream_t s);
+
+// Small device -> host reads gathered behind one synchronisation: add()
+// queues an asynchronous copy into this host thread's pinned staging area
+// (a copy into pageable memory would block the host once per copy), sync()
+// waits for the stream once and hands the values out.
+class HostReads {
+  public:
+    explicit HostReads(cudaStream_t s) : s_(s) {}
+    cudaError_t add(void* host_dst, const void* dev_src, size_t bytes);
+    cudaError_t sync();
+
+  private:
+    struct Item {
+        void* dst;
+        size_t off, bytes;
+    };
+    cudaStream_t s_;
+    size_t used_ = 0;
+    int n_ = 0;
+    Item items_[8];
+};
 void dev_free(void* p, cudaStream_t s);
 
 // Kernel launch bookkeeping: counts launches and, while profiling is on,

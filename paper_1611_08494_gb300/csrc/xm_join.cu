@@ -286,8 +286,9 @@ static xm_status resolve_rows(xm_rows* J) {
     std::lock_guard<std::mutex> g(g_rows_mu);
     if (!J->pending) return XM_OK;
     int64_t h[5];
-    cudaError_t e = cudaMemcpyAsync(h, J->pending, sizeof(h), cudaMemcpyDeviceToHost, J->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(J->stream);
+    HostReads rd(J->stream);
+    cudaError_t e = rd.add(h, J->pending, sizeof(h));
+    if (e == cudaSuccess) e = rd.sync();
     if (e != cudaSuccess) return cuda_fail(e, "xm_rows_get sync");
     if ((int32_t)h[4] & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_join: scan look-back timed out");
     J->n_unmatched_a = h[2];

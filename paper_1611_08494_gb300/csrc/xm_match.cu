@@ -311,12 +311,11 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             int32_t h_small[8];
             int64_t h_total[2] = {0, 0};
             int32_t h_berr = 0;  // a deferred index build's error bits
-            e = cudaMemcpyAsync(h_small, small, sizeof(h_small), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h_total, total, sizeof(h_total), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && X->build_err)
-                e = cudaMemcpyAsync(&h_berr, X->build_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            HostReads rd(s);
+            e = rd.add(h_small, small, sizeof(h_small));
+            if (e == cudaSuccess) e = rd.add(h_total, total, sizeof(h_total));
+            if (e == cudaSuccess && X->build_err) e = rd.add(&h_berr, X->build_err, sizeof(int32_t));
+            if (e == cudaSuccess) e = rd.sync();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match sync");
             if (h_berr) return index_build_status(h_berr);
             if (h_small[0] & kErrCoord) return set_error(XM_EINVAL, "A: NaN/inf or |lat| > 90");

@@ -192,9 +192,10 @@ extern "C" xm_status xm_pick_pairs(const xm_index* X, const xm_result* R, int32_
         if (st != XM_OK) return st;
         int64_t total = 0;
         int32_t h_err = 0;
-        e = cudaMemcpyAsync(&total, off + n1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        HostReads rd(s);
+        e = rd.add(&total, off + n1, sizeof(int64_t));
+        if (e == cudaSuccess) e = rd.add(&h_err, err, sizeof(int32_t));
+        if (e == cudaSuccess) e = rd.sync();
         if (e != cudaSuccess) return cuda_fail(e, "xm_pick_pairs sync");
         if (h_err & kErrTimeout) return set_error(XM_ETIMEOUT, "xm_pick_pairs: scan look-back timed out");
         J->n = total;
