@@ -147,14 +147,17 @@ __device__ __forceinline__ void make_aprep(double lon, double lat, double gamma,
     P.zfrac = k.zfrac;
     P.row = row;
     P.shape = shape;
+    // (float64 operations are scarce on this GPU: a circle needs one size
+    // and no angle)
+    const bool circle = shape == XM_CIRCLE;
     C.a = a * size_k;
-    C.b = b * size_k;
+    C.b = circle ? C.a : b * size_k;
     // position angle east of north of the input frame, in degrees; gamma
     // turns it to the index frame's north. The float64 angle (for rechecks)
     // is one fused step; the float32 one is reduced to [0, 360) first so the
     // float32 rotation sees a small argument (in float64 only when large).
-    double raw = pa_zero + (pa_dir > 0 ? pa : -pa);
-    C.theta = fma(raw, kDeg, gamma);
+    double raw = circle ? 0.0 : pa_zero + (pa_dir > 0 ? pa : -pa);
+    C.theta = circle ? 0.0 : fma(raw, kDeg, gamma);
     float af = (float)C.a, bf = (float)C.b;
     if (!ok || !(af > 0.0f || C.a > 0.0) || !(bf > 0.0f || C.b > 0.0)) {
         P.R = 0.0f;
@@ -173,11 +176,13 @@ __device__ __forceinline__ void make_aprep(double lon, double lat, double gamma,
         // (rho / s)^2 - 1 <= R^2 / 3 (planar against azimuthal distance)
         const float L_box = 1.42f * P.R + 2.0f * h_f;
         P.g = 128.0f * kEps32 * L_box / fminf(af, bf) + 0.34f * P.R * P.R + 16.0f * kEps32;
-        if (!(fabs(raw) < 720.0)) raw -= 360.0 * floor(raw * (1.0 / 360.0));
-        float tf = (float)raw;
-        tf -= 360.0f * floorf(tf * (1.0f / 360.0f));
-        float st, ct;
-        sincosf(fmaf(tf, 0.017453292519943295f, gamma_f(gamma)), &st, &ct);
+        float st = 0.0f, ct = 1.0f;
+        if (!circle) {
+            if (!(fabs(raw) < 720.0)) raw -= 360.0 * floor(raw * (1.0 / 360.0));
+            float tf = (float)raw;
+            tf -= 360.0f * floorf(tf * (1.0f / 360.0f));
+            sincosf(fmaf(tf, 0.017453292519943295f, gamma_f(gamma)), &st, &ct);
+        }
         const float ia = 1.0f / af, ib = 1.0f / bf;
         P.m00 = st * ia;
         P.m01 = ct * ia;
