@@ -129,8 +129,24 @@ cudaError_t HostReads::add(void* host_dst, const void* dev_src, size_t bytes) {
     return cudaSuccess;
 }
 
+namespace {
+thread_local cudaEvent_t t_read_ev = nullptr;
+}
+
+cudaError_t HostReads::mark() {
+    if (!t_read_ev && cudaEventCreateWithFlags(&t_read_ev, cudaEventDisableTiming) != cudaSuccess) {
+        t_read_ev = nullptr;
+        cudaGetLastError();
+        return cudaSuccess;  // sync() waits for the whole stream instead
+    }
+    const cudaError_t e = cudaEventRecord(t_read_ev, s_);
+    marked_ = e == cudaSuccess;
+    return e;
+}
+
 cudaError_t HostReads::sync() {
-    const cudaError_t e = cudaStreamSynchronize(s_);
+    const cudaError_t e = marked_ ? cudaEventSynchronize(t_read_ev) : cudaStreamSynchronize(s_);
+    marked_ = false;
     if (e != cudaSuccess) return e;
     unsigned char* st = stage_area();
     for (int i = 0; i < n_; i++) memcpy(items_[i].dst, st + items_[i].off, items_[i].bytes);

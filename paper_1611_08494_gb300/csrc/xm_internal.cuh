@@ -386,6 +386,9 @@ class HostReads {
   public:
     explicit HostReads(cudaStream_t s) : s_(s) {}
     cudaError_t add(void* host_dst, const void* dev_src, size_t bytes);
+    // Marks the copies queued so far: sync() then waits for them only, so
+    // work queued on the stream after mark() keeps the GPU busy meanwhile.
+    cudaError_t mark();
     cudaError_t sync();
 
   private:
@@ -396,6 +399,7 @@ class HostReads {
     cudaStream_t s_;
     size_t used_ = 0;
     int n_ = 0;
+    bool marked_ = false;
     Item items_[8];
 };
 void dev_free(void* p, cudaStream_t s);

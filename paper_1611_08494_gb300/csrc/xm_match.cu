@@ -21,6 +21,9 @@ namespace {
 constexpr int kBlock = 256;
 // Scan order when the caller leaves it to the library.
 constexpr bool kDefaultSortedA = false;
+// Largest member arena (records) whose pair list is placed before the pair
+// count is known (the list is then sized by the arena: at most 192 MB).
+constexpr long long kSpeculateRecords = 8LL << 20;
 
 unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -307,7 +310,45 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             if (r != XM_OK) return r;
             r = exclusive_scan_i32(R->count, R->pair_off, nA, total, err, s);
             if (r != XM_OK) return r;
-            // one synchronisation: total pairs, list lengths, error bits
+
+            // the pair list placed (member records -> canonical order) and its
+            // segments sorted, for a list of at most np slots
+            auto place_and_sort = [&](int64_t np, int64_t n_ovf) -> xm_status {
+                XM_LAUNCH("k_place", 4 * 152, 256, 0, s, k_place, arena, arena_n, arena_cap,
+                          R->pair_off, (const int32_t*)nullptr, (long long)np, R->a_row, R->b_row,
+                          R->sep);
+                if (n_ovf > 0) {
+                    ScanArgs b = a;
+                    b.list = lists;
+                    b.nlist = n_ovf;
+                    b.pair_off = R->pair_off;
+                    b.out_a = R->a_row;
+                    b.out_b = R->b_row;
+                    b.out_sep = R->sep;
+                    b.out_cap = np;
+                    xm_status rr = launch_scan_any(prec, b, kModeEmit, n_ovf, s);
+                    if (rr != XM_OK) return rr;
+                }
+                XM_LAUNCH("k_sort_small", grid_for(nA), kBlock, 0, s, k_sort_small, R->count,
+                          R->pair_off, nA, (long long)np, R->b_row, R->sep);
+                const int64_t gw = (nA + 32 * kWarpSortWarps - 1) / (32 * kWarpSortWarps);
+                XM_LAUNCH("k_sort_warp", (unsigned)(gw < 8 * 152 ? gw : 8 * 152),
+                          32 * kWarpSortWarps, 0, s, k_sort_warp, R->count, R->pair_off, nA,
+                          (long long)np, R->b_row, R->sep);
+                const int64_t gs = (nA + 255) / 256;
+                XM_LAUNCH("k_seg_sort", (unsigned)(gs < 2 * 152 ? gs : 2 * 152), 256, 0, s,
+                          k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep);
+                return XM_OK;
+            };
+            auto alloc_pairs = [&](int64_t np) -> bool {
+                R->a_row = (int64_t*)dev_alloc(np * (2 * sizeof(int64_t) + sizeof(double)), s);
+                if (!R->a_row) return false;
+                R->b_row = R->a_row + np;
+                R->sep = (double*)(R->b_row + np);
+                return true;
+            };
+            // the counts go to the host first; the side stream (float64 best
+            // pairs) forks here, before the speculative work below
             int32_t h_small[8];
             int64_t h_total[2] = {0, 0};
             int32_t h_berr = 0;  // a deferred index build's error bits
@@ -315,7 +356,26 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             e = rd.add(h_small, small, sizeof(h_small));
             if (e == cudaSuccess) e = rd.add(h_total, total, sizeof(h_total));
             if (e == cudaSuccess && X->build_err) e = rd.add(&h_berr, X->build_err, sizeof(int32_t));
-            if (e == cudaSuccess) e = rd.sync();
+            if (e == cudaSuccess) e = rd.mark();
+            if (e != cudaSuccess) return cuda_fail(e, "xm_match count reads");
+            Side* side = ((sel & XM_SEL_BEST) && prec == XM_PREC_FP32_RECHECK) ? side_stream() : nullptr;
+            if (side && cudaEventRecord(side->fork, s) != cudaSuccess) {
+                cudaGetLastError();
+                side = nullptr;
+            }
+            // Speculation: without overflowed sources the list holds at most
+            // the arena's records, so it is placed and sorted into a list of
+            // that size before the counts reach the host, and the GPU stays
+            // busy through the synchronisation below. (Large arenas, and
+            // overflow, take the exact size after it.)
+            int64_t np_spec = 0;
+            if (want_all && nA > 0 && arena_cap <= kSpeculateRecords && alloc_pairs(arena_cap)) {
+                np_spec = arena_cap;
+                r = place_and_sort(np_spec, 0);
+                if (r != XM_OK) return r;
+            }
+            // one synchronisation: total pairs, list lengths, error bits
+            e = rd.sync();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match sync");
             if (h_berr) return index_build_status(h_berr);
             if (h_small[0] & kErrCoord) return set_error(XM_EINVAL, "A: NaN/inf or |lat| > 90");
@@ -332,10 +392,8 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 ScanArgs b = a;
                 b.list = lists + nn;
                 b.nlist = n_tie;
-                Side* side = side_stream();
                 cudaStream_t rs = s;
-                if (side && cudaEventRecord(side->fork, s) == cudaSuccess &&
-                    cudaStreamWaitEvent(side->st, side->fork, 0) == cudaSuccess) {
+                if (side && cudaStreamWaitEvent(side->st, side->fork, 0) == cudaSuccess) {
                     joiner.s = s;
                     joiner.side = side;
                     rs = side->st;
@@ -343,38 +401,24 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 r = launch_scan_any(prec, b, kModeResolve, n_tie, rs);
                 if (r != XM_OK) return r;
             }
-            if (want_all) {
+            if (want_all && !(np_spec > 0 && n_ovf == 0 && h_total[0] <= np_spec)) {
+                if (np_spec > 0) {  // the speculation did not hold: the exact size
+                    dev_free(R->a_row, s);
+                    R->a_row = nullptr;
+                }
                 const int64_t np = h_total[0] > 0 ? h_total[0] : 1;
-                R->a_row = (int64_t*)dev_alloc(np * (2 * sizeof(int64_t) + sizeof(double)), s);
-                if (!R->a_row) return set_error(XM_ENOMEM, "xm_match: %lld pairs", (long long)h_total[0]);
-                R->b_row = R->a_row + np;
-                R->sep = (double*)(R->b_row + np);
-                XM_LAUNCH("k_place", 4 * 152, 256, 0, s, k_place, arena, arena_n, arena_cap,
-                          R->pair_off, (const int32_t*)nullptr, (long long)np, R->a_row, R->b_row,
-                          R->sep);
-                if (n_ovf > 0) {
-                    ScanArgs b = a;
-                    b.list = lists;
-                    b.nlist = n_ovf;
-                    b.pair_off = R->pair_off;
-                    b.out_a = R->a_row;
-                    b.out_b = R->b_row;
-                    b.out_sep = R->sep;
-                    b.out_cap = np;
-                    r = launch_scan_any(prec, b, kModeEmit, n_ovf, s);
-                    if (r != XM_OK) return r;
-                }
+                if (!alloc_pairs(np))
+                    return set_error(XM_ENOMEM, "xm_match: %lld pairs", (long long)h_total[0]);
                 if (nA > 0) {
-                    XM_LAUNCH("k_sort_small", grid_for(nA), kBlock, 0, s, k_sort_small, R->count,
-                              R->pair_off, nA, (long long)np, R->b_row, R->sep);
-                    const int64_t gw = (nA + 32 * kWarpSortWarps - 1) / (32 * kWarpSortWarps);
-                    XM_LAUNCH("k_sort_warp", (unsigned)(gw < 8 * 152 ? gw : 8 * 152),
-                              32 * kWarpSortWarps, 0, s, k_sort_warp, R->count, R->pair_off, nA,
-                              (long long)np, R->b_row, R->sep);
-                    const int64_t gs = (nA + 255) / 256;
-                    XM_LAUNCH("k_seg_sort", (unsigned)(gs < 2 * 152 ? gs : 2 * 152), 256, 0, s,
-                              k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep);
+                    r = place_and_sort(np, n_ovf);
+                    if (r != XM_OK) return r;
+                } else {
+                    XM_LAUNCH("k_place", 4 * 152, 256, 0, s, k_place, arena, arena_n, arena_cap,
+                              R->pair_off, (const int32_t*)nullptr, (long long)np, R->a_row,
+                              R->b_row, R->sep);
                 }
+            }
+            if (want_all) {
                 if (n_big > 0) {
                     // rare: regions holding more than kSegMax sources
                     r = sort_long_segments(lists + 2 * nn, n_big, R, err, s);
