@@ -220,7 +220,8 @@ XM_API xm_status xm_index_info(const xm_index* index, int64_t* n, int64_t* zones
  *   ALL:  every member pair, ordered by A row then B row;
  *   BEST: per A row, the member of smallest angular separation, ties to the
  *         lowest B row (-1 / NaN when the A source has no member).
- * Synchronises `stream` once (to size the pair list).
+ * Synchronises `stream` once, for the pair count (the pair list of a result
+ * whose member records fit 2^23 is placed and sorted on the GPU meanwhile).
  * Errors: XM_EINVAL (bad region/opts/coordinates), XM_ENOMEM, XM_ECUDA. */
 XM_API xm_status xm_match(const xm_index* index, const xm_columns* A, const xm_region* region,
                           const xm_match_opts* opts, void* stream, xm_result** out);
