@@ -9,7 +9,11 @@
 //                 NaN -> all ones, above every number, never looked up), row
 //                 payloads, and the AND / OR of all B codes (bits that never
 //                 differ need no sort pass)
-//   radix sort    stable, so equal keys keep ascending B rows (xm_sort.cu)
+//   radix sort    stable, so equal keys keep ascending B rows (xm_sort.cu):
+//                 on the codes themselves when they differ in at most 32
+//                 bits, else on a 32-bit hash of them (half the passes;
+//                 equal keys still form one run, now shared with the few
+//                 keys whose hash collides, told apart by the codes)
 //   k_val_lut     a bucket table over the sorted codes (one bucket per two
 //                 to four keys; long runs of entries by k_val_runs)
 //   k_val_probe   per A: the run of equal B codes, searched inside one
@@ -37,11 +41,24 @@ __device__ __forceinline__ uint64_t key_code(const void* keys, int64_t i, int32_
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// 32-bit hash of a code (the finaliser of the SplitMix64 generator, Steele,
+// Lea & Flood 2014, high half): equal codes hash equally, distinct ones
+// collide with probability about 2^-32.
+__device__ __forceinline__ uint64_t code_hash(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x >> 32;
+}
+
 // Grid-stride over B (a few blocks per SM), so the AND / OR of all codes
-// costs one pair of atomics per block.
+// costs one pair of atomics per block. Writes the codes by row and, for the
+// hashed order, their hashes.
 __global__ void k_val_key(const void* __restrict__ keys, int64_t n, int32_t type,
-                          uint64_t* __restrict__ codes, uint32_t* __restrict__ rows,
-                          unsigned long long* __restrict__ and_or) {
+                          uint64_t* __restrict__ codes, uint64_t* __restrict__ hashes,
+                          uint32_t* __restrict__ rows, unsigned long long* __restrict__ and_or) {
     pdl_wait();
     __shared__ unsigned long long s_and, s_or;
     if (threadIdx.x == 0) {
@@ -54,6 +71,7 @@ __global__ void k_val_key(const void* __restrict__ keys, int64_t n, int32_t type
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t c = key_code(keys, i, type);
         codes[i] = c;
+        hashes[i] = code_hash(c);
         rows[i] = (uint32_t)i;
         c_and &= c;
         c_or |= c;
@@ -164,6 +182,65 @@ __global__ void k_val_probe(const void* __restrict__ a_keys, int64_t n_a, int32_
     }
 }
 
+// Hashed order: the run of A's hash, then the B rows whose code is A's.
+__global__ void k_val_probe_hashed(const void* __restrict__ a_keys, int64_t n_a, int32_t type,
+                                   const uint64_t* __restrict__ sorted,
+                                   const uint32_t* __restrict__ rows,
+                                   const uint64_t* __restrict__ codes, int64_t n_b, ValLut V,
+                                   int32_t* __restrict__ count, int64_t* __restrict__ first,
+                                   int64_t* __restrict__ best_b, double* __restrict__ best_sep) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_a) return;
+    const uint64_t c = key_code(a_keys, i, type);
+    int64_t lo = 0, m = 0, best = -1;
+    if (n_b > 0 && !(type == XM_KEY_FLOAT64 && c == kNaNCode)) {
+        const uint64_t h = code_hash(c);
+        const uint32_t b = val_bucket(V, h);
+        const int64_t b0 = __ldg(&V.lut[b]), b1 = __ldg(&V.lut[b + 1]);
+        lo = bound(sorted, b0, b1, h, false);
+        for (int64_t p = lo; p < b1 && __ldg(&sorted[p]) == h; p++) {
+            const uint32_t r = __ldg(&rows[p]);
+            if (__ldg(&codes[r]) == c) {
+                if (m == 0) best = r;
+                m++;
+            }
+        }
+    }
+    count[i] = (int32_t)(m < 2147483647 ? m : 2147483647);
+    first[i] = lo;
+    if (best_b) {
+        best_b[i] = best;
+        best_sep[i] = m > 0 ? 0.0 : NAN;
+    }
+}
+
+__global__ void k_val_emit_hashed(const void* __restrict__ a_keys, int32_t type,
+                                  const int32_t* __restrict__ count,
+                                  const int64_t* __restrict__ first,
+                                  const int64_t* __restrict__ pair_off,
+                                  const uint32_t* __restrict__ rows,
+                                  const uint64_t* __restrict__ codes, int64_t n_a,
+                                  int64_t* __restrict__ pa, int64_t* __restrict__ pb,
+                                  double* __restrict__ ps) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_a) return;
+    const int32_t c = count[i];
+    if (c == 0) return;
+    const uint64_t code = key_code(a_keys, i, type);
+    const int64_t o = pair_off[i];
+    int32_t k = 0;
+    for (int64_t p = first[i]; k < c; p++) {  // (the run holds all c matches)
+        const uint32_t r = rows[p];
+        if (codes[r] != code) continue;
+        pa[o + k] = i;
+        pb[o + k] = r;
+        ps[o + k] = 0.0;
+        k++;
+    }
+}
+
 __global__ void k_val_emit(const int32_t* __restrict__ count, const int64_t* __restrict__ first,
                            const int64_t* __restrict__ pair_off, const uint32_t* __restrict__ rows,
                            int64_t n_a, int64_t* __restrict__ pa, int64_t* __restrict__ pb,
@@ -227,14 +304,15 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
     void* d_a = nullptr;
     void* d_b = nullptr;
     uint64_t* codes = (uint64_t*)dev_alloc(2 * nb1 * sizeof(uint64_t), s);
+    uint64_t* hashes = (uint64_t*)dev_alloc(2 * nb1 * sizeof(uint64_t), s);
     uint32_t* rows = (uint32_t*)dev_alloc(2 * nb1 * sizeof(uint32_t), s);
     int64_t* first = (int64_t*)dev_alloc(na1 * sizeof(int64_t), s);
     unsigned long long* small = (unsigned long long*)dev_alloc(4 * sizeof(unsigned long long), s);
     uint32_t* lut = nullptr;
     ValRun* runs = nullptr;
     auto body = [&]() -> xm_status {
-        if (!R->count || !R->pair_off || (want_best && !R->best_b) || !codes || !rows || !first ||
-            !small)
+        if (!R->count || !R->pair_off || (want_best && !R->best_b) || !codes || !hashes || !rows ||
+            !first || !small)
             return set_error(XM_ENOMEM, "xm_match_values: work buffers");
         cudaError_t e;
         const void* ak = a_keys;
@@ -257,23 +335,27 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
         int32_t* err = (int32_t*)(small + 3);
         if (n_b > 0) {
             const unsigned gk = grid_of(n_b) < 8 * 152 ? grid_of(n_b) : 8 * 152;
-            XM_LAUNCH("k_val_key", gk, kBlock, 0, s, k_val_key, bk, n_b, key_type, codes, rows,
-                      small);
+            XM_LAUNCH("k_val_key", gk, kBlock, 0, s, k_val_key, bk, n_b, key_type, codes, hashes,
+                      rows, small);
         }
         unsigned long long h_ao[2] = {~0ull, 0ull};
         e = cudaMemcpyAsync(h_ao, small, sizeof(h_ao), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "xm_match_values sync");
-        // bits where the codes differ: the sort covers only those
-        const int end_bit = top_bit(h_ao[0] ^ h_ao[1]);
+        // bits where the codes differ: the sort covers only those, or the
+        // 32 bits of the hash when there are more
+        const int code_bits = top_bit(h_ao[0] ^ h_ao[1]);
+        const bool hashed = code_bits > 32;
+        const int end_bit = hashed ? 32 : code_bits;
+        uint64_t* sorted = hashed ? hashes : codes;
         if (n_b > 1 && end_bit > 0) {
-            xm_status r = radix_sort_u64(codes, rows, codes + nb1, rows + nb1, n_b, 0, end_bit, err, s);
+            xm_status r = radix_sort_u64(sorted, rows, sorted + nb1, rows + nb1, n_b, 0, end_bit, err, s);
             if (r != XM_OK) return r;
         }
         // bucket table: about one bucket per 2-4 keys over the differing bits
         ValLut V{};
         V.mask = end_bit >= 64 ? ~0ull : ((1ull << end_bit) - 1);
-        V.prefix = h_ao[0] & ~V.mask;
+        V.prefix = hashed ? 0ull : (h_ao[0] & ~V.mask);
         int lg = top_bit((uint64_t)nb1) - 2;
         lg = lg < 1 ? 1 : (lg > 28 ? 28 : lg);
         if (lg > end_bit) lg = end_bit > 0 ? end_bit : 0;
@@ -288,11 +370,15 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
         e = cudaMemsetAsync(n_runs, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(e, "xm_match_values: memset");
         if (n_b > 0) {
-            XM_LAUNCH("k_val_lut", grid_of(n_b), kBlock, 0, s, k_val_lut, codes, n_b, V, runs,
+            XM_LAUNCH("k_val_lut", grid_of(n_b), kBlock, 0, s, k_val_lut, sorted, n_b, V, runs,
                       n_runs, run_cap, err);
             XM_LAUNCH("k_val_runs", 4 * 152, kBlock, 0, s, k_val_runs, runs, n_runs, run_cap, lut);
         }
-        if (n_a > 0)
+        if (n_a > 0 && hashed)
+            XM_LAUNCH("k_val_probe", grid_of(n_a), kBlock, 0, s, k_val_probe_hashed, ak, n_a,
+                      key_type, sorted, rows, codes, n_b, V, R->count, first, R->best_b,
+                      R->best_sep);
+        else if (n_a > 0)
             XM_LAUNCH("k_val_probe", grid_of(n_a), kBlock, 0, s, k_val_probe, ak, n_a, key_type,
                       codes, rows, n_b, V, R->count, first, R->best_b, R->best_sep);
         xm_status r = exclusive_scan_i32(R->count, R->pair_off, n_a, (int64_t*)(small + 2), err, s);
@@ -310,7 +396,11 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
             if (!R->a_row) return set_error(XM_ENOMEM, "xm_match_values: %lld pairs", (long long)R->n_pairs);
             R->b_row = R->a_row + np;
             R->sep = (double*)(R->b_row + np);
-            if (n_a > 0)
+            if (n_a > 0 && hashed)
+                XM_LAUNCH("k_val_emit", grid_of(n_a), kBlock, 0, s, k_val_emit_hashed, ak, key_type,
+                          R->count, first, R->pair_off, rows, codes, n_a, R->a_row, R->b_row,
+                          R->sep);
+            else if (n_a > 0)
                 XM_LAUNCH("k_val_emit", grid_of(n_a), kBlock, 0, s, k_val_emit, R->count, first,
                           R->pair_off, rows, n_a, R->a_row, R->b_row, R->sep);
         }
@@ -320,6 +410,7 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
     dev_free(d_a, s);
     dev_free(d_b, s);
     dev_free(codes, s);
+    dev_free(hashes, s);
     dev_free(rows, s);
     dev_free(first, s);
     dev_free(small, s);

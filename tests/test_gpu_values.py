@@ -100,3 +100,56 @@ def test_value_results_have_no_positions(xm):
     h = ctypes.c_void_p()
     st = xm.xm_pick_pairs(idx.handle, res.handle, 1, None, ctypes.byref(h))
     assert xm.STATUS[st] in ("XM_EUNSUPPORTED", "XM_EINVAL")
+
+
+def test_narrow_int64_keys_sort_directly(xm):
+    """Keys that differ in at most 32 bits are sorted on their codes (no
+    hash): non-negative ids in a 2^20 range, with repeats."""
+    g = synth.rng(8)
+    b = 1000 + g.integers(0, 1 << 20, 300_000)
+    a = np.concatenate([b[::7], 1000 + g.integers(0, 1 << 20, 50_000)])
+    _check(xm, xm.ValueResult(_cuda(a), _cuda(b)), a, b)
+
+
+def _colliding_keys(n_groups, per_group, seed):
+    """int64 keys whose 32-bit hash in the library's hashed order collides in
+    groups: codes are the inverse of the hash's 64-bit mixer at values that
+    share their high 32 bits (the mixer is a bijection)."""
+    m64 = (1 << 64) - 1
+    c1, c2 = 0xbf58476d1ce4e5b9, 0x94d049bb133111eb
+    i1, i2 = pow(c1, -1, 1 << 64), pow(c2, -1, 1 << 64)
+
+    def unxorshift(y, k):
+        x = y
+        for _ in range(64 // k + 1):
+            x = y ^ (x >> k)
+        return x & m64
+
+    def unmix(z):
+        x = unxorshift(z, 31)
+        x = (x * i2) & m64
+        x = unxorshift(x, 27)
+        x = (x * i1) & m64
+        return unxorshift(x, 30)
+
+    g = synth.rng(seed)
+    keys = []
+    for hi in g.integers(0, 1 << 32, n_groups).tolist():
+        for lo in g.integers(0, 1 << 32, per_group).tolist():
+            code = unmix((hi << 32) | lo)
+            key = code ^ (1 << 63)
+            keys.append(key - (1 << 64) if key >= 1 << 63 else key)
+    return np.array(keys, np.int64)
+
+
+def test_hash_collisions_are_told_apart(xm):
+    """Groups of distinct keys with one 32-bit hash: each A key matches only
+    the B rows of its own value, in ascending B row."""
+    col = _colliding_keys(200, 4, 9)
+    g = synth.rng(10)
+    b = np.concatenate([col, col[::3], g.integers(-(2**62), 2**62, 20_000)])
+    b = b[g.permutation(b.size)]
+    a = np.concatenate([col[::2], col[1::4], g.integers(-(2**62), 2**62, 5_000)])
+    res = xm.ValueResult(_cuda(a), _cuda(b))
+    ref = _check(xm, res, a, b)
+    assert ref["a_row"].size > 400
