@@ -203,21 +203,31 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             return set_error(XM_ENOMEM, "xm_match: result arrays");
         }
 
+        // host A in input order is copied and prepared on the side stream,
+        // alongside what the caller's stream is still running (an index build
+        // launched just before, say); its buffers are freed on `s` after it
+        const bool sorted_a = opts->a_order == XM_A_ORDER_SORTED ||
+                              (opts->a_order == XM_A_ORDER_DEFAULT && kDefaultSortedA);
+        Side* pre = (!Acols->on_device && nA > 0 && !sorted_a) ? side_stream() : nullptr;
+        const cudaStream_t ps = pre ? pre->st : s;
+        double* a_buf = nullptr;   // A columns on the device (host input)
+        APrep* a_prep = nullptr;   // (side stream only)
+        int32_t* a_err = nullptr;  // (side stream only) preparation's error bits
         auto body = [&]() -> xm_status {
             // A columns on the device
             const double *lon = Acols->lon_deg, *lat = Acols->lat_deg;
             const double *ac = region->a_col, *bc = region->b_col, *pc = region->pa_col;
             if (!Acols->on_device && nA > 0) {
-                double* buf = T.get<double>(5 * nA);
-                if (!buf) return set_error(XM_ENOMEM, "A input copy");
+                a_buf = (double*)dev_alloc(5 * nA * sizeof(double), ps);
+                if (!a_buf) return set_error(XM_ENOMEM, "A input copy");
                 const double* src[5] = {lon, lat, ac, bc, pc};
                 const double** dst[5] = {&lon, &lat, &ac, &bc, &pc};
                 for (int k = 0; k < 5; k++) {
                     if (!src[k]) continue;
-                    e = cudaMemcpyAsync(buf + k * nA, src[k], nA * sizeof(double),
-                                        cudaMemcpyHostToDevice, s);
+                    e = cudaMemcpyAsync(a_buf + k * nA, src[k], nA * sizeof(double),
+                                        cudaMemcpyHostToDevice, ps);
                     if (e != cudaSuccess) return cuda_fail(e, "A input copy");
-                    *dst[k] = buf + k * nA;
+                    *dst[k] = a_buf + k * nA;
                 }
             }
             AIn I;
@@ -247,14 +257,20 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             // member records: room for 12 per A source on average; sources
             // that overflow it are scanned again in emit mode
             const long long arena_cap = want_all ? 12LL * nA + 65536 : 0;
-            const bool sorted_a = opts->a_order == XM_A_ORDER_SORTED ||
-                                  (opts->a_order == XM_A_ORDER_DEFAULT && kDefaultSortedA);
             uint64_t* keys = sorted_a ? T.get<uint64_t>(2 * nn) : nullptr;
             uint32_t* vals = sorted_a ? T.get<uint32_t>(2 * nn) : nullptr;
-            APrep* prep = T.get<APrep>(nn);
+            APrep* prep = nullptr;
+            if (pre) {
+                prep = a_prep = (APrep*)dev_alloc(nn * sizeof(APrep), ps);
+                a_err = (int32_t*)dev_alloc(sizeof(int32_t), ps);
+                if (!a_err || cudaMemsetAsync(a_err, 0, sizeof(int32_t), ps) != cudaSuccess)
+                    return set_error(XM_ENOMEM, "xm_match: preparation buffers");
+            } else {
+                prep = T.get<APrep>(nn);
+            }
             // the float64 part stays with the result (float64 decisions after
             // the match); in sorted order with the row -> slot map
-            R->acold = (ACold*)dev_alloc(nn * sizeof(ACold), s);
+            R->acold = (ACold*)dev_alloc(nn * sizeof(ACold), ps);
             ACold* cold = R->acold;
             int32_t* lists = T.get<int32_t>(3 * nn);
             int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts, [4] chunk queue
@@ -280,8 +296,13 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 XM_LAUNCH("k_slot_of_row", grid_for(nA), kBlock, 0, s, k_slot_of_row, vals, nA,
                           R->a_slot);
             } else if (nA > 0) {
-                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, s, k_prep_a, I,
-                          (const uint32_t*)nullptr, prep, cold, err);
+                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, ps, k_prep_a, I,
+                          (const uint32_t*)nullptr, prep, cold, pre ? a_err : err);
+                if (pre) {  // the scan waits for the preparation
+                    e = cudaEventRecord(pre->join, ps);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pre->join, 0);
+                    if (e != cudaSuccess) return cuda_fail(e, "xm_match: preparation join");
+                }
             }
             ScanArgs a{};
             a.G = X->geom();
@@ -356,6 +377,8 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             e = rd.add(h_small, small, sizeof(h_small));
             if (e == cudaSuccess) e = rd.add(h_total, total, sizeof(h_total));
             if (e == cudaSuccess && X->build_err) e = rd.add(&h_berr, X->build_err, sizeof(int32_t));
+            int32_t h_aerr = 0;
+            if (e == cudaSuccess && a_err) e = rd.add(&h_aerr, a_err, sizeof(int32_t));
             if (e == cudaSuccess) e = rd.mark();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match count reads");
             Side* side = ((sel & XM_SEL_BEST) && prec == XM_PREC_FP32_RECHECK) ? side_stream() : nullptr;
@@ -378,6 +401,7 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             e = rd.sync();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match sync");
             if (h_berr) return index_build_status(h_berr);
+            h_small[0] |= h_aerr;
             if (h_small[0] & kErrCoord) return set_error(XM_EINVAL, "A: NaN/inf or |lat| > 90");
             if (h_small[0] & kErrSize)
                 return set_error(XM_EINVAL, "A: negative or non-finite region size or angle");
@@ -439,6 +463,14 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             return XM_OK;
         };
         st = body();
+        if (pre) {  // (also when the body stopped early: nothing of it is left on ps)
+            if (cudaEventRecord(pre->join, ps) == cudaSuccess) cudaStreamWaitEvent(s, pre->join, 0);
+            else cudaGetLastError();
+        }
+        dev_free(a_buf, s);
+        dev_free(a_prep, s);
+        dev_free(a_err, s);
+        if (st != XM_OK && pre) cudaStreamSynchronize(ps);  // (before the result is freed)
     }
     if (st != XM_OK) {
         free_result(R);
