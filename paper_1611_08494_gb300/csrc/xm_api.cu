@@ -155,6 +155,24 @@ cudaError_t HostReads::sync() {
     return cudaSuccess;
 }
 
+Side* side_stream() {
+    static thread_local Side sd[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    Side& d = sd[dev];
+    if (!d.st) {
+        const bool ok = cudaStreamCreateWithFlags(&d.st, cudaStreamNonBlocking) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            d = Side();
+            return nullptr;
+        }
+    }
+    return &d;
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 1;
     AllocHook h;

@@ -378,6 +378,16 @@ __device__ __forceinline__ void unit64_deg(double lon, double lat, double* px, d
 
 void* dev_alloc(size_t bytes, cudaStream_t s);
 
+// A second stream per host thread and device, with a fork and a join event,
+// for work of a call that can overlap the rest of it (the near-tie resolve
+// beside the pair placement; host A copied and prepared beside an index
+// build). Null when it cannot be created.
+struct Side {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+Side* side_stream();
+
 // Small device -> host reads gathered behind one synchronisation: add()
 // queues an asynchronous copy into this host thread's pinned staging area
 // (a copy into pageable memory would block the host once per copy), sync()

@@ -88,31 +88,6 @@ __global__ void k_slot_of_row(const uint32_t* __restrict__ vals, int64_t n,
     if (s < n) a_slot[vals[s]] = (int32_t)s;
 }
 
-// A second stream per host thread and device, with a fork and a join event,
-// for work of a call that can overlap the rest of it (the near-tie resolve
-// runs beside the pair placement and sorts).
-struct Side {
-    cudaStream_t st = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-};
-
-Side* side_stream() {
-    static thread_local Side sd[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    Side& d = sd[dev];
-    if (!d.st) {
-        if (cudaStreamCreateWithFlags(&d.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            d = Side();
-            return nullptr;
-        }
-    }
-    return &d;
-}
-
 // Makes `s` wait for the side stream's work when it goes out of scope (so
 // temporaries freed on `s` afterwards are no longer read there).
 struct Joiner {

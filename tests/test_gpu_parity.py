@@ -487,3 +487,22 @@ def test_index_sort_plan(xm, case):
             assert list(_host(res.best_b)) == [0, 0, -1]
         else:
             check_best(res, ref, a_lon.size)
+
+
+def test_large_host_input_equals_device_input(xm):
+    """B of 5e6 and A from host memory (A copied and prepared on a side
+    stream beside the build): the results equal those from device columns."""
+    import torch
+
+    d = synth.c2(scale=1.0)
+    out = {}
+    for dev in (True, False):
+        conv = _cuda if dev else (lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory())
+        idx = xm.Index(conv(d["b_lon"]), conv(d["b_lat"]), frame=d["b_frame"], zone_height_arcsec=12.0,
+                       deferred_check=True)
+        reg = {k: (conv(v) if isinstance(v, np.ndarray) else v) for k, v in d["region"].items()}
+        res = xm.Result(idx, conv(d["a_lon"]), conv(d["a_lat"]), frame=d["a_frame"], **reg)
+        out[dev] = [_host(t) for t in (res.a_row, res.b_row, res.sep, res.best_b)]
+    for x, y in zip(out[True], out[False]):
+        np.testing.assert_array_equal(x, y)
+    assert out[True][0].size > 1_000_000
