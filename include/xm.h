@@ -225,6 +225,9 @@ XM_API xm_status xm_index_info(const xm_index* index, int64_t* n, int64_t* zones
  * Errors: XM_EINVAL (bad region/opts/coordinates), XM_ENOMEM, XM_ECUDA. */
 XM_API xm_status xm_match(const xm_index* index, const xm_columns* A, const xm_region* region,
                           const xm_match_opts* opts, void* stream, xm_result** out);
+/* Frees the result's device arrays in the order of the stream it was computed
+ * on (work queued there that reads them runs first); that stream must still
+ * exist. */
 XM_API xm_status xm_result_free(xm_result* result);
 
 /* Device arrays of a result (valid until xm_result_free):

@@ -564,6 +564,9 @@ struct xm_result {
     // (or a itself when a_slot is NULL)
     xm::ACold* acold;
     int32_t* a_slot;
+    // the stream the result was computed on: its arrays are freed in that
+    // stream's order, after the work the caller queued there to read them
+    cudaStream_t stream;
 };
 
 struct xm_rows {

@@ -108,7 +108,7 @@ using namespace xm;
 
 static void free_result(xm_result* R) {
     if (!R) return;
-    cudaStream_t s = nullptr;
+    cudaStream_t s = R->stream;
     dev_free(R->count, s);
     dev_free(R->pair_off, s);
     dev_free(R->a_row, s);
@@ -156,6 +156,7 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
     cudaError_t e;
     xm_result* R = new (std::nothrow) xm_result();
     if (!R) return set_error(XM_ENOMEM, "xm_match: host allocation");
+    R->stream = (cudaStream_t)stream;
     cudaGetDevice(&R->device);
     R->selection = sel;
     R->precision = prec;

@@ -285,6 +285,7 @@ extern "C" xm_status xm_match_values(const void* a_keys, int64_t n_a, const void
     cudaStream_t s = (cudaStream_t)stream;
     xm_result* R = new (std::nothrow) xm_result();
     if (!R) return set_error(XM_ENOMEM, "xm_match_values: host allocation");
+    R->stream = (cudaStream_t)stream;
     cudaGetDevice(&R->device);
     R->selection = selection;
     R->precision = XM_PREC_FP64;
