@@ -133,6 +133,7 @@ struct OnesweepSmem {
     uint32_t vals[kSortTile];
     uint8_t dig[kSortTile];          // digit of each placed key
     int32_t wcount[kWarps][kRadix];  // per-warp digit counts, then warp offsets
+    int32_t hist[kRadix];            // the tile's digit counts (published early)
     int32_t dstart[kRadix];          // tile-local start of each digit
     int64_t gstart[kRadix];          // global start of each digit for this tile, less its
                                      // tile-local start (output slot = gstart[d] + p)
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
         if (S.tile == 0 && stats) atomicAdd(&stats[5], (unsigned long long)n);  // keys this pass
     }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
+    if (threadIdx.x < kRadix) S.hist[threadIdx.x] = 0;
     __syncthreads();
     const int tile = S.tile;
     const int64_t tile_base = (int64_t)tile * kSortTile;
@@ -185,10 +187,26 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
         const int64_t i = warp_base + 32 * k + lane;
         key[k] = i < n ? keys_in[i] : 0;
     }
+    // The tile's digit counts first (shared-memory atomics), published at
+    // once: the tiles after this one find them while this one still ranks,
+    // so their look-backs rarely wait.
+    uint32_t dpack[kSortItems / 4] = {};
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
+        dpack[k >> 2] |= d << (8 * (k & 3));
+        if (warp_base + 32 * k + lane < n) atomicAdd(&S.hist[d], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRadix) {
+        const int d = threadIdx.x;
+        st_relaxed(status + (int64_t)tile * kRadix + d,
+                   (tile == 0 ? kStInc : kStAgg) | (uint64_t)S.hist[d]);
+    }
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         const bool valid = warp_base + 32 * k + lane < n;
-        const uint32_t d = (uint32_t)((planned ? plan_key(P, key[k]) : key[k]) >> shift) & 0xFF;
+        const uint32_t d = (dpack[k >> 2] >> (8 * (k & 3))) & 0xFF;
         // lanes holding the same digit: one vote per digit bit (the
         // multisplit form), cheaper than a match instruction
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -219,13 +237,10 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
             S.wcount[w][d] = run;
             run += c;
         }
-        S.dstart[d] = run;  // tile count, scanned below
+        S.dstart[d] = run;  // tile count (= hist[d]), scanned below
         uint64_t* my = status + (int64_t)tile * kRadix + d;
         int64_t prefix = 0;
-        if (tile == 0) {
-            st_relaxed(my, kStInc | (uint64_t)run);
-        } else {
-            st_relaxed(my, kStAgg | (uint64_t)run);
+        if (tile != 0) {  // (tile 0 published its inclusive counts already)
             // walk back kLookWindow tiles per step: their words are loaded
             // together, then taken in order until an inclusive prefix (done)
             // or a tile that has not published yet (wait there)
