@@ -147,8 +147,7 @@ struct OnesweepSmem {
 // an inclusive prefix, then scatter through shared memory. A walk that finds
 // no progress for kSpinLimit polls flags a timeout and carries on, so no
 // block can wait forever; the caller turns the flag into XM_ETIMEOUT.
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kSortThreads, kMinBlocks) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
     int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -558,28 +557,19 @@ void radix_sort_prepare() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> g(mu);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_onesweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(OnesweepSmem));
-    cudaFuncSetAttribute(k_onesweep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(OnesweepSmem));
     done[dev] = true;
 }
 
-// One pass. Large sorts run three tiles per SM (registers capped at 40, a
-// few spilled): more tiles in flight hide more of each tile's latency
-// chain. Sorts of a few waves keep two (no spills, shorter tiles).
-constexpr int64_t kThreeBlockTiles = 2048;
-
+// One pass (two tiles per SM: 64 registers, no spills; three, with spills,
+// measured slower once tiles publish their counts early).
 void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* ki,
                    const uint32_t* vi, int64_t n, int shift, const unsigned long long* offs,
                    uint64_t* status, unsigned int* counter, uint64_t* ko, uint32_t* vo,
                    int32_t* err, const SortPlan* plan, int pass) {
-    if (ntiles >= kThreeBlockTiles)
-        launch_pdl(k_onesweep<3>, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n,
-                   shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
-    else
-        launch_pdl(k_onesweep<2>, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n,
-                   shift, offs, status, counter, ko, vo, err, plan, pass, device_stats());
+    launch_pdl(k_onesweep, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n, shift,
+               offs, status, counter, ko, vo, err, plan, pass, device_stats());
 }
 
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
