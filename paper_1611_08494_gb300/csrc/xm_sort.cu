@@ -52,10 +52,12 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t* __r
     __syncthreads();
     SortPlan P{};
     if (plan) P = *plan;
+    // (passes a plan leaves out are not counted: all their digits are 0)
+    const int counted = plan ? min(passes, (int)P.active) : passes;
     for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * kSortThreads) {
         const uint64_t k = plan ? plan_key(P, keys[i]) : keys[i] >> begin_bit;
-        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+        for (int p = 0; p < counted; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
