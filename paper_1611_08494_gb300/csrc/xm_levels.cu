@@ -2,11 +2,14 @@
 // the best pair of each A source by it (a reading of the "best pairs" of
 // §2.2) and the levels of concentric scaled regions (§3, ClumpPopulator).
 //
-//   k_lvl_a64     per A source: float64 sines and cosines of its position and
-//                 orientation, once (the pairs of a source share them)
+//   k_lvl_a64     per A source: float64 sines and cosines of its latitude
+//                 and orientation, reciprocals of its semi-axes, once (the
+//                 pairs of a source share them)
 //   k_lvl_pair    per pair: float64 normalised distance from the exact
-//                 positions, its level among the scales, the count of its
-//                 copy, the smallest distance of its A source
+//                 positions (from their differences by short series when B
+//                 is within half a degree of A, else from unit vectors), its
+//                 level among the scales, the count of its copy, the smallest
+//                 distance of its A source
 //   k_lvl_best    per pair at that smallest distance: the lowest B row
 //   k_lvl_finish  per A source: counts made cumulative over the copies, the
 //                 best pair written out
@@ -48,14 +51,60 @@ constexpr int kBlock = 256;
 
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
 
-__global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, A64* __restrict__ out) {
+// What the pairs of an A source share: its position (degrees), the sine and
+// cosine of its latitude and orientation, its semi-axes and their
+// reciprocals. The longitude's sine and cosine are left to the pairs that
+// need them (the ones farther than the series' reach).
+struct LvA {
+    double lon, lat;
+    double sd, cd, st, ct;
+    double a, b, inv_a, inv_b;
+};
+
+__global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, LvA* __restrict__ out) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = make_a64(acold[i]);
+    const ACold C = acold[i];
+    LvA L;
+    L.lon = C.lon;
+    L.lat = C.lat;
+    sincospi(C.lat * (1.0 / 180.0), &L.sd, &L.cd);  // degrees reduced exactly
+    sincos(C.theta, &L.st, &L.ct);
+    L.a = C.a;
+    L.b = C.b;
+    L.inv_a = 1.0 / C.a;
+    L.inv_b = 1.0 / C.b;
+    out[i] = L;
 }
 
-__global__ void k_lvl_pair(IndexGeom G, const A64* __restrict__ a64,
+// sin x and 1 - cos x for |x| <= 0.01 rad by their Taylor series (the first
+// omitted terms are below 1e-21 of the result).
+__device__ __forceinline__ void sin_vers_small(double x, double* s, double* v) {
+    const double x2 = x * x;
+    *s = x * (1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0))));
+    *v = x2 * 0.5 * (1.0 - x2 * (1.0 / 12.0) * (1.0 - x2 * (1.0 / 30.0) * (1.0 - x2 * (1.0 / 56.0))));
+}
+
+// The normalised distance of B from its east/north components (x, y) in A's
+// frame, B in A's hemisphere and s2 = x^2 + y^2 < 1e-4 (separation below
+// ~0.57 deg): the quantity norm64 computes, with rho / sin(rho) from its
+// series, one square root and the semi-axes' reciprocals.
+__device__ __forceinline__ double norm_small(const LvA& L, int shape, double x, double y,
+                                             double s2) {
+    if (L.a == 0.0 || L.b == 0.0) return INFINITY;
+    const double k = rho_over_s(s2);
+    if (shape == XM_CIRCLE) return k * sqrt(s2) * L.inv_a;
+    const double X = x * L.st + y * L.ct;
+    const double Y = x * L.ct - y * L.st;
+    if (shape == XM_ELLIPSE) {
+        const double u = X * L.inv_a, v = Y * L.inv_b;
+        return k * sqrt(u * u + v * v);
+    }
+    return k * fmax(fabs(X) * L.inv_a, fabs(Y) * L.inv_b);
+}
+
+__global__ void k_lvl_pair(IndexGeom G, const LvA* __restrict__ a64,
                            const int32_t* __restrict__ a_slot, int shape,
                            const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
                            int64_t n, Scales S, double* __restrict__ dist,
@@ -65,18 +114,56 @@ __global__ void k_lvl_pair(IndexGeom G, const A64* __restrict__ a64,
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t a = pa[p];
-    const A64& A = a64[a_slot ? a_slot[a] : a];
+    const LvA& L = a64[a_slot ? a_slot[a] : a];
     const int32_t row = (int32_t)pb[p];
-    double px, py, pz;
-    if (G.px) {
-        px = G.px[row];
-        py = G.py[row];
-        pz = G.pz[row];
-    } else {
-        const double2 q = G.pos[row];
-        unit64_deg(q.x, q.y, &px, &py, &pz);
+    double d = 0.0;
+    bool near = false;
+    // B within half a degree of A in both coordinates: its east and north
+    // components in A's frame follow exactly from the differences of the
+    // positions (rotation by the latitude difference, then by the longitude
+    // difference), whose sines the series give without a trigonometric call
+    const double2 q = G.pos[row];
+    double dlon = q.x - L.lon;
+    if (dlon > 180.0) dlon -= 360.0;
+    else if (dlon < -180.0) dlon += 360.0;
+    const double dlat = q.y - L.lat;
+    if (fabs(dlon) <= 0.5 && fabs(dlat) <= 0.5) {  // separation below 0.71 deg: z > 0
+        double sa, va, sd, vd;
+        sin_vers_small(dlon * kDeg, &sa, &va);
+        sin_vers_small(dlat * kDeg, &sd, &vd);
+        const double cb = L.cd * (1.0 - vd) - L.sd * sd;  // cos(lat_B)
+        const double x = cb * sa;
+        const double y = sd + cb * L.sd * va;  // sin(dlat) + cos(lat_B) sin(lat_A) (1 - cos dlon)
+        const double s2 = x * x + y * y;
+        if (s2 < 1e-4) {
+            d = norm_small(L, shape, x, y, s2);
+            near = true;
+        }
     }
-    const double d = norm64(A, shape, px, py, pz);
+    if (!near) {  // from B's unit vector and A's full basis
+        A64 A;
+        sincospi(L.lon * (1.0 / 180.0), &A.sa, &A.ca);
+        A.sd = L.sd;
+        A.cd = L.cd;
+        A.st = L.st;
+        A.ct = L.ct;
+        A.a = L.a;
+        A.b = L.b;
+        double px, py, pz;
+        if (G.px) {
+            px = G.px[row];
+            py = G.py[row];
+            pz = G.pz[row];
+        } else {
+            double sl, cl, sb, cb;
+            sincospi(q.x * (1.0 / 180.0), &sl, &cl);
+            sincospi(q.y * (1.0 / 180.0), &sb, &cb);
+            px = cb * cl;
+            py = cb * sl;
+            pz = sb;
+        }
+        d = norm64(A, shape, px, py, pz);
+    }
     dist[p] = d;
     atomicMin(&mind[a], (unsigned long long)dbits(d));  // d >= 0: bit order is value order
     if (S.k > 0) {
@@ -159,7 +246,7 @@ extern "C" xm_status xm_levels_compute(const xm_index* X, const xm_result* R, co
     const size_t bytes = (size_t)n1 * sizeof(double) + (size_t)a1 * (sizeof(double) + sizeof(int64_t)) +
                          lvl_bytes + (size_t)(nw > 0 ? nw : 0) * sizeof(int32_t);
     unsigned char* base = (unsigned char*)dev_alloc(bytes, s);
-    A64* a64 = (A64*)dev_alloc((size_t)a1 * sizeof(A64), s);
+    LvA* a64 = (LvA*)dev_alloc((size_t)a1 * sizeof(LvA), s);
     unsigned long long* w = (unsigned long long*)dev_alloc(2 * (size_t)a1 * sizeof(unsigned long long), s);
     auto body = [&]() -> xm_status {
         if (!base || !a64 || !w) return set_error(XM_ENOMEM, "xm_levels_compute: %lld pairs", (long long)n);

@@ -195,3 +195,28 @@ def test_needs_all_selection_and_positions(xm):
     h = ctypes.c_void_p()
     st = xm.xm_levels_compute(idx.handle, vals.handle, None, 0, None, ctypes.byref(h))
     assert xm.STATUS[st] in ("XM_EUNSUPPORTED", "XM_EINVAL")
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_wide_regions(xm, shape):
+    """Regions of a degree and more, around the equator and near a pole:
+    pairs beyond the short-series reach (separation or coordinate
+    differences above half a degree) take the unit-vector form."""
+    g = synth.rng(90 + shape)
+    pa_, pb_ = [], []
+    for lon0, lat0 in ((30.0, 5.0), (250.0, 87.5)):
+        pa_.append(synth.cap(g, 60, lon0, lat0, 2.0))
+        pb_.append(synth.cap(g, 1500, lon0, lat0, 3.0))
+    n = 120
+    a_col = g.uniform(1800.0, 7200.0, n)  # 0.5 to 2 deg
+    d = dict(a_lon=np.concatenate([p[0] for p in pa_]), a_lat=np.concatenate([p[1] for p in pa_]),
+             b_lon=np.concatenate([p[0] for p in pb_]), b_lat=np.concatenate([p[1] for p in pb_]),
+             a_frame=0, b_frame=0,
+             region=dict(shape=shape, a_col=a_col, b_col=a_col * g.uniform(0.3, 1.0, n),
+                         pa_col=g.uniform(0.0, 180.0, n)))
+    ref = _oracle(d)
+    assert ref["a_row"].size > 10000
+    sep_deg = ref["sep"] / 3600.0
+    assert np.sum(sep_deg > 0.6) > 1000 and np.sum(sep_deg < 0.4) > 1000
+    for build_fp64 in (True, False):
+        _check(xm, _gpu(xm, d, "fp64", build_fp64=build_fp64), ref, n)
