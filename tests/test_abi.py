@@ -70,6 +70,76 @@ def test_validation_before_device_work(xm):
     assert xm.xm_set_allocator(None, None, None) == 0
 
 
+def test_every_entry_point_rejects_null_arguments(xm):
+    """Each call checks its handles and output pointers before any device
+    work: EINVAL with a message, the output handle cleared; the free
+    functions accept NULL."""
+    EINVAL = 1
+    bad = ctypes.c_void_p(0)
+
+    def rejects(status, word):
+        assert status == EINVAL
+        assert word.encode() in xm.xm_last_error()
+
+    def cleared():
+        h = ctypes.c_void_p(12345)  # overwritten with NULL by the call
+        return h
+
+    h = cleared()
+    rejects(xm.xm_match(None, None, None, None, None, ctypes.byref(h)), "NULL argument")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_join(None, 1, 0, None, ctypes.byref(h)), "NULL result")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_pick_pairs(None, None, 0, None, ctypes.byref(h)), "NULL argument")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_levels_compute(None, None, None, 0, None, ctypes.byref(h)), "NULL argument")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_match_batch(None, None, 0, None, None, ctypes.byref(h)), "bad arguments")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_batch_join(None, 0, None, ctypes.byref(h)), "bad arguments")
+    assert h.value is None
+    h = cleared()
+    rejects(xm.xm_match_values(None, -1, None, 0, 0, 0, 1, None, ctypes.byref(h)), "")
+    assert h.value is None
+    rejects(xm.xm_match_values(None, 0, None, 0, 0, 0, 1, None, None), "out is NULL")
+    rejects(xm.xm_levels_compute(None, None, None, 0, None, None), "out is NULL")
+    rejects(xm.xm_pick_pairs(None, None, 0, None, None), "out is NULL")
+    rejects(xm.xm_join(None, 1, 0, None, None), "out is NULL")
+
+    n = xm._i64(7)
+    rejects(xm.xm_join_noalloc(None, 1, 0, None, None, None, 0, ctypes.byref(n), None), "NULL result")
+    assert n.value == 0
+    rejects(xm.xm_join_noalloc(None, 1, 0, None, None, None, 0, None, None), "n_rows")
+    rejects(xm.xm_result_get(None, None), "NULL argument")
+    rejects(xm.xm_rows_get(None, None), "NULL argument")
+    rejects(xm.xm_levels_get(None, None), "NULL argument")
+    rejects(xm.xm_index_info(None, None, None, None, None), "NULL index")
+    rejects(xm.xm_batch_get(None, 0, None), "bad arguments")
+    rejects(xm.xm_batch_info(None, None, None, None), "NULL")
+    rejects(xm.xm_autotune(None, None, 0, None, 0, None, None), "bad arguments")
+    rejects(xm.xm_serve_open(None, None, ctypes.byref(h)), "bad arguments")
+    rejects(xm.xm_serve_submit(None, None, None), "bad arguments")
+    rejects(xm.xm_serve_poll(None, 0, None), "bad arguments")
+    rejects(xm.xm_serve_wait(None, 0, 0), "NULL server")
+    rejects(xm.xm_serve_result(None, 0, None), "bad arguments")
+    rejects(xm.xm_serve_release(None, 0), "NULL server")
+    rejects(xm.xm_serve_get_stats(None, None), "bad arguments")
+    rejects(xm.xm_serve_reset_stats(None), "NULL server")
+    rejects(xm.xm_copy_to_host(None, None, 8, None), "NULL pointer")
+    assert xm.xm_copy_to_host(None, None, 0, None) == 0  # nothing to copy
+    rejects(xm.xm_frame_matrix(None), "NULL")
+    rejects(xm.xm_get_stats(None), "NULL")
+    rejects(xm.xm_prof_read(None, None, None), "NULL name")
+    for free in (xm.xm_index_free, xm.xm_result_free, xm.xm_rows_free, xm.xm_levels_free,
+                 xm.xm_batch_free, xm.xm_serve_close):
+        assert free(bad) == 0
+
+
 def test_stats_reset(xm):
     xm.reset_stats()
     s = xm.stats()
