@@ -167,8 +167,9 @@ def best(pairs, n_a, tau=1e-9):
     """Best pair of every A source (paper §2.2 "best"): the member with the
     smallest separation, ties to the lowest B row. Returns ``best_b`` (int64,
     -1 when A has no member), ``best_sep`` (NaN when none) and ``near_tie``, the
-    A rows whose two smallest separations differ by less than tau times the
-    smallest (their order may depend on the last ulp)."""
+    A rows whose two smallest separations differ, but by less than tau times
+    the smallest (their order may depend on the last ulp; exactly equal ones
+    resolve by row on both sides)."""
     a, b, sep = pairs["a_row"], pairs["b_row"], pairs["sep"]
     best_b = np.full(n_a, -1, np.int64)
     best_sep = np.full(n_a, np.nan)
@@ -187,7 +188,9 @@ def best(pairs, n_a, tau=1e-9):
         same_a = a_s[second] == a_s[idx2]
         second, idx2 = second[same_a], idx2[same_a]
         gap = s_s[second] - s_s[idx2]
-        near = a_s[idx2[gap < tau * s_s[idx2]]]
+        # equal separations are not ambiguous: both programs give them to
+        # the lowest B row; unequal ones closer than tau may swap
+        near = a_s[idx2[(gap > 0) & (gap < tau * s_s[idx2])]]
     return {"best_b": best_b, "best_sep": best_sep, "near_tie": np.asarray(near, np.int64)}
 
 

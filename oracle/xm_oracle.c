@@ -39,7 +39,9 @@
  *      members by how deep inside the region they lie (the "best" pair by
  *      normalised distance) and places them among concentric scaled copies
  *      of the region (paper §3, ClumpPopulator).
- * A region with a zero size has no interior and matches nothing.
+ * A region with a zero size has no interior and matches nothing (whether a
+ * separation is exactly zero depends on the order of rounding, so the closed
+ * boundary would make every such candidate a last-ulp decision).
  *
  * Two ways of finding the candidates, with identical results:
  *   - brute force: every (i, j) pair;

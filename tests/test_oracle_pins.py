@@ -349,6 +349,8 @@ def test_best_is_argmin_of_all(c1_result):
     bb = oracle.best(r, n_a)
     sel = oracle.selected_pairs(r, n_a, "best")
     assert _pairs(sel) <= _pairs(r)
+    # one pair per A source that has members
+    np.testing.assert_array_equal(sel["a_row"], np.unique(r["a_row"]))
     for i in np.unique(r["a_row"])[:2000]:
         m = r["a_row"] == i
         j = np.lexsort((r["b_row"][m], r["sep"][m]))[0]
@@ -601,3 +603,156 @@ def test_concentric_rejects_bad_scales(bad):
     r = oracle.match([1.0], [1.0], [1.0], [1.0], a=1.0)
     with pytest.raises(oracle.OracleError):
         oracle.concentric(r, 1, bad)
+
+
+# -------------------------------------- borderline and near-tie report --
+#
+# Parity is exact equality outside the oracle's borderline set (candidates
+# whose decision margin is below tau = 1e-9, and best pairs whose two
+# smallest separations differ by less than tau times the smallest); these
+# pins show the oracle sees that set, with the margin it defines.
+
+TAU = 1e-9
+
+
+def _on_scaled_boundary(shape, t, a, b, pa, lon0, lat0, n_dir=8):
+    """Points whose normalised distance from (lon0, lat0) is t for a region
+    of the shape: t times the boundary (ellipse (a cos u, b sin u); the
+    rectangle's edges), for n_dir directions."""
+    u = np.radians(np.arange(n_dir) * (360.0 / n_dir) + 7.0)
+    if shape == oracle.RECT:
+        # midpoints and near-corners of the four edges
+        xy = np.array([[a, 0.3 * b], [-a, -0.7 * b], [0.4 * a, b], [-0.9 * a, -b],
+                       [a, -0.99 * b], [-a, 0.5 * b], [0.0, b], [0.2 * a, -b]])[:n_dir]
+    else:
+        bb = a if shape == oracle.CIRCLE else b
+        xy = np.stack([a * np.cos(u), bb * np.sin(u)], 1)
+    return _region_points(lon0, lat0, pa, t * xy)
+
+
+def _margin_of(shape, t):
+    """The decision margin the oracle defines for a point at normalised
+    distance t: |rho/r - 1| for circles, |q - 1| = |t^2 - 1| for ellipses,
+    |max(|X|/a, |Y|/b) - 1| for rectangles."""
+    return abs(t * t - 1.0) if shape == oracle.ELLIPSE else abs(t - 1.0)
+
+
+@pytest.mark.parametrize("shape", [oracle.CIRCLE, oracle.ELLIPSE, oracle.RECT])
+@pytest.mark.parametrize("lat0", [3.0, -71.0, 89.9])
+def test_borderline_candidates_are_listed(shape, lat0):
+    # large regions (10 arcmin) so the construction's ~1e-10 arcsec position
+    # error is ~1e-13 relative, far below every margin used here
+    a, b, pa = 600.0, 350.0, 40.0
+    listed, unlisted = (1.0 - 1e-11, 1.0 + 1e-11), (1.0 - 1e-7, 1.0 + 1e-7)
+    ts = listed + unlisted
+    lon, lat = [], []
+    for t in ts:
+        lo, la = _on_scaled_boundary(shape, t, a, b, pa, 150.0, lat0)
+        lon.append(lo); lat.append(la)
+    n_dir = lon[0].size
+    lon, lat = np.concatenate(lon), np.concatenate(lat)
+    r = oracle.match([150.0], [lat0], lon, lat, shape=shape, a=a, b=b, pa=pa)
+    t_of = np.repeat(ts, n_dir)
+    # members: exactly the points at t <= 1
+    np.testing.assert_array_equal(r["b_row"], np.nonzero(t_of <= 1.0)[0])
+    # listed: exactly the points within 1e-11 of the boundary, with A's row
+    np.testing.assert_array_equal(np.sort(r["border_b"]), np.nonzero(np.abs(t_of - 1.0) < 1e-9)[0])
+    assert np.all(r["border_a"] == 0)
+    assert np.all(r["border_margin"] < TAU)
+
+
+@pytest.mark.parametrize("shape", [oracle.CIRCLE, oracle.ELLIPSE, oracle.RECT])
+def test_borderline_margin_values(shape):
+    """The reported margin is the one defined per shape (not, say, the
+    normalised distance's distance from 1 for ellipses)."""
+    a, b, pa = 900.0, 500.0, 115.0
+    ts = (1.0 - 3e-10, 1.0 + 3e-10, 1.0 - 4.5e-10)
+    lon, lat = [], []
+    for t in ts:
+        lo, la = _on_scaled_boundary(shape, t, a, b, pa, 20.0, 40.0, n_dir=4)
+        lon.append(lo); lat.append(la)
+    lon, lat = np.concatenate(lon), np.concatenate(lat)
+    r = oracle.match([20.0], [40.0], lon, lat, shape=shape, a=a, b=b, pa=pa)
+    expect = np.repeat([_margin_of(shape, t) for t in ts], 4)
+    assert r["border_b"].size == expect.size
+    got = np.empty(expect.size)
+    got[r["border_b"]] = r["border_margin"]
+    np.testing.assert_allclose(got, expect, rtol=0, atol=2e-11)
+
+
+def test_borderline_circle_relative_to_radius():
+    """The circle's margin is relative to the radius: a point 1e-7 arcsec
+    outside a 1e-3 arcsec circle is far from borderline (1e-4), one
+    2e-13 arcsec outside it is listed."""
+    lon, lat = _region_points(10.0, 0.0, 0.0, np.array([[1e-3 + 1e-7, 0.0], [5e-4, 0.0]]))
+    r = oracle.match([10.0], [0.0], lon, lat, a=1e-3)
+    assert r["border_b"].size == 0
+    np.testing.assert_array_equal(r["b_row"], [1])
+    r2 = oracle.match([10.0], [0.0], lon, lat, a=(1e-3 + 1e-7) * (1.0 + 1e-11))
+    np.testing.assert_array_equal(r2["border_b"], [0])
+
+
+def _two_members(s1, s2, s3=None):
+    """A at (60, -20) with members at separations s1, s2 (and s3) arcsec
+    along different bearings, inside a circle of twice the largest."""
+    seps = [s1, s2] + ([s3] if s3 is not None else [])
+    xy = np.array([[s * np.cos(np.radians(50 * k + 10)), s * np.sin(np.radians(50 * k + 10))]
+                   for k, s in enumerate(seps)])
+    lon, lat = _region_points(60.0, -20.0, 0.0, xy)
+    return oracle.match([60.0], [-20.0], lon, lat, a=2.0 * max(seps))
+
+
+@pytest.mark.parametrize("s", [500.0, 2.0])
+def test_best_near_tie_listed(s):
+    r = _two_members(s, s * (1.0 + 1e-11))
+    assert r["a_row"].size == 2
+    np.testing.assert_array_equal(oracle.best(r, 1)["near_tie"], [0])
+    r = _two_members(s, s * (1.0 + 1e-7))
+    assert oracle.best(r, 1)["near_tie"].size == 0
+
+
+def test_best_near_tie_is_relative_to_the_separation():
+    # 500 arcsec apart by 5e-9 arcsec (1e-11 relative): listed; 0.01 arcsec
+    # apart by 5e-10 arcsec (5e-8 relative): not listed
+    np.testing.assert_array_equal(oracle.best(_two_members(500.0, 500.0 + 5e-9), 1)["near_tie"], [0])
+    assert oracle.best(_two_members(0.01, 0.01 * (1 + 5e-8)), 1)["near_tie"].size == 0
+
+
+def test_best_near_tie_compares_the_two_smallest():
+    # first and second differ by 1e-11 (listed) although the third is far;
+    # first and second far apart, second and third close: not listed
+    r = _two_members(3.0, 3.0 * (1 + 1e-11), 4.0)
+    np.testing.assert_array_equal(oracle.best(r, 1)["near_tie"], [0])
+    r = _two_members(2.0, 3.0, 3.0 * (1 + 1e-11))
+    assert oracle.best(r, 1)["near_tie"].size == 0
+
+
+def test_near_tie_from_pair_lists():
+    """The selection logic alone, on hand-made pair lists: rows 0 and 2 have
+    near ties, row 1 an exact duplicate (ties resolve by row, not listed as
+    near), row 3 a single member; per B the same through best_per_b."""
+    pairs = {"a_row": np.array([0, 0, 1, 1, 2, 2, 2, 3]),
+             "b_row": np.array([5, 3, 1, 2, 0, 4, 6, 7]),
+             "sep": np.array([7.0, 7.0 * (1 + 3e-10), 2.0, 2.0, 1.5, 9.0, 1.5 * (1 - 4e-10), 1.0])}
+    bb = oracle.best(pairs, 4)
+    np.testing.assert_array_equal(bb["near_tie"], [0, 2])
+    np.testing.assert_array_equal(bb["best_b"], [5, 1, 6, 7])
+    # every B source of these pairs is held once: no near tie per B
+    np.testing.assert_array_equal(oracle.best_per_b(pairs, 8)["near_tie"], [])
+    # B 9 held by A rows 0 and 1 at nearly equal separations
+    two = {"a_row": np.array([0, 1]), "b_row": np.array([9, 9]), "sep": np.array([4.0, 4.0 * (1 + 1e-10)])}
+    np.testing.assert_array_equal(oracle.best_per_b(two, 10)["near_tie"], [9])
+    np.testing.assert_array_equal(oracle.pick(two, 2, 10, "best_b")["near_tie_b"], [9])
+
+
+def test_concentric_scale_border_listed():
+    """Pairs whose normalised distance lies within tau (relative) of a scale
+    are listed; the test is relative to the scale (5e-10 away from a scale of
+    0.01 is 5e-8 relative: not listed)."""
+    sc = [0.01, 0.5, 0.9]
+    d = np.array([0.01 * (1 + 1e-11), 0.01 * (1 + 5e-8), 0.5 * (1 - 2e-10), 0.5 * (1 - 1e-7),
+                  0.9, 0.3, 0.9 * (1 + 1e-6)])
+    pairs = {"a_row": np.zeros(d.size, np.int64), "b_row": np.arange(d.size), "sep": d, "dist": d}
+    c = oracle.concentric(pairs, 1, sc)
+    np.testing.assert_array_equal(c["border"], [0, 2, 4])
+    np.testing.assert_array_equal(c["level"], [1, 1, 1, 1, 2, 1, 3])
