@@ -170,13 +170,16 @@ struct JoinScratch {
 static __device__ __align__(256) JoinScratch g_join_scratch;
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is not a device address).
-xm_status join_scratch(JoinScratch** out) {
+// device current (the host-side symbol is not a device address); *dev_out
+// is the current device. Thread-safe.
+xm_status join_scratch(JoinScratch** out, int* dev_out) {
+    static std::mutex mu;
     static JoinScratch* addr[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return set_error(XM_EUNSUPPORTED, "device %d", dev);
+    std::lock_guard<std::mutex> g(mu);
     if (!addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_join_scratch);
@@ -184,6 +187,7 @@ xm_status join_scratch(JoinScratch** out) {
         addr[dev] = (JoinScratch*)p;
     }
     *out = addr[dev];
+    *dev_out = dev;
     return XM_OK;
 }
 
@@ -222,8 +226,14 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
     const int64_t nwords = (nB + 31) / 32;
     cudaStream_t s = (cudaStream_t)stream;
     JoinScratch* S = nullptr;
-    xm_status st = join_scratch(&S);
+    int dev = -1;
+    xm_status st = join_scratch(&S, &dev);
     if (st != XM_OK) return st;
+    // the scratch array is the current device's; the result's arrays live on
+    // the device it was computed on
+    if (dev != R->device)
+        return set_error(XM_EINVAL, "xm_join_noalloc: the result belongs to device %d, current is %d",
+                         R->device, dev);
     // the array keeps the previous call's contents: clear what starts at zero
     cudaError_t e = cudaMemsetAsync(S->bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->small, 0, sizeof(S->small), s);
