@@ -546,6 +546,19 @@ XM_API xm_status xm_serve_close(xm_server* server);
  * waits for it (convenience for callers without their own CUDA runtime). */
 XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);
 
+/* ---- test hook (no counterpart in the paper) ----------------------------- */
+
+/* Sets the look-back of the radix sort's counting passes for tests of its
+ * bounded waits: spin_limit is the number of polls after which a look-back
+ * gives up (0 restores the default, one to two seconds of polling), and
+ * silent_tile (-1 = none) is a tile that publishes none of its status words,
+ * so the look-backs after it wait on words nobody writes. A look-back that
+ * gives up lets its kernel finish (that pass's output is then not sorted)
+ * and the call that ran the sort returns XM_ETIMEOUT; the device stays
+ * usable. The setting holds for every later sort in the process until it is
+ * reset; it is for tests, not for production use. Errors: XM_EINVAL. */
+XM_API xm_status xm_debug_lookback(int32_t spin_limit, int32_t silent_tile);
+
 /* Host only, no device work: the library's galactic -> equatorial rotation
  * (row major, v_eq = m v_gal) built from the IAU frame angles of paper §2's
  * galactic coordinate system (north galactic pole at RA 192.85948 deg,

@@ -13,6 +13,7 @@
 // stores of one digit are contiguous.
 // Prefix sums are reduce-then-scan over tiles of 4096 elements, applied
 // recursively to the tile sums, or a single chained pass.
+#include <atomic>
 #include <mutex>
 
 #include "xm_internal.cuh"
@@ -117,7 +118,7 @@ __global__ void k_plan_finish(SortPlan* plan) {
 constexpr uint64_t kStAgg = 1ull << 62;   // tile's own count is available
 constexpr uint64_t kStInc = 2ull << 62;   // inclusive prefix is available
 constexpr uint64_t kStMask = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 22;      // polls before a look-back gives up
+constexpr int kSpinLimit = 1 << 22;      // polls before a look-back gives up (~1-2 s)
 constexpr int kLookWindow = 8;           // status words loaded per look-back step
 
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
@@ -149,11 +150,17 @@ struct OnesweepSmem {
 // an inclusive prefix, then scatter through shared memory. A walk that finds
 // no progress for kSpinLimit polls flags a timeout and carries on, so no
 // block can wait forever; the caller turns the flag into XM_ETIMEOUT.
+//
+// spin_limit is the poll budget of one look-back (kSpinLimit unless a test
+// lowers it); silent_tile (-1 = none) is a tile that publishes nothing, so
+// the look-backs after it wait on words nobody writes -- the test form of a
+// stalled predecessor, which must end in XM_ETIMEOUT and never in a hang.
 __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
     int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
     unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats) {
+    int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats, int spin_limit,
+    int silent_tile) {
     pdl_wait();
     // with a plan: the digit of pass `pass` of the virtual key, and nothing
     // to do past the passes the plan needs (uniform over the grid)
@@ -199,7 +206,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
         if (warp_base + 32 * k + lane < n) atomicAdd(&S.hist[d], 1);
     }
     __syncthreads();
-    if (threadIdx.x < kRadix) {
+    const bool silent = tile == silent_tile;
+    if (threadIdx.x < kRadix && !silent) {
         const int d = threadIdx.x;
         st_relaxed(status + (int64_t)tile * kRadix + d,
                    (tile == 0 ? kStInc : kStAgg) | (uint64_t)S.hist[d]);
@@ -263,14 +271,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
                     else t--;
                 }
                 if (!done && t >= 0 && (w[0] & ~kStMask) == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicOr(err, kErrTimeout);
                         break;
                     }
                     __nanosleep(64);
                 }
             }
-            st_relaxed(my, kStInc | (uint64_t)(prefix + run));
+            if (!silent) st_relaxed(my, kStInc | (uint64_t)(prefix + run));
         }
         S.gstart[d] = (int64_t)offs[d] + prefix;
     }
@@ -564,6 +572,11 @@ void radix_sort_prepare() {
     done[dev] = true;
 }
 
+// Test settings of the look-back (xm_debug_lookback): poll budget and the
+// tile that withholds its status words.
+std::atomic<int> g_spin_limit{kSpinLimit};
+std::atomic<int> g_silent_tile{-1};
+
 // One pass (two tiles per SM: 64 registers, no spills; three, with spills,
 // measured slower once tiles publish their counts early).
 void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* ki,
@@ -571,7 +584,8 @@ void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* 
                    uint64_t* status, unsigned int* counter, uint64_t* ko, uint32_t* vo,
                    int32_t* err, const SortPlan* plan, int pass) {
     launch_pdl(k_onesweep, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n, shift,
-               offs, status, counter, ko, vo, err, plan, pass, device_stats());
+               offs, status, counter, ko, vo, err, plan, pass, device_stats(), g_spin_limit.load(),
+               g_silent_tile.load());
 }
 
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
@@ -673,3 +687,13 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
 }
 
 }  // namespace xm
+
+extern "C" xm_status xm_debug_lookback(int32_t spin_limit, int32_t silent_tile) {
+    using namespace xm;
+    if (spin_limit < 0 || silent_tile < -1)
+        return set_error(XM_EINVAL, "xm_debug_lookback: spin_limit %d, silent_tile %d", spin_limit,
+                         silent_tile);
+    g_spin_limit.store(spin_limit ? spin_limit : kSpinLimit);
+    g_silent_tile.store(silent_tile);
+    return XM_OK;
+}

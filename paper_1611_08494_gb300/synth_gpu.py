@@ -172,7 +172,10 @@ def c5_requests(b, seed=1006, n_pool=256, a_lo=1_000, a_hi=10_000_000, device="c
     as offset copies (sigma = 0.3 x size) of B sources inside its cap, half
     uniform in the cap; an equatorial request is uniform in a cap given in
     equatorial coordinates (its sources meet B wherever the cap falls).
-    Device tensors; sizes are drawn on the host from the same seed."""
+    Device tensors; sizes are drawn on the host from the same seed. Each
+    request records its cap (centre and radius in its own frame, degrees),
+    the sigma of its offset copies and its largest region size (arcsec), so
+    tests can cut B around it."""
     g = generator(seed, device)
     h = np.random.Generator(np.random.Philox(key=seed))
     bx = torch.cos(torch.deg2rad(b["b_lat"])) * torch.cos(torch.deg2rad(b["b_lon"]))
@@ -211,7 +214,9 @@ def c5_requests(b, seed=1006, n_pool=256, a_lo=1_000, a_hi=10_000_000, device="c
             region.update(a=size, b=size * ratio, pa=float(h.uniform(0.0, 180.0)))
         out.append(dict(lon=u_lon.contiguous(), lat=u_lat.contiguous(), frame=frame,
                         region=region, selection=3, join=JOIN_NAMES[combo % 7],
-                        join_selection=1 if combo < 7 else 2))
+                        join_selection=1 if combo < 7 else 2,
+                        cap=(c_lon, c_lat, rad), offset_sigma=0.3 * size if n_half else 0.0,
+                        max_size=30.0 if per_source else size))
     return out
 
 

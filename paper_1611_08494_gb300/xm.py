@@ -112,6 +112,7 @@ xm_copy_to_host = _sig("xm_copy_to_host", _i32, _p, _p, ctypes.c_size_t, _p)
 xm_join_noalloc = _sig("xm_join_noalloc", _i32, _p, _i32, _i32, _p, _p, _p, _i64,
                        ctypes.POINTER(_i64), _p)
 xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
+xm_debug_lookback = _sig("xm_debug_lookback", _i32, _i32, _i32)
 xm_pick_pairs = _sig("xm_pick_pairs", _i32, _p, _p, _i32, _p, ctypes.POINTER(_p))
 xm_match_values = _sig("xm_match_values", _i32, _p, _i64, _p, _i64, _i32, _i32, _i32, _p,
                        ctypes.POINTER(_p))
