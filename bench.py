@@ -3,23 +3,35 @@
 A step is one pass of the whole path over one synthetic workload: build the
 index of catalogue B (ingest, radix sort on (zone, RA), bucket tables, cell
 offsets), match catalogue A against it with both selections (all pairs and
-best pair), and build the "1 or 2" join rows. Default workload: the
-clump-vs-compact-source case of the paper's §3 use, A = 200,000 per-source
-ellipses against B = 5,000,000 point sources in galactic coordinates.
+best pair), and build the "1 or 2" join rows. The workload is the largest
+single-GPU configuration: the all-sky circle cross-match, A = 5e7 against
+B = 2e8 (int64 ids), r = 2 arcsec, density 1 + 9 exp(-|b|/10 deg) in
+galactic latitude, both poles and the 0/360 seam included.
 
-value      A sources per second over K timed steps, inputs resident in HBM,
-           float32 path with float64 recheck; L2 flushed before every step.
-e2e        the same step through the C ABI with pinned host buffers, the
-           host->device copies of the catalogues and the device->host copy of
-           the join rows and best pairs inside the timed region.
+value      A sources per second over K timed steps, inputs resident in HBM
+           (4 GB of input, far beyond L2; L2 also flushed before every step),
+           float32 tests with float64 recheck in the guard band.
+e2e        the same step through the C ABI with pinned host buffers: the
+           host->device copies of both catalogues (and B's ids) and the
+           device->host copy of the join rows and best pairs in the timed
+           region.
 fp64_path  the same step on the all-float64 path.
 roofline   the dominant kernel, timed with CUDA events on its stream during
-           the timed steps, against the measured HBM copy bandwidth.
-cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+           profiled steps, against the measured HBM copy bandwidth; and the
+           scan's count pass against the same peak (scan_roofline).
+peaks      measured float32 / float64 FMA rates and read-only HBM bandwidth
+           of this GPU (xm_measure_peak).
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload:
+           every A source in 16 seeded caps, against every B source they can
+           reach.
+Legs (N = 1): c2 (the clump-vs-compact-source ellipses, 2e5 x 5e6, with the
+count pass against the measured float32 FMA peak), c4 (4096 batched
+requests, one graph launch), exact_value, serving (C5).
 
---impl reference times that oracle as the reference arm. Under torchrun
-(N > 1) each rank runs its own copy of the workload (weak scaling, no
-data-path collective); rank 0 prints the line with the max time over ranks.
+--impl reference times that oracle as the reference arm on the same sample.
+Under torchrun (N > 1) each rank runs its own copy of the workload (weak
+scaling, no data-path collective); rank 0 prints the line with the max time
+over ranks.
 """
 
 from __future__ import annotations
@@ -27,6 +39,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -40,25 +53,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A-sources cross-matched/sec, FP32+FP64-recheck vs FP64 path; serving p99 ms"
 UNIT = "A-sources/s"
-KERNELS_FOR_ROOFLINE = ("k_scan_fp32_count", "k_digit_scatter", "k_scan_fp32_emit", "k_gather_b")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="size of the all-sky workload (1 = A 5e7 x B 2e8)")
     p.add_argument("--zone-height", type=float, default=0.0, help="arcsec; 0 = tuned default")
     p.add_argument("--cpu-sample", type=int, default=0, help="A sources in the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="serving window after a warm-up of 1/6 of it; 0 skips the serving leg")
     p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     p.add_argument("--serve-b", type=int, default=300_000_000, help="resident B sources")
     p.add_argument("--serve-pool", type=int, default=256, help="distinct request payloads")
     p.add_argument("--serve-slots", type=int, default=3)
-    p.add_argument("--c3-scale", type=float, default=1.0, help="0 skips the all-sky C3 leg")
+    p.add_argument("--c2-leg", type=int, default=1, help="0 skips the C2 ellipse leg")
     p.add_argument("--c4-requests", type=int, default=4096, help="0 skips the batched C4 leg")
     p.add_argument("--c4-b", type=int, default=100_000_000, help="resident B of the C4 leg")
     p.add_argument("--values-scale", type=float, default=1.0,
@@ -90,77 +105,111 @@ def dist_env():
     return rank, world, local
 
 
-def workload(seed_offset=0, scale=1.0):
-    """The C2 workload of one rank: ranks draw different catalogues of the
-    same shape (seed 1002 + rank)."""
-    from paper_1611_08494_gb300 import synth
+def workload(seed_offset=0, scale=1.0, device="cuda"):
+    """The all-sky workload of one rank, on the device: ranks draw different
+    catalogues of the same shape (seed 1003 + rank)."""
+    from paper_1611_08494_gb300 import synth_gpu
 
-    d = synth.c2(seed=1002 + seed_offset, scale=scale)
-    d["desc"] = ("c2 clump-vs-compact-source: A=200000 per-source ellipses (a 5-60 arcsec "
-                 "log-uniform, b/a 0.3-1, PA 0-180), B=5000000, galactic l 0-60 |b|<=1 "
-                 "density exp(-|b|/0.3deg)")
+    d = synth_gpu.c3(seed=1003 + seed_offset, scale=scale, device=device)
+    n_a, n_b = d["a_lon"].numel(), d["b_lon"].numel()
+    d["desc"] = (f"c3 all-sky circle cross-match: A={n_a}, B={n_b} (int64 ids), r=2 arcsec, "
+                 "density 1+9exp(-|b|/10deg) in galactic latitude, both poles and the 0/360 seam, "
+                 "60% of A with a counterpart (sigma 0.5 arcsec)")
     return d
 
 
 # ------------------------------------------------------------------- oracle
 
-def oracle_sample(d, n_sample, nthreads):
-    """Times the oracle (as it stands) on the first n_sample A sources against
-    all of B: its voxel indexing of B, the pair tests and best selection."""
+def cap_sample(d, n_target, seed=2003, n_caps=16):
+    """A bounded sample of the all-sky workload for the oracle: every A source
+    within n_caps caps of equal radius at seeded centres uniform on the
+    sphere (sized so the caps hold about n_target of A), and every B source
+    within that radius plus twice the region radius (all B that can be a
+    member of a sampled A). Host arrays, rows in catalogue order."""
+    import torch
+
+    n_a = d["a_lon"].numel()
+    f = min(1.0, n_target / max(n_a, 1))
+    cos_r = max(-1.0, 1.0 - 2.0 * f / n_caps)  # n_caps x 2 pi (1 - cos r) = 4 pi f
+    rad = math.degrees(math.acos(cos_r))
+    margin = 2.0 * d["region"]["a"] / 3600.0
+    h = np.random.Generator(np.random.Philox(key=seed))
+    centres = [(h.uniform(0.0, 360.0), math.degrees(math.asin(h.uniform(-1.0, 1.0))))
+               for _ in range(n_caps)]
+
+    def unit(lon, lat):
+        lr, br = torch.deg2rad(lon), torch.deg2rad(lat)
+        return torch.cos(br) * torch.cos(lr), torch.cos(br) * torch.sin(lr), torch.sin(br)
+
+    def in_caps(lon, lat, r_deg):
+        x, y, z = unit(lon, lat)
+        m = torch.zeros(lon.numel(), dtype=torch.bool, device=lon.device)
+        for cl, cb in centres:
+            c = (math.cos(math.radians(cb)) * math.cos(math.radians(cl)),
+                 math.cos(math.radians(cb)) * math.sin(math.radians(cl)), math.sin(math.radians(cb)))
+            m |= x * c[0] + y * c[1] + z * c[2] >= math.cos(math.radians(r_deg))
+        return torch.nonzero(m).flatten()
+
+    a_rows = in_caps(d["a_lon"], d["a_lat"], rad)
+    b_rows = in_caps(d["b_lon"], d["b_lat"], min(180.0, rad + margin))
+    return {"a_lon": d["a_lon"][a_rows].cpu().numpy(), "a_lat": d["a_lat"][a_rows].cpu().numpy(),
+            "b_lon": d["b_lon"][b_rows].cpu().numpy(), "b_lat": d["b_lat"][b_rows].cpu().numpy(),
+            "a_frame": d["a_frame"], "b_frame": d["b_frame"], "region": dict(d["region"]),
+            "desc": f"every A source within {n_caps} caps of radius {rad:.3f} deg at seeded "
+                    f"centres ({a_rows.numel()} of {n_a} A) against the {b_rows.numel()} B within "
+                    f"{rad:.3f} deg + {margin * 3600:.0f} arcsec"}
+
+
+def oracle_time(smp, nthreads):
+    """Seconds the oracle (as it stands) takes on a sample: its voxel grid
+    over the sample's B, the pair tests and best selection."""
     import oracle
 
-    sub = np.arange(n_sample, dtype=np.int64)
     t = time.perf_counter()
-    r = oracle.match(d["a_lon"], d["a_lat"], d["b_lon"], d["b_lat"], a_frame=d["a_frame"],
-                     b_frame=d["b_frame"], subset=sub, nthreads=nthreads, **d["region"])
-    oracle.best(r, d["a_lon"].size)
+    r = oracle.match(smp["a_lon"], smp["a_lat"], smp["b_lon"], smp["b_lat"], a_frame=smp["a_frame"],
+                     b_frame=smp["b_frame"], nthreads=nthreads, **smp["region"])
+    oracle.best(r, smp["a_lon"].size)
     return time.perf_counter() - t
 
 
-def cpu_baseline(d, n_sample=0):
-    nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    if not n_sample:
-        # size the sample so the run takes ~10-20 s of CPU work: the time of
-        # a sample is a fixed part (the oracle's grid over all of B) plus a
-        # part per A source, estimated from two small samples
-        t1 = oracle_sample(d, 2000, nthreads)
-        t2 = oracle_sample(d, 12000, nthreads)
-        per_a = max((t2 - t1) / 10000, 1e-9)
-        fixed = max(t1 - 2000 * per_a, 0.0)
-        n_sample = int(min(d["a_lon"].size, max(2000, (12.0 - fixed) / per_a)))
-    dt = oracle_sample(d, n_sample, nthreads)
-    return {"value": n_sample / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"first {n_sample} of {d['a_lon'].size} A sources against all "
-                      f"{d['b_lon'].size} B (voxel grid over B, pair tests, best), "
-                      f"{dt:.2f} s on {nthreads} threads"}
+def host_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(smp):
+    nthreads = host_threads()
+    dt = oracle_time(smp, nthreads)
+    n = smp["a_lon"].size
+    return {"value": n / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{smp['desc']}; {dt:.2f} s on {nthreads} threads"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    d = workload()
-    nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    # each step is a bounded sample, sized so the K steps take about a minute
-    dt = oracle_sample(d, 2000, nthreads)
-    per_step_s = 60.0 / max(args.steps, 1)
-    n_s = args.cpu_sample or int(min(d["a_lon"].size, max(200, 2000 * per_step_s / max(dt, 1e-3))))
-    cb = {"kind": "oracle", "cores": nthreads, "unit": UNIT,
-          "sample": f"first {n_s} of {d['a_lon'].size} A sources per step against all "
-                    f"{d['b_lon'].size} B (voxel grid over B, pair tests, best), "
-                    f"{nthreads} threads"}
-    times = []
+    import torch
+
+    d = workload(scale=args.scale)
+    # each step is the oracle on a bounded sample, sized so the K + W steps
+    # take a minute or two
+    smp = cap_sample(d, args.cpu_sample or 400_000)
+    desc = d["desc"]
+    del d
+    torch.cuda.empty_cache()
+    nthreads = host_threads()
     for _ in range(args.warmup):
-        oracle_sample(d, min(n_s, 2000), nthreads)
-    for _ in range(args.steps):
-        times.append(oracle_sample(d, n_s, nthreads))
+        oracle_time(smp, nthreads)
+    times = [oracle_time(smp, nthreads) for _ in range(args.steps)]
     tot = sum(times)
+    n_s = smp["a_lon"].size
     v = n_s * len(times) / tot
-    cb = dict(cb, value=v)
+    cb = {"kind": "oracle", "cores": nthreads, "unit": UNIT, "value": v,
+          "sample": f"{smp['desc']}, per step, {nthreads} threads"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": d["desc"], "sample_a": n_s},
+            "data": "synthetic", "config": {"workload": desc, "sample_a": n_s},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -294,26 +343,26 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_1611_08494_gb300 import xm
 
-    d = workload(seed_offset=rank)
-    n_a, n_b = d["a_lon"].size, d["b_lon"].size
-    cu = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")  # noqa: E731
-    dev = {k: cu(d[k]) for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
-    reg_dev = {k: (cu(v) if isinstance(v, np.ndarray) else v) for k, v in d["region"].items()}
+    measured = xm.measure_peaks()  # this GPU's float32 / float64 FMA and read rates
+    d = workload(seed_offset=rank, scale=args.scale)
+    n_a, n_b = d["a_lon"].numel(), d["b_lon"].numel()
+    # the oracle's sample is cut now (small host arrays), timed at the end
+    smp = cap_sample(d, args.cpu_sample or 1_500_000) if (rank == 0 and world == 1
+                                                          and not args.no_cpu_baseline) else None
+    dev = {k: d[k] for k in ("a_lon", "a_lat", "b_lon", "b_lat", "b_id")}
     zone_h = args.zone_height or 12.0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-
     host_out = {}
 
-    def step(prec, fp64_index, cols=None, reg=None, copy_out=False, out_slot=0, idx=None):
+    def step(prec, fp64_index, cols=None, copy_out=False, out_slot=0, idx=None):
         cols = cols or dev
-        reg = reg or reg_dev
         # the build's input check is read at the match's synchronisation
         if idx is None:
-            idx = xm.Index(cols["b_lon"], cols["b_lat"], frame=d["b_frame"],
+            idx = xm.Index(cols["b_lon"], cols["b_lat"], frame=d["b_frame"], ids=cols["b_id"],
                            zone_height_arcsec=zone_h, build_fp64=fp64_index, deferred_check=True)
         res = xm.Result(idx, cols["a_lon"], cols["a_lat"], frame=d["a_frame"], precision=prec,
-                        selection=xm.SEL_ALL | xm.SEL_BEST, **reg)
+                        selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
         rows = res.join("or")
         out = None
         if copy_out:
@@ -329,10 +378,10 @@ def run_ours(args):
                 dst.copy_(src, non_blocking=True)
         return idx, res, rows, out
 
-    def timed(prec, fp64_index, steps, warmup, cols=None, reg=None, copy_out=False,
-              profile=False, clocks=None):
+    def timed(prec, fp64_index, steps, warmup, cols=None, copy_out=False, profile=False,
+              clocks=None):
         for _ in range(warmup):
-            step(prec, fp64_index, cols, reg, copy_out)
+            step(prec, fp64_index, cols, copy_out)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -344,15 +393,16 @@ def run_ours(args):
             nvtx_push("xm_timed")
         ms, bytes_out = [], 0
         for _ in range(steps):
-            flush.zero_()  # evict the inputs from L2 between steps
+            flush.zero_()  # evict what the previous step left in L2
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, res, rows, out = step(prec, fp64_index, cols, reg, copy_out)
+            _, res, rows, out = step(prec, fp64_index, cols, copy_out)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
             if out is not None:
                 bytes_out = sum(t.numel() * t.element_size() for t in out)
+            del res, rows
         torch.cuda.synchronize()
         if clocks:
             nvtx_pop()
@@ -363,87 +413,36 @@ def run_ours(args):
         st = xm.stats()
         if world > 1:
             dist.barrier()
-        return ms, st, prof, res, rows, bytes_out
+        return ms, st, prof, bytes_out
 
     # float32 + float64 recheck (the product path), uninstrumented
     with Clocks(local) as clk:
-        ms, st, _, res, rows, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup, clocks=clk)
+        ms, st, _, _ = timed(xm.PREC_FP32, False, args.steps, args.warmup, clocks=clk)
     total_ms = max_over_ranks(sum(ms), world, "cuda")
     value = weak_scaling_value(n_a, args.steps, world, total_ms)
     launches = st["kernel_launches"]
+    _, res, rows, _ = step(xm.PREC_FP32, False)
+    n_pairs, n_rows = int(res.n_pairs), int(rows.n)
+    del res, rows
 
     # the same steps again with an event pair around every launch: per-kernel
     # times for the shares and the roofline (the events cost a little time,
     # so these steps are not the ones the value comes from)
-    prof_steps = max(10, args.steps // 4)
-    ms_p, st_p, prof, _, _, _ = timed(xm.PREC_FP32, False, prof_steps, 1, profile=True)
+    prof_steps = max(5, args.steps // 4)
+    ms_p, st_p, prof, _ = timed(xm.PREC_FP32, False, prof_steps, 1, profile=True)
 
     # all-float64 path
-    ms64, _, _, _, _, _ = timed(xm.PREC_FP64, True, max(3, args.steps // 2), 1)
+    ms64, _, _, _ = timed(xm.PREC_FP64, True, max(3, args.steps // 2), 1)
     v64 = n_a * len(ms64) / (sum(ms64) / 1e3)
 
-    # end to end through the C ABI from pinned host memory
-    host = {k: torch.as_tensor(d[k]).pin_memory() for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
-    reg_host = {k: (torch.as_tensor(v).pin_memory() if isinstance(v, np.ndarray) else v)
-                for k, v in d["region"].items()}
-    ms_e2e, _, _, _, _, d2h = timed(xm.PREC_FP32, False, max(3, args.steps // 2), 1, cols=host,
-                                    reg=reg_host, copy_out=True)
-    h2d = sum(t.numel() * t.element_size() for t in host.values()) + \
-        sum(t.numel() * t.element_size() for t in reg_host.values() if hasattr(t, "numel"))
-    v_e2e = n_a * len(ms_e2e) / (sum(ms_e2e) / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a)
 
-    # the same, pipelined as a throughput-bound user would run it: steps go
-    # to two streams in turn, and each step's index build (with its input
-    # copy) is issued before the previous step's match, whose pair count
-    # holds the host; so one step's input copy and build overlap the
-    # previous step's match, and its result copy the next step's work (each
-    # step still copies all of its inputs in and its result out; the clock
-    # covers the whole run)
-    def e2e_pipelined(n_steps, warmup):
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        in_flight = [None, None]
-
-        def build(k):
-            with torch.cuda.stream(streams[k % 2]):
-                flush.zero_()
-                return xm.Index(host["b_lon"], host["b_lat"], frame=d["b_frame"],
-                                zone_height_arcsec=zone_h, deferred_check=True)
-
-        def finish(k, idx):
-            with torch.cuda.stream(streams[k % 2]):
-                in_flight[k % 2] = step(xm.PREC_FP32, False, host, reg_host, True,
-                                        out_slot=k % 2, idx=idx)
-
-        def run(n):
-            nxt = build(0)
-            for k in range(n):
-                idx, nxt = nxt, (build(k + 1) if k + 1 < n else None)
-                finish(k, idx)
-
-        run(warmup)
-        torch.cuda.synchronize()
-        cur = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(cur)
-        for st in streams:
-            st.wait_event(e0)
-        run(n_steps)
-        for st in streams:
-            cur.wait_stream(st)
-        e1.record(cur)
-        e1.synchronize()
-        in_flight[0] = in_flight[1] = None
-        return e0.elapsed_time(e1)
-
-    n_pipe = max(3, args.steps // 2)
-    ms_pipe = e2e_pipelined(n_pipe, 2)
-    v_e2e_pipe = n_a * n_pipe / (ms_pipe / 1e3)
-
-    # roofline of the dominant kernel
-    roof = roofline(prof, st_p, prof_steps, n_a, n_b, zone_h, sum(ms_p))
-
-    # further readings of "best pairs" over the C2 pair list (index resident)
-    picks = pick_leg(xm, torch, step, stream)
+    roof = roofline(prof, st_p, prof_steps, n_a, n_b, sum(ms_p), d["region"])
+    scan_roof = kernel_roofline("k_scan_fp32_count", prof, st_p, prof_steps, n_a, n_b, d["region"])
+    del dev, d
+    torch.cuda.empty_cache()
 
     if rank != 0:
         return
@@ -451,33 +450,35 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": d["desc"], "n_a": n_a, "n_b": n_b,
-                   "step": "build B index + match (all and best pairs) + join '1 or 2'",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-recheck", "data": "synthetic",
+        "config": {"workload": workload_desc(n_a, n_b), "n_a": n_a, "n_b": n_b,
+                   "step": "build B index (with int64 ids) + match (all and best pairs) + "
+                           "join '1 or 2'",
                    "precision": "float32 tests, float64 recheck in the guard band",
-                   "zone_height_arcsec": zone_h, "l2": "flushed (256 MiB write) before each step",
+                   "zone_height_arcsec": zone_h,
+                   "l2": "inputs 4 GB, larger than L2; L2 also flushed (256 MiB write) before "
+                         "each step",
                    "index_check": "deferred to the match's synchronisation",
-                   "pairs": int(res.n_pairs), "join_rows": int(rows.n)},
-        "e2e": {"value": v_e2e_pipe, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h),
-                "mode": "two streams in turn, each step's index build (and input copy) issued "
-                        "before the previous step's match: copies overlap the neighbouring "
-                        "steps' work; L2 flushed before each step",
-                "serial_value": v_e2e,
-                "serial_mode": "one step at a time, events around each step"},
-        "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": statistics.mean(ms64)},
+                   "pairs": n_pairs, "join_rows": n_rows},
+        "e2e": e2e,
+        "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": statistics.mean(ms64),
+                      "fp32_recheck_speedup": v64 and value / world / v64},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "scan_roofline": scan_roof,
         "clocks": clk.summary(),
-        "picks": picks,
         "kernels_ms_per_step": {k: round(v[0] / prof_steps, 4) for k, v in
                                 sorted(prof.items(), key=lambda kv: -kv[1][0])[:16]},
         "profiled_ms_per_step": sum(ms_p) / prof_steps,
         "stats_per_step": {k: v // args.steps for k, v in st.items()},
-        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peaks.get("_source")},
+        "peaks": {"hbm_copy_gbs": peaks.get("hbm_gbs"), "hbm_copy_source": peaks.get("_source"),
+                  "hbm_read_gbs": measured["hbm_read_gbs"],
+                  "fp32_fma_tflops": measured["fp32_fma_tflops"],
+                  "fp64_fma_tflops": measured["fp64_fma_tflops"],
+                  "measured_by": "xm_measure_peak on this GPU, best of 5 launches"},
     }
-    if world == 1 and args.c3_scale > 0:
-        line["c3"] = c3_leg(args, xm, torch)
+    if world == 1 and args.c2_leg:
+        line["c2"] = c2_leg(args, xm, torch, measured)
     if world == 1 and args.c4_requests > 0:
         line["c4"] = c4_leg(args, xm, torch)
     if world == 1 and args.values_scale > 0:
@@ -486,9 +487,86 @@ def run_ours(args):
         line["serving"] = serving_leg(args, xm, torch)
     elif world > 1:
         line["serving"] = {"skipped": "the serving leg runs at N = 1 only"}
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(d, args.cpu_sample)
+    if smp is not None:
+        line["cpu_baseline"] = cpu_baseline(smp)
     print(json.dumps(line), flush=True)
+
+
+def workload_desc(n_a, n_b):
+    return (f"c3 all-sky circle cross-match: A={n_a}, B={n_b} (int64 ids), r=2 arcsec, "
+            "density 1+9exp(-|b|/10deg) in galactic latitude, both poles and the 0/360 seam, "
+            "60% of A with a counterpart (sigma 0.5 arcsec)")
+
+
+def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
+    """The step through the C ABI from pinned host memory: inputs copied in
+    and the join rows and best pairs copied out inside the timed region."""
+    host = {k: d[k].cpu().pin_memory() for k in ("a_lon", "a_lat", "b_lon", "b_lat", "b_id")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    stream = torch.cuda.current_stream()
+    n_ser = max(3, args.steps // 4)
+    for _ in range(1):
+        step(xm.PREC_FP32, False, host, True)
+    torch.cuda.synchronize()
+    ms_ser, d2h = [], 0
+    for _ in range(n_ser):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, res, rows, out = step(xm.PREC_FP32, False, host, True)
+        e1.record(stream)
+        e1.synchronize()
+        ms_ser.append(e0.elapsed_time(e1))
+        d2h = sum(t.numel() * t.element_size() for t in out)
+        del res, rows
+    v_ser = n_a * n_ser / (sum(ms_ser) / 1e3)
+
+    # pipelined as a throughput-bound user would run it: steps go to two
+    # streams in turn, and each step's index build (with its input copy) is
+    # issued before the previous step's match, whose pair count holds the
+    # host; so one step's input copy and build overlap the previous step's
+    # match, and its result copy the next step's work (each step still copies
+    # all of its inputs in and its result out; the clock covers the whole run)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    keep = [None, None]
+
+    def build(k):
+        with torch.cuda.stream(streams[k % 2]):
+            flush.zero_()
+            return xm.Index(host["b_lon"], host["b_lat"], frame=d["b_frame"], ids=host["b_id"],
+                            zone_height_arcsec=zone_h, deferred_check=True)
+
+    def finish(k, idx):
+        with torch.cuda.stream(streams[k % 2]):
+            keep[k % 2] = step(xm.PREC_FP32, False, host, True, out_slot=k % 2, idx=idx)
+
+    def run(n):
+        nxt = build(0)
+        for k in range(n):
+            idx, nxt = nxt, (build(k + 1) if k + 1 < n else None)
+            finish(k, idx)
+
+    run(2)
+    torch.cuda.synchronize()
+    n_pipe = max(3, args.steps // 4)
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for st in streams:
+        st.wait_event(e0)
+    run(n_pipe)
+    for st in streams:
+        cur.wait_stream(st)
+    e1.record(cur)
+    e1.synchronize()
+    keep[0] = keep[1] = None
+    ms_pipe = e0.elapsed_time(e1)
+    del host
+    return {"value": n_a * n_pipe / (ms_pipe / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "mode": "two streams in turn, each step's index build (and input copy) issued before "
+                    "the previous step's match: copies overlap the neighbouring steps' work",
+            "serial_value": v_ser, "serial_mode": "one step at a time, events around each step"}
 
 
 def pick_leg(xm, torch, step, stream):
@@ -526,62 +604,81 @@ def pick_leg(xm, torch, step, stream):
     return out
 
 
-# ------------------------------------------------------- all-sky C3 leg
+# --------------------------------------------------------- C2 ellipse leg
 
-def c3_leg(args, xm, torch):
-    """The all-sky circle workload at full size (A = 5e7, B = 2e8 by
-    default): index build, then match with both selections, FP32 + recheck
-    and all-FP64; the scan's count pass against the HBM roofline."""
-    from paper_1611_08494_gb300 import synth_gpu
+def c2_leg(args, xm, torch, measured):
+    """The clump-vs-compact-source case: A = 2e5 per-source ellipses against
+    B = 5e6 in the galactic plane. The same step (build + match all and best
+    + join "1 or 2") on both paths, the count pass against the measured
+    float32 FMA peak (12 float32 operations per candidate), the index sort
+    against the HBM peak, and the further readings of "best pairs" over its
+    pair list."""
+    from paper_1611_08494_gb300 import synth
 
-    d = synth_gpu.c3(scale=args.c3_scale)
-    n_a, n_b = d["a_lon"].numel(), d["b_lon"].numel()
+    d = synth.c2()
+    n_a, n_b = d["a_lon"].size, d["b_lon"].size
+    cu = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")  # noqa: E731
+    cols = {k: cu(d[k]) for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
+    reg = {k: (cu(v) if isinstance(v, np.ndarray) else v) for k, v in d["region"].items()}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    out = {"workload": f"c3 all-sky circle r=2 arcsec: A={n_a}, B={n_b}, density 1+9exp(-|b|/10deg), "
-                       "poles and 0/360 seam, int64 ids, galactic", "steps": 3}
-    peak = load_peaks().get("hbm_gbs", 6800.0)
-    for prec, fp64_index, name in ((xm.PREC_FP32, False, "fp32_recheck"), (xm.PREC_FP64, True, "fp64")):
-        t_build, t_match = [], []
-        for k in range(5):  # a warm-up, three timed passes, one profiled
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            if k == 4:
-                xm.reset_stats()
-                xm.prof_enable(True)
-                nvtx_push(f"c3_{name}")
+
+    def step(prec, fp64_index=False):
+        idx = xm.Index(cols["b_lon"], cols["b_lat"], frame=d["b_frame"], zone_height_arcsec=12.0,
+                       build_fp64=fp64_index, deferred_check=True)
+        res = xm.Result(idx, cols["a_lon"], cols["a_lat"], frame=d["a_frame"], precision=prec,
+                        selection=xm.SEL_ALL | xm.SEL_BEST, **reg)
+        rows = res.join("or")
+        return idx, res, rows, None
+
+    def timed(prec, fp64_index, steps, profile=False):
+        for _ in range(3):
+            step(prec, fp64_index)
+        torch.cuda.synchronize()
+        xm.reset_stats()
+        if profile:
+            xm.prof_enable(True)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            idx = xm.Index(d["b_lon"], d["b_lat"], frame=d["b_frame"], ids=d["b_id"],
-                           zone_height_arcsec=12.0, build_fp64=fp64_index)
+            step(prec, fp64_index)
             e1.record(stream)
-            res = xm.Result(idx, d["a_lon"], d["a_lat"], frame=d["a_frame"], precision=prec,
-                            selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
-            e2.record(stream)
-            e2.synchronize()
-            if k == 4:
-                nvtx_pop()
-            if 1 <= k <= 3:
-                t_build.append(e0.elapsed_time(e1))
-                t_match.append(e1.elapsed_time(e2))
-            pairs = int(res.n_pairs)
-            del res, idx
-        prof = xm.prof_all()
-        xm.prof_enable(False)
-        st = xm.stats()
-        scan = prof.get("k_scan_fp32_count" if prec == xm.PREC_FP32 else "k_scan_fp64_count")
-        entry = {"a_per_s_match": n_a / (statistics.median(t_match) / 1e3),
-                 "a_per_s_step": n_a / ((statistics.median(t_match) + statistics.median(t_build)) / 1e3),
-                 "index_build_ms": statistics.median(t_build), "match_ms": statistics.median(t_match),
-                 "pairs": pairs, "candidates": int(st["candidates"]),
-                 "kernels_ms": {k: round(v[0], 3) for k, v in
-                                sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
-        if scan:
-            alg = n_a * (16 + 24 + 16) + st["candidates"] * 12
-            ach = alg / (scan[0] / scan[1] * 1e-3) / 1e9
-            entry["scan_roofline"] = {"kernel": "k_scan count pass", "bound": "hbm",
-                                      "algorithmic_bytes": alg, "ms": scan[0] / scan[1],
-                                      "achieved": ach, "peak": peak, "unit": "GB/s",
-                                      "frac": ach / peak, "peak_source": "of measured"}
-        out[name] = entry
-    del d
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        prof = xm.prof_all() if profile else {}
+        if profile:
+            xm.prof_enable(False)
+        return ms, xm.stats(), prof
+
+    k = max(10, args.steps)
+    ms32, _, _ = timed(xm.PREC_FP32, False, k)
+    ms64, _, _ = timed(xm.PREC_FP64, True, max(5, k // 2))
+    ms_p, st_p, prof = timed(xm.PREC_FP32, False, 10, profile=True)
+    out = {"workload": "c2 clump-vs-compact-source: A=200000 per-source ellipses (a 5-60 arcsec "
+                       "log-uniform, b/a 0.3-1, PA 0-180), B=5000000, galactic l 0-60 |b|<=1 "
+                       "density exp(-|b|/0.3deg)",
+           "ms_per_step": statistics.median(ms32), "a_per_s": n_a / (statistics.median(ms32) / 1e3),
+           "fp64_ms_per_step": statistics.median(ms64),
+           "fp64_a_per_s": n_a / (statistics.median(ms64) / 1e3),
+           "kernels_ms_per_step": {kk: round(v[0] / 10, 4) for kk, v in
+                                   sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]}}
+    scan = prof.get("k_scan_fp32_count")
+    if scan:
+        cand = st_p["candidates"] / 10
+        t = scan[0] / scan[1] * 1e-3
+        flops = 12.0 * cand
+        out["count_pass_fp32"] = {"kernel": "k_scan count pass", "bound": "fp32",
+                                  "candidates": int(cand), "flops_per_candidate": 12,
+                                  "ms": t * 1e3, "achieved_tflops": flops / t / 1e12,
+                                  "peak_tflops": measured["fp32_fma_tflops"],
+                                  "frac": flops / t / 1e12 / measured["fp32_fma_tflops"],
+                                  "peak_source": "of measured (xm_measure_peak)"}
+        out["count_pass_hbm"] = kernel_roofline("k_scan_fp32_count", prof, st_p, 10, n_a, n_b, reg)
+    out["sort_roofline"] = kernel_roofline("k_onesweep", prof, st_p, 10, n_a, n_b, reg)
+    out["picks"] = pick_leg(xm, torch, step, stream)
+    del cols, reg
     torch.cuda.empty_cache()
     return out
 
@@ -780,42 +877,59 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "_source": "fallback"}
 
 
-def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, zone_h):
+def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, region):
     """Bytes the method must move per launch of a kernel (averaged over the
     launches, so achieved = all bytes / all kernel time):
     k_onesweep   per key and pass 8 B key + 4 B row, read and written, over
                  the passes that ran (the library counts keys x passes; an
                  index sort planned to fewer passes launches the rest empty);
-    k_scan_fp32_count  per A 16 B position + 24 B region columns + 16 B best
-                 row, per candidate 12 B (offsets + RA key);
+    k_scan_fp32_count  per A 16 B position + 8 B per region column given per
+                 source + 16 B best pair, per candidate 12 B (offsets + RA
+                 key);
+    k_prep_a     per A 16 B position (+ region columns) read, 88 B of
+                 prepared record written;
     k_gather_b   per B 16 B position read + 16 B record + 16 B position
                  written."""
+    cols = sum(1 for k in ("a_col", "b_col", "pa_col") if region.get(k) is not None)
     if kernel == "k_onesweep":
         return 24.0 * st["sort_key_passes"] / launches
-    if kernel == "k_scan_fp32_count":
-        return n_a * (16 + 24 + 16) + st["candidates"] / steps * 12
+    if kernel in ("k_scan_fp32_count", "k_scan_fp64_count"):
+        return (n_a * (16 + 8 * cols + 16) + st["candidates"] / steps * 12) * steps / launches
+    if kernel == "k_prep_a":
+        return n_a * (16 + 8 * cols + 88) * steps / launches
     if kernel == "k_gather_b":
-        return n_b * (16 + 16 + 16)
+        return n_b * (16 + 16 + 16) * steps / launches
     return None
 
 
-def roofline(prof, st, steps, n_a, n_b, zone_h, total_ms):
-    if not prof:
+def kernel_roofline(name, prof, st, steps, n_a, n_b, region):
+    """achieved = algorithmic bytes per launch / average launch time, against
+    the measured HBM copy bandwidth."""
+    if name not in prof:
         return None
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    name, (tot_ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    tot_ms, launches = prof[name]
     per_launch_ms = tot_ms / launches
-    alg = algorithmic_bytes(name, st, steps, launches, n_a, n_b, zone_h)
-    out = {"kernel": name, "bound": "hbm", "peak": peak, "unit": "GB/s", "ms_per_launch": per_launch_ms,
-           "launches_per_step": launches / steps, "share_of_step": tot_ms / total_ms,
+    out = {"kernel": name, "bound": "hbm", "peak": peak, "unit": "GB/s",
+           "ms_per_launch": per_launch_ms, "launches_per_step": launches / steps,
            "achieved": None, "frac": None, "traffic": None,
            "peak_source": "of measured" if peaks.get("_source") == "measured" else "of fallback"}
-    if alg is None:
-        return out
-    achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    out.update(achieved=achieved, frac=achieved / peak, algorithmic_bytes=alg,
-               traffic=traffic_record(name))
+    alg = algorithmic_bytes(name, st, steps, launches, n_a, n_b, region)
+    if alg is not None:
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        out.update(achieved=achieved, frac=achieved / peak, algorithmic_bytes=alg,
+                   traffic=traffic_record(name))
+    return out
+
+
+def roofline(prof, st, steps, n_a, n_b, total_ms, region):
+    """The dominant kernel of the step (largest share of the profiled time)."""
+    if not prof:
+        return None
+    name, (tot_ms, _) = max(prof.items(), key=lambda kv: kv[1][0])
+    out = kernel_roofline(name, prof, st, steps, n_a, n_b, region)
+    out["share_of_step"] = tot_ms / total_ms
     return out
 
 

@@ -546,6 +546,20 @@ XM_API xm_status xm_serve_close(xm_server* server);
  * waits for it (convenience for callers without their own CUDA runtime). */
 XM_API xm_status xm_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);
 
+/* ---- measured ceilings of this device (no counterpart in the paper) ----- */
+
+/* The denominators of the library's rooflines, measured on the current
+ * device with kernels built into the library (each the best of five
+ * event-timed launches on `stream` after one untimed launch):
+ *   XM_PEAK_FP32_FMA  float32 fused multiply-add rate, TFLOP/s (2 per FMA);
+ *   XM_PEAK_FP64_FMA  float64 fused multiply-add rate, TFLOP/s;
+ *   XM_PEAK_HBM_READ  read-only streaming bandwidth over a 4 GiB buffer
+ *                     (far beyond L2), GB/s.
+ * Allocates (and frees) a 4 GiB buffer for XM_PEAK_HBM_READ. Synchronises
+ * `stream`. Errors: XM_EINVAL, XM_ENOMEM, XM_ECUDA. */
+typedef enum { XM_PEAK_FP32_FMA = 0, XM_PEAK_FP64_FMA = 1, XM_PEAK_HBM_READ = 2 } xm_peak;
+XM_API xm_status xm_measure_peak(int32_t what, double* value, void* stream);
+
 /* ---- test hook (no counterpart in the paper) ----------------------------- */
 
 /* Sets the look-back of the radix sort's counting passes for tests of its

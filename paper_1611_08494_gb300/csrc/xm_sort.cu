@@ -173,14 +173,25 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int given_up;
     if (threadIdx.x == 0) {
         S.tile = (int)atomicAdd(tile_counter, 1u);
         if (S.tile == 0 && stats) atomicAdd(&stats[5], (unsigned long long)n);  // keys this pass
+        given_up = (*(volatile int32_t*)err & kErrTimeout) != 0;
     }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
     if (threadIdx.x < kRadix) S.hist[threadIdx.x] = 0;
     __syncthreads();
     const int tile = S.tile;
+    // A look-back of this sort gave up (in this pass or an earlier one): the
+    // keys of this pass may hold holes and repeats, so their digit counts no
+    // longer match the offsets. Scatter nothing (every write stays in
+    // bounds), and publish inclusive words so no later tile waits here; the
+    // sort's guard then leaves a valid permutation for whoever reads it.
+    if (given_up) {
+        if (threadIdx.x < kRadix) st_relaxed(status + (int64_t)tile * kRadix + threadIdx.x, kStInc);
+        return;
+    }
     const int64_t tile_base = (int64_t)tile * kSortTile;
     const int64_t warp_base = tile_base + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -317,9 +328,30 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
         const int p = threadIdx.x + j * kSortThreads;
         if (p < valid_n) {
             const int64_t g = S.gstart[S.dig[p]] + p;
-            keys_out[g] = S.keys[p];
-            vals_out[g] = S.vals[p];
+            if ((uint64_t)g < (uint64_t)n) {  // (always, unless a look-back gave up)
+                keys_out[g] = S.keys[p];
+                vals_out[g] = S.vals[p];
+            }
         }
+    }
+}
+
+// After the counting passes of a sort: if a look-back gave up, the keys and
+// rows are not a sorted permutation (a tile that timed out scattered with a
+// partial prefix, later tiles and passes scattered nothing). Both buffers of
+// the pair are then set to one valid, sorted content -- every key 0, rows in
+// order -- so the kernels that read the sort before the host sees
+// XM_ETIMEOUT index only rows that exist. Returns at once otherwise.
+__global__ void k_sort_guard(const int32_t* err, uint64_t* k0, uint32_t* v0, uint64_t* k1,
+                             uint32_t* v1, int64_t n) {
+    pdl_wait();
+    if (!(*(volatile const int32_t*)err & kErrTimeout)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        k0[i] = 0;
+        k1[i] = 0;
+        v0[i] = (uint32_t)i;
+        v1[i] = (uint32_t)i;
     }
 }
 
@@ -588,6 +620,12 @@ void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* 
                g_silent_tile.load());
 }
 
+xm_status sort_guard(const int32_t* err, uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
+                     int64_t n, cudaStream_t s) {
+    XM_LAUNCH("k_sort_guard", 2 * 152, 256, 0, s, k_sort_guard, err, k0, v0, k1, v1, n);
+    return XM_OK;
+}
+
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
     XM_LAUNCH("k_plan_init", 1, 1, 0, s, k_plan_init, plan);
     return XM_OK;
@@ -633,6 +671,7 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
         uint64_t* t = ki; ki = ko; ko = t;
         uint32_t* u = vi; vi = vo; vo = u;
     }
+    if (st == XM_OK) st = sort_guard(err, keys, vals, tk, tv, n, s);
     dev_free(work, s);
     return st;
 }
@@ -677,6 +716,7 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
         uint64_t* t = ki; ki = ko; ko = t;
         uint32_t* u = vi; vi = vo; vo = u;
     }
+    if (st == XM_OK) st = sort_guard(err, keys, vals, tk, tv, n, s);
     if (st == XM_OK && ki != keys) {
         cudaError_t e1 = cudaMemcpyAsync(keys, ki, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
         cudaError_t e2 = cudaMemcpyAsync(vals, vi, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);

@@ -113,6 +113,19 @@ xm_join_noalloc = _sig("xm_join_noalloc", _i32, _p, _i32, _i32, _p, _p, _p, _i64
                        ctypes.POINTER(_i64), _p)
 xm_frame_matrix = _sig("xm_frame_matrix", _i32, ctypes.POINTER(_f64))
 xm_debug_lookback = _sig("xm_debug_lookback", _i32, _i32, _i32)
+xm_measure_peak = _sig("xm_measure_peak", _i32, _i32, ctypes.POINTER(_f64), _p)
+PEAKS = {"fp32_fma_tflops": 0, "fp64_fma_tflops": 1, "hbm_read_gbs": 2}
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured float32 / float64 FMA rates (TFLOP/s) and read-only HBM
+    bandwidth (GB/s) of the current device (xm_measure_peak)."""
+    out = {}
+    for name, what in PEAKS.items():
+        v = _f64()
+        check(xm_measure_peak(what, ctypes.byref(v), _stream_handle(stream)), "xm_measure_peak")
+        out[name] = v.value
+    return out
 xm_pick_pairs = _sig("xm_pick_pairs", _i32, _p, _p, _i32, _p, ctypes.POINTER(_p))
 xm_match_values = _sig("xm_match_values", _i32, _p, _i64, _p, _i64, _i32, _i32, _i32, _p,
                        ctypes.POINTER(_p))

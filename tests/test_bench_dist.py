@@ -26,7 +26,7 @@ def _rank_main(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     local = [12.5, 30.0][rank]
     job = bench.max_over_ranks(local, world, "cpu")
-    d = bench.workload(seed_offset=rank, scale=0.001)
+    d = bench.workload(seed_offset=rank, scale=0.0002, device="cpu")
     dist.barrier()
     out[rank] = (job, bench.weak_scaling_value(1000, 10, world, job), float(d["a_lon"][:50].sum()))
     dist.destroy_process_group()

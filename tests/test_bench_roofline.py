@@ -9,6 +9,8 @@ import pytest
 
 import bench
 
+REGION = dict(shape=0, a=2.0)  # fixed circles, as the all-sky workload
+
 
 def test_dominant_kernel_and_arithmetic(monkeypatch):
     monkeypatch.setattr(bench, "load_peaks", lambda: {"hbm_gbs": 6000.0, "_source": "measured"})
@@ -17,7 +19,7 @@ def test_dominant_kernel_and_arithmetic(monkeypatch):
     # two steps, four planned passes over n_b keys each, five launches a step
     st = {"sort_key_passes": steps * 4 * n_b, "candidates": 40_000}
     prof = {"k_onesweep": (0.5, 10), "k_scan_fp32_count": (0.3, 2), "k_gather_b": (0.1, 2)}
-    r = bench.roofline(prof, st, steps, n_a, n_b, 12.0, total_ms=2.0)
+    r = bench.roofline(prof, st, steps, n_a, n_b, total_ms=2.0, region=REGION)
     assert r["kernel"] == "k_onesweep"
     alg = 24.0 * steps * 4 * n_b / 10  # 8 B key + 4 B row, read and written, per key and pass
     assert r["algorithmic_bytes"] == pytest.approx(alg)
@@ -28,24 +30,29 @@ def test_dominant_kernel_and_arithmetic(monkeypatch):
     assert r["launches_per_step"] == pytest.approx(5.0)
     assert r["traffic"] == 1.5e7 and r["peak_source"] == "of measured"
 
-    # the count pass dominating: per A 56 B, per candidate 12 B
+    # the count pass dominating: per A 16 B position + 16 B best (fixed
+    # circles: no region column), per candidate 12 B
     prof["k_scan_fp32_count"] = (0.9, 2)
-    r = bench.roofline(prof, st, steps, n_a, n_b, 12.0, total_ms=2.0)
+    r = bench.roofline(prof, st, steps, n_a, n_b, total_ms=2.0, region=REGION)
     assert r["kernel"] == "k_scan_fp32_count"
-    assert r["algorithmic_bytes"] == pytest.approx(n_a * 56 + 40_000 / steps * 12)
+    assert r["algorithmic_bytes"] == pytest.approx(n_a * 32 + 40_000 / steps * 12)
     assert r["traffic"] is None
+    # per-source ellipses read three float64 columns more per A
+    r = bench.roofline(prof, st, steps, n_a, n_b, total_ms=2.0,
+                       region=dict(shape=1, a_col=[1.0], b_col=[1.0], pa_col=[0.0]))
+    assert r["algorithmic_bytes"] == pytest.approx(n_a * 56 + 40_000 / steps * 12)
 
     # a kernel without an algorithmic figure: no fraction is claimed
     prof["k_other"] = (5.0, 1)
-    r = bench.roofline(prof, st, steps, n_a, n_b, 12.0, total_ms=8.0)
+    r = bench.roofline(prof, st, steps, n_a, n_b, total_ms=8.0, region=REGION)
     assert r["kernel"] == "k_other" and r["achieved"] is None and r["frac"] is None
-    assert bench.roofline({}, st, steps, n_a, n_b, 12.0, 1.0) is None
+    assert bench.roofline({}, st, steps, n_a, n_b, 1.0, REGION) is None
 
 
 def test_fallback_peak_is_named(monkeypatch):
     monkeypatch.setattr(bench, "load_peaks", lambda: {"hbm_gbs": 6800.0, "_source": "fallback"})
     r = bench.roofline({"k_gather_b": (0.2, 2)}, {"sort_key_passes": 0, "candidates": 0}, 2,
-                       10, 1000, 12.0, 1.0)
+                       10, 1000, 1.0, REGION)
     assert r["peak_source"] == "of fallback" and r["peak"] == 6800.0
     assert r["algorithmic_bytes"] == 1000 * 48
 

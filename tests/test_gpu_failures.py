@@ -6,8 +6,8 @@
   and the next build on the same device must succeed and match correctly.
 * A failing allocation: a caller allocator (xm_set_allocator) that fails on
   its k-th request, for every k a match makes; the match must return
-  XM_ENOMEM, give back everything it had allocated, and the next match must
-  succeed."""
+  XM_ENOMEM (or, where the failed buffer was optional, the right result),
+  give back everything it had allocated, and the next match must succeed."""
 
 import ctypes
 import gc
@@ -135,12 +135,23 @@ def test_failed_allocation_returns_enomem_and_leaks_nothing(xm):
         torch.cuda.synchronize()
         assert al.live == held
         assert n_alloc >= 3
+        refused = 0
         for k in range(n_alloc):
             al.arm(k)
-            with pytest.raises(xm.XMError, match="XM_ENOMEM"):
-                match()
+            try:
+                r = match()
+            except xm.XMError as ex:
+                assert ex.status == "XM_ENOMEM", str(ex)
+                refused += 1
+            else:
+                # an optional buffer (the speculative pair list) may fail
+                # without failing the call: the result must still be right
+                np.testing.assert_array_equal(r.a_row.cpu().numpy(), ref_a)
+                np.testing.assert_array_equal(r.b_row.cpu().numpy(), ref_b)
+                del r
             torch.cuda.synchronize()
             assert al.live == held, f"allocation {k} failed: {len(al.live) - len(held)} arrays leaked"
+        assert refused >= n_alloc // 2
         al.arm(None)
         again = match()  # the next call succeeds
         np.testing.assert_array_equal(again.a_row.cpu().numpy(), ref_a)
