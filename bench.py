@@ -775,32 +775,68 @@ def c4_leg(args, xm, torch):
 def serving_leg(args, xm, torch):
     """Poisson arrivals against a resident B index through the library's
     serving loop (continuous batching, admission by free device memory).
-    Requests take their payloads from a pool of pre-generated device
-    requests; latency is submit -> results complete on the device."""
-    import threading
-
+    Requests take their payloads from a pool of pre-generated requests;
+    latency runs from the call that submits a request (its columns are
+    copied inside it) to its results complete on the device. Three windows:
+    requests submitted from pinned host columns (the headline), the same
+    from device-resident columns, and host submission under a small memory
+    budget (admission refuses requests that can never fit and queues the
+    ones that do not fit yet)."""
     from paper_1611_08494_gb300 import synth_gpu
 
     t_setup = time.perf_counter()
     b = synth_gpu.c5_catalogue(n_b=args.serve_b)
     pool = synth_gpu.c5_requests(b, n_pool=args.serve_pool)
-    sample = [dict(q, lon=q["lon"], lat=q["lat"], **q["region"]) for q in pool[:6]]
-    for q in sample:
-        q.pop("region")
+    sample = [dict(lon=q["lon"], lat=q["lat"], frame=q["frame"], selection=q["selection"],
+                   join=q["join"], join_selection=q["join_selection"], **q["region"])
+              for q in pool[:6]]
     tuned = xm.autotune(b["b_lon"], b["b_lat"], sample, frame=b["b_frame"],
                         zone_heights=(10.0, 20.0, 40.0), blocks_per_sm=(2, 4))
     idx = xm.Index(b["b_lon"], b["b_lat"], frame=b["b_frame"], ids=b["b_id"],
                    zone_height_arcsec=tuned["zone_height_arcsec"])
     del b
+    pinned = lambda t: t.cpu().pin_memory()  # noqa: E731
+    host_pool = []
+    for q in pool:
+        reg = {k: (pinned(v) if hasattr(v, "numel") else v) for k, v in q["region"].items()}
+        host_pool.append(dict(q, lon=pinned(q["lon"]), lat=pinned(q["lat"]), region=reg))
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     setup_s = time.perf_counter() - t_setup
+    common = dict(slots=args.serve_slots, pool=len(pool),
+                  zone_height_arcsec=tuned["zone_height_arcsec"],
+                  persistent_blocks=tuned["persistent_blocks"], setup_s=setup_s)
+    out = {"workload": f"c5 serving: B={args.serve_b} resident (C3 latitude profile, galactic, "
+                       f"int64 ids), Poisson {args.serve_rate:g} req/s, n_A log-uniform 1e3-1e7, "
+                       "mixed shapes/joins/frames, admission by free HBM",
+           "latency": "from the submitting call (input copy included) to results complete on "
+                      "the device"}
+    host = serve_window(args, xm, idx, host_pool, args.serve_seconds, 0, tuned, 0)
+    out.update(host, input="pinned host columns, copied by the submitting call", **common)
+    short = max(5.0, args.serve_seconds / 3.0)
+    out["device_inputs"] = dict(serve_window(args, xm, idx, pool, short, 1, tuned, 0),
+                                input="device-resident columns (device-to-device copy)")
+    budget = 2 << 30
+    out["memory_pressure"] = dict(serve_window(args, xm, idx, host_pool, short, 2, tuned, budget),
+                                  input="pinned host columns", mem_budget_bytes=budget)
+    del pool, host_pool, idx
+    torch.cuda.empty_cache()
+    return out
 
-    warm = args.serve_seconds / 6.0
-    times, h = synth_gpu.poisson_arrivals(args.serve_rate, warm + args.serve_seconds)
+
+def serve_window(args, xm, idx, pool, seconds, seed_offset, tuned, budget):
+    """One serving window: Poisson arrivals for seconds (after a sixth of it
+    of warm-up) drawing payloads from pool; a completion thread waits for and
+    releases every ticket. Returns the server's statistics for the window."""
+    import threading
+
+    from paper_1611_08494_gb300 import synth_gpu
+
+    warm = seconds / 6.0
+    times, h = synth_gpu.poisson_arrivals(args.serve_rate, warm + seconds, seed=1007 + seed_offset)
     which = h.integers(0, len(pool), len(times))
     srv = xm.Server(idx, slots=args.serve_slots, precision=xm.PREC_FP32, use_graph=True,
-                    persistent_blocks=tuned["persistent_blocks"])
+                    persistent_blocks=tuned["persistent_blocks"], mem_budget_bytes=budget)
     tickets = []
     done = threading.Event()
     lock = threading.Lock()
@@ -828,8 +864,10 @@ def serving_leg(args, xm, torch):
     th = threading.Thread(target=complete, daemon=True)
     th.start()
     offered_a = 0
+    refused_submit = 0
     t0 = time.perf_counter()
     reset_done = False
+    t_win = t0
     for t_arr, w in zip(times, which):
         now = time.perf_counter() - t0
         if t_arr > now:
@@ -839,8 +877,14 @@ def serving_leg(args, xm, torch):
             t_win = time.perf_counter()
             reset_done = True
         q = pool[w]
-        tk = srv.submit(q["lon"], q["lat"], frame=q["frame"], selection=q["selection"],
-                        join=q["join"], join_selection=q["join_selection"], **q["region"])
+        try:
+            tk = srv.submit(q["lon"], q["lat"], frame=q["frame"], selection=q["selection"],
+                            join=q["join"], join_selection=q["join_selection"], **q["region"])
+        except xm.XMError as ex:
+            if ex.status != "XM_EBUSY":
+                raise
+            refused_submit += reset_done
+            continue
         with lock:
             tickets.append(tk)
         if reset_done:
@@ -851,21 +895,12 @@ def serving_leg(args, xm, torch):
     st = srv.stats()
     srv.close()
     window = t_end - t_win if reset_done else float("nan")
-    out = {"workload": f"c5 serving: B={args.serve_b} resident (C3 latitude profile, galactic, "
-                       f"int64 ids), Poisson {args.serve_rate:g} req/s, n_A log-uniform 1e3-1e7, "
-                       "mixed shapes/joins/frames, admission by free HBM",
-           "window_s": args.serve_seconds, "warmup_s": warm, "requests": int(st["completed"]),
-           "failed": int(st["failed"]), "refused": int(st["refused"]),
-           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-           "sustained_a_per_s": st["a_sources"] / window,
-           "offered_a_per_s": offered_a / args.serve_seconds,
-           "drain_s": window - args.serve_seconds, "batches": int(st["batches"]),
-           "busy_s": st["busy_s"], "slots": args.serve_slots, "pool": len(pool),
-           "zone_height_arcsec": tuned["zone_height_arcsec"],
-           "persistent_blocks": tuned["persistent_blocks"], "setup_s": setup_s}
-    del pool, idx
-    torch.cuda.empty_cache()
-    return out
+    return {"window_s": seconds, "warmup_s": warm, "requests": int(st["completed"]),
+            "failed": int(st["failed"]), "refused": int(st["refused"]),
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "sustained_a_per_s": st["a_sources"] / window,
+            "offered_a_per_s": offered_a / seconds,
+            "drain_s": window - seconds, "batches": int(st["batches"]), "busy_s": st["busy_s"]}
 
 
 def load_peaks():

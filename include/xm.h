@@ -494,7 +494,9 @@ typedef struct {
     int64_t submitted, completed, failed, refused;
     int64_t a_sources;            /* A sources of completed requests */
     int64_t batches;
-    double p50_ms, p99_ms, max_ms;  /* latency submit -> results complete */
+    double p50_ms, p99_ms, max_ms;  /* latency: entry into xm_serve_submit (the copy of the
+                                       request's columns included) -> results complete on
+                                       the device */
     double busy_s;                /* wall time with at least one batch on the device */
     int64_t mem_in_use, mem_budget;
 } xm_serve_stats;
@@ -510,8 +512,9 @@ typedef struct xm_server xm_server;
  * free up and their work overlaps on the device. */
 XM_API xm_status xm_serve_open(const xm_index* index, const xm_serve_opts* opts, xm_server** out);
 
-/* Queues a request; its columns are copied, so the caller may free them on
- * return. *ticket identifies it. XM_EBUSY when the request alone exceeds the
+/* Queues a request; its columns are copied (host or device, by on_device)
+ * before it returns, so the caller may free them on return; its latency is
+ * counted from the call. *ticket identifies it. XM_EBUSY when the request alone exceeds the
  * memory budget (it could never be admitted); XM_EINVAL as xm_match. */
 XM_API xm_status xm_serve_submit(xm_server* server, const xm_request* request, int64_t* ticket);
 

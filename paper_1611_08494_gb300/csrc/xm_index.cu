@@ -194,12 +194,24 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, 
 }
 
 __global__ void k_zone_lut(int32_t nz, const int64_t* __restrict__ lut_off,
-                           ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut) {
+                           ZoneInfo* __restrict__ zones, ZoneHot* __restrict__ zhot,
+                           uint32_t* __restrict__ lut) {
     pdl_wait();
     const int32_t z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= nz) return;
     const int64_t base = lut_off[z];
     zones[z].lut_base = base;
+    const ZoneInfo& Z = zones[z];
+    ZoneHot H;
+    H.start = (uint32_t)Z.start;
+    H.lut_rel = (int32_t)(base - 2 * Z.start);
+    H.lut_kmin = Z.lut_kmin;
+    H.shift_lg = Z.lut_shift | ((uint32_t)(__ffs(Z.lut_nb) - 1) << 8);
+    H.nbins = Z.nbins;
+    H.sin_cf = Z.sin_cf;
+    H.cos_cf = Z.cos_cf;
+    H.binw_f = Z.binw_f;
+    zhot[z] = H;
     if (zones[z].end == zones[z].start) {  // empty zone: one empty bucket
         lut[base] = 0;
         lut[base + 1] = 0;
@@ -374,9 +386,10 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         X->pos = (double2*)dev_alloc(nn * sizeof(double2), s);
         X->zone_start = (int64_t*)dev_alloc((X->nz + 1) * sizeof(int64_t), s);
         X->zones = (ZoneInfo*)dev_alloc(X->nz * sizeof(ZoneInfo), s);
-        if (!X->rec || !X->pos || !X->zone_start || !X->zones) { fail(set_error(XM_ENOMEM, "index arrays")); break; }
+        X->zhot = (ZoneHot*)dev_alloc(X->nz * sizeof(ZoneHot), s);
+        if (!X->rec || !X->pos || !X->zone_start || !X->zones || !X->zhot) { fail(set_error(XM_ENOMEM, "index arrays")); break; }
         X->bytes = nn * (sizeof(BRec) + sizeof(double2)) + (X->nz + 1) * sizeof(int64_t) +
-                   X->nz * sizeof(ZoneInfo);
+                   X->nz * (sizeof(ZoneInfo) + sizeof(ZoneHot));
         if (fp64) {
             X->px = (double*)dev_alloc(3 * nn * sizeof(double), s);
             if (!X->px) { fail(set_error(XM_ENOMEM, "index unit vectors")); break; }
@@ -454,7 +467,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
                       X->zones, lut_cnt);
             r = exclusive_scan_i32(lut_cnt, lut_off, X->nz, nullptr, err, s);
             if (r != XM_OK) return r;
-            XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->lut);
+            XM_LAUNCH("k_zone_lut", gz, kBlock, 0, s, k_zone_lut, X->nz, lut_off, X->zones, X->zhot,
+                      X->lut);
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
                 XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, S, n, X->pos, X->nz,
@@ -510,6 +524,7 @@ extern "C" xm_status xm_index_free(xm_index* X) {
     dev_free(X->id, s);
     dev_free(X->zone_start, s);
     dev_free(X->zones, s);
+    dev_free(X->zhot, s);
     dev_free(X->lut, s);
     dev_free(X->build_err, s);
     delete X;

@@ -81,12 +81,52 @@ struct __align__(16) ZoneInfo {
     uint32_t lut_nb;       // buckets (a power of two)
 };
 
+// The fields of a zone the candidate scan reads, packed into one 32-byte
+// sector (the table of all zones stays in L2). Catalogues hold fewer than
+// 2^31 rows, so the zone's first row fits 32 bits; the bucket table of a zone
+// of m rows has at most 2m + 1 entries (2 when empty), so its first entry lies
+// within [start + z, 2 start + 2z] and is kept relative to 2 start.
+struct __align__(32) ZoneHot {
+    uint32_t start;     // first index row of the zone
+    int32_t lut_rel;    // first bucket entry of the zone, minus 2 * start
+    uint32_t lut_kmin;  // smallest ra_key of the zone
+    uint32_t shift_lg;  // key bits per bucket | log2(buckets) << 8
+    uint32_t nbins;     // RA cells
+    float sin_cf, cos_cf;  // of the zone centre latitude
+    float binw_f;          // RA cell width (rad)
+};
+
+__device__ __forceinline__ ZoneHot load_zone_hot(const ZoneHot* p) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + 1);
+    ZoneHot z;
+    z.start = u.x;
+    z.lut_rel = (int32_t)u.y;
+    z.lut_kmin = u.z;
+    z.shift_lg = u.w;
+    z.nbins = v.x;
+    z.sin_cf = __uint_as_float(v.y);
+    z.cos_cf = __uint_as_float(v.z);
+    z.binw_f = __uint_as_float(v.w);
+    return z;
+}
+
 // One B source in index order (16 bytes: one vector load per candidate).
 struct __align__(16) BRec {
     float xi, eta;    // offsets in the tangent frame of the source's cell
     uint32_t ra_key;  // key64 >> 32
     int32_t row;      // row in the caller's B catalogue
 };
+
+__device__ __forceinline__ BRec load_brec(const BRec* p) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    BRec b;
+    b.xi = __uint_as_float(u.x);
+    b.eta = __uint_as_float(u.y);
+    b.ra_key = u.z;
+    b.row = (int32_t)u.w;
+    return b;
+}
 
 // One A source, prepared in (zone, RA) order.
 struct __align__(16) APrep {
@@ -116,6 +156,7 @@ struct IndexGeom {
     const double* py;
     const double* pz;
     const ZoneInfo* zones;  // [nz]
+    const ZoneHot* zhot;    // [nz] the scan's part of each zone
     const uint32_t* lut;    // RA bucket tables of all zones
     int32_t nz;
     double h;        // zone height (rad)
@@ -540,12 +581,13 @@ struct xm_index {
     int64_t* id;
     int64_t* zone_start;
     xm::ZoneInfo* zones;
+    xm::ZoneHot* zhot;
     uint32_t* lut;
     int64_t lut_n;
     int64_t bytes;
     int32_t* build_err;  // error bits of a build whose check was deferred (else NULL)
     xm::IndexGeom geom() const {
-        return xm::IndexGeom{rec, pos, px, py, pz, zones, lut, nz, h, (float)h};
+        return xm::IndexGeom{rec, pos, px, py, pz, zones, zhot, lut, nz, h, (float)h};
     }
 };
 

@@ -278,7 +278,7 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
     int64_t dk = 0;
     if (!full) {
         // half-width of the RA window: asin(sin R / cos dec), widened
-        const ZoneInfo& Z = G.zones[A.z];
+        const ZoneHot Z = load_zone_hot(G.zhot + A.z);
         const LatTerms L = lat_terms(G.h_f * A.zfrac, Z.sin_cf, Z.cos_cf);
         const float ratio = sinf(Rm) / L.cd;
         if (!(L.cd > 0.0f && ratio < 0.9999f)) full = true;
@@ -311,38 +311,25 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
     return W;
 }
 
-// Rows [lo, hi) of a zone whose ra_key lies in [klo, khi]: the zone's RA
-// bucket table narrows each bound to one bucket (about one source), and the
-// two searches run in step so their loads overlap. Keys outside the zone's
-// key range clamp to its first or last bucket.
-__device__ __forceinline__ void zone_bounds(const IndexGeom& G, const ZoneInfo& Z, uint32_t klo,
-                                            uint32_t khi, int64_t* lo_out, int64_t* hi_out) {
-    const uint32_t* L = G.lut + Z.lut_base;
-    const uint32_t last = Z.lut_nb - 1;
+// Rows [lo, hi) of a zone holding every row whose ra_key lies in
+// [klo, khi]: the whole buckets of the zone's RA bucket table that the key
+// window touches (about one source per bucket), from two table reads and no
+// search; the candidates' own keys are compared with the window as they are
+// read. Keys outside the zone's key range clamp to its first or last bucket.
+__device__ __forceinline__ void bucket_bounds(const IndexGeom& G, const ZoneHot& Z, uint32_t klo,
+                                              uint32_t khi, int64_t* lo_out, int64_t* hi_out) {
+    const int64_t start = Z.start;
     if (khi < Z.lut_kmin) {  // the whole window lies before the zone's first key
-        *lo_out = *hi_out = Z.start;
+        *lo_out = *hi_out = start;
         return;
     }
-    const uint32_t bl = klo <= Z.lut_kmin ? 0u : min((klo - Z.lut_kmin) >> Z.lut_shift, last);
-    const uint32_t bh = min((khi - Z.lut_kmin) >> Z.lut_shift, last);
-    int64_t lo0 = Z.start + __ldg(&L[bl]), lo1 = Z.start + __ldg(&L[bl + 1]);
-    int64_t hi0 = Z.start + __ldg(&L[bh]), hi1 = Z.start + __ldg(&L[bh + 1]);
-    // first row with key >= klo in [lo0, lo1]; first row with key > khi in [hi0, hi1]
-    while (lo0 < lo1 || hi0 < hi1) {
-        const int64_t ml = lo0 + ((lo1 - lo0) >> 1), mh = hi0 + ((hi1 - hi0) >> 1);
-        const uint32_t vl = lo0 < lo1 ? __ldg(&G.rec[ml].ra_key) : 0u;
-        const uint32_t vh = hi0 < hi1 ? __ldg(&G.rec[mh].ra_key) : 0u;
-        if (lo0 < lo1) {
-            if (vl < klo) lo0 = ml + 1;
-            else lo1 = ml;
-        }
-        if (hi0 < hi1) {
-            if (vh <= khi) hi0 = mh + 1;
-            else hi1 = mh;
-        }
-    }
-    *lo_out = lo0;
-    *hi_out = hi0 < lo0 ? lo0 : hi0;
+    const uint32_t shift = Z.shift_lg & 0xFFu;
+    const uint32_t last = (1u << (Z.shift_lg >> 8)) - 1u;
+    const uint32_t* L = G.lut + (2 * start + Z.lut_rel);
+    const uint32_t bl = klo <= Z.lut_kmin ? 0u : min((klo - Z.lut_kmin) >> shift, last);
+    const uint32_t bh = min((khi - Z.lut_kmin) >> shift, last);
+    *lo_out = start + __ldg(&L[bl]);
+    *hi_out = start + __ldg(&L[bh + 1]);
 }
 
 // Float64 unit vector of B row `row` (exact positions are kept by row).
@@ -373,7 +360,7 @@ struct ItemTerms {
     uint32_t binA, nbins;      // integer cell of A (exact product), cells
 };
 
-__device__ __forceinline__ ItemTerms item_terms(const APrep& A, const ZoneInfo& Z, int32_t z,
+__device__ __forceinline__ ItemTerms item_terms(const APrep& A, const ZoneHot& Z, int32_t z,
                                                 float h_f) {
     ItemTerms t;
     const LatTerms L = lat_terms(h_f * ((float)(A.z - z) + A.zfrac), Z.sin_cf, Z.cos_cf);
@@ -459,6 +446,7 @@ struct ScanWarpSmem {
     uint32_t wlo[32][2], whi[32][2];
     int32_t ipref[33];         // first item of each source
     int32_t it_a[kItemCap];
+    uint32_t it_klo[kItemCap], it_khi[kItemCap];  // the item's key window
     int64_t it_lo[kItemCap];
     int32_t it_start[kItemCap + 1];  // first candidate of each item
     ItemTerms it_t[kItemCap];
@@ -552,10 +540,13 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
             const int r = t - W.ipref[al];
             const int ns = W.nseg[al];
             const int z = W.z0[al] + r / ns, sg = r % ns;
-            const ZoneInfo& Z = G.zones[z];
-            int64_t lo = Z.start, hi = Z.start;
-            if (Z.end > Z.start) zone_bounds(G, Z, W.wlo[al][sg], W.whi[al][sg], &lo, &hi);
+            const ZoneHot Z = load_zone_hot(G.zhot + z);
+            const uint32_t klo = W.wlo[al][sg], khi = W.whi[al][sg];
+            int64_t lo, hi;
+            bucket_bounds(G, Z, klo, khi, &lo, &hi);
             W.it_a[k] = al;
+            W.it_klo[k] = klo;
+            W.it_khi[k] = khi;
             W.it_lo[k] = lo;
             W.it_start[k] = (int32_t)(hi - lo);  // count, scanned below
             if (PREC == kPrecFP32 && hi > lo) W.it_t[k] = item_terms(W.A[al], Z, z, G.h_f);
@@ -590,24 +581,33 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
         __syncwarp();
         const int total_cand = W.it_start[nb];
 
-        // ---- candidates, 32 per round
-        int k = 0;  // item of this lane's candidate; only moves forward
+        // ---- candidates, 32 per round. The records of the next round are
+        // loaded before this round is tested, so consecutive rounds' loads
+        // overlap the tests. A lane's record belongs to its item's bucket
+        // range; it is a candidate when its key lies in the item's window.
+        int kp = 0;  // item of the prefetched candidate; only moves forward
+        int nxt_k = 0;
+        BRec nxt;
+        auto fetch = [&](int c) {
+            const int cc = c < total_cand ? c : total_cand - 1;
+            while (W.it_start[kp + 1] <= cc) kp++;  // last item with start <= c
+            nxt_k = kp;
+            if (c < total_cand) nxt = load_brec(G.rec + W.it_lo[kp] + (c - W.it_start[kp]));
+        };
+        if (total_cand > 0) fetch(lane);
         for (int c0 = 0; c0 < total_cand; c0 += 32) {
             const int c = c0 + lane;
             const bool active = c < total_cand;
-            {
-                const int cc = active ? c : total_cand - 1;
-                while (W.it_start[k + 1] <= cc) k++;  // last item with start <= c
-            }
+            const int k = nxt_k;
+            const BRec b = nxt;
+            if (c0 + 32 < total_cand) fetch(c0 + 32 + lane);
             const int al = W.it_a[k];
             bool is_mem = false;
             long long key = kKeyInf, rep = 0;
             int32_t brow = 0x7fffffff;
             bool rep32 = false;
-            if (active) {
-                const int64_t j = W.it_lo[k] + (c - W.it_start[k]);
+            if (active && b.ra_key >= W.it_klo[k] && b.ra_key <= W.it_khi[k]) {
                 const APrep& A = W.A[al];
-                const BRec b = G.rec[j];
                 brow = b.row;
                 n_cand++;
                 const bool s64 = W.sep64[al];

@@ -205,6 +205,9 @@ extern "C" xm_status xm_serve_open(const xm_index* index, const xm_serve_opts* o
 }
 
 extern "C" xm_status xm_serve_submit(xm_server* S, const xm_request* q, int64_t* ticket) {
+    // a request's latency runs from here (its arrival), so the copy of its
+    // columns is inside it
+    const auto t_arrival = Clock::now();
     if (!S || !q || !ticket) return set_error(XM_EINVAL, "xm_serve_submit: bad arguments");
     *ticket = 0;
     xm_status st = check_request(*q, 0);
@@ -269,7 +272,7 @@ extern "C" xm_status xm_serve_submit(xm_server* S, const xm_request* q, int64_t*
             return set_error(XM_EBUSY, "xm_serve_submit: server is closing");
         }
         t->id = S->next_id++;
-        t->t_submit = Clock::now();
+        t->t_submit = t_arrival;
         S->tickets[t->id] = t;
         S->queue.push_back(t);
         S->submitted++;
