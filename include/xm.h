@@ -293,6 +293,36 @@ XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int
                                  int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
                                  int64_t* n_rows, void* stream);
 
+/* ---- catalogue 1 split across processes (paper §2.3) --------------------- */
+
+/* The paper's tool splits the first catalogue across processes, each
+ * matching its part against the whole second catalogue. Here each process
+ * (one per GPU) matches a contiguous slice of A rows against its own copy of
+ * the index (xm_match); the only exchange is the set of matched B rows,
+ * which the B-side joins need over all slices (a B source is unmatched only
+ * if no slice matched it).
+ *
+ * xm_result_mark_b ORs into `bits` (device memory, (n_b + 31) / 32 words,
+ * bit j of word j / 32 = B row j) the B rows of the result's selected pairs
+ * (selection ALL or BEST). It does not clear `bits`. Does not synchronise.
+ * Errors: XM_EINVAL (NULL argument, selection not in the result), XM_ECUDA.
+ *
+ * xm_join_shard builds the join rows of one slice as xm_join would for the
+ * whole catalogue: `b_matched` (device, the OR over every slice's
+ * xm_result_mark_b) decides which B rows are unmatched; every A row written
+ * is shifted by a_row_offset (the slice's first row in the whole
+ * catalogue); B-only rows are written only when with_b_rows is non-zero
+ * (give it to the last slice, so that the rows of the slices, concatenated in
+ * slice order, are exactly xm_join's rows of the whole catalogue), and their
+ * number is in n_unmatched_b either way. Does not synchronise; xm_rows_get
+ * reads the count. Errors: as xm_join; XM_EINVAL for a NULL b_matched or a
+ * negative offset. */
+XM_API xm_status xm_result_mark_b(const xm_result* result, int32_t selection, uint32_t* bits,
+                                  void* stream);
+XM_API xm_status xm_join_shard(const xm_result* result, int32_t selection, int32_t join_type,
+                               const uint32_t* b_matched, int64_t a_row_offset,
+                               int32_t with_b_rows, void* stream, xm_rows** out);
+
 /* ---- the Exact Value functional case (paper §2.1) ------------------------ */
 
 typedef enum { XM_KEY_INT64 = 0, XM_KEY_FLOAT64 = 1 } xm_key_type;

@@ -573,11 +573,11 @@ static xm_status batch_pass(const xm_index* X, const xm_request* reqs, int64_t n
             r = launch_persistent_any(prec, kModeEmit, b, pblocks, s);
             if (r != XM_OK) return r;
             XM_LAUNCH("k_sort_small", grid_for(total), kBlock, 0, s, k_sort_small, B.count,
-                      B.pair_off, total, pair_cap, B.pb, B.ps);
+                      B.pair_off, total, pair_cap, B.pb, B.ps, (const int32_t*)nullptr);
             XM_LAUNCH("k_sort_warp", (unsigned)(8 * sms), 32 * kWarpSortWarps, 0, s, k_sort_warp,
-                      B.count, B.pair_off, total, pair_cap, B.pb, B.ps);
+                      B.count, B.pair_off, total, pair_cap, B.pb, B.ps, (const int32_t*)nullptr);
             XM_LAUNCH("k_seg_sort", (unsigned)(2 * sms), 256, 0, s, k_seg_sort, B.count,
-                      B.pair_off, total, pair_cap, B.pb, B.ps);
+                      B.pair_off, total, pair_cap, B.pb, B.ps, (const int32_t*)nullptr);
             if (prec == XM_PREC_FP32_RECHECK) {
                 ScanArgs c = a;
                 c.list = B.lists + nn;

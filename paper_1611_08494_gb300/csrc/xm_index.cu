@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(kBlock) k_ingest_b(
         lo = lon_mod360(lo);
         const PosKey k = pos_key(lo, la, nz);
         z = (uint32_t)k.z;
-        const uint32_t rk = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
-        ra = rk >> kSortBeginBit;
+        const uint32_t rk = (uint32_t)(k.key64 >> 32) & kIndexRaMask;
+        ra = rk >> kIndexSortBeginBit;
         keys[i] = ((uint64_t)z << 32) | rk;
         vals[i] = (uint32_t)i;
         pos[i] = make_double2(lo, la);
@@ -176,8 +176,8 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, 
     Z.start = zone_start[z];
     Z.end = zone_start[z + 1];
     // RA buckets over the zone's own key range: a power of two, one to two
-    // per source (so a window bound is one table read and rarely a step of
-    // search), at most 2^24 (the resolution of the stored RA keys)
+    // per source (a window's candidates are the rows of the buckets it
+    // touches), at most 2^24
     const int64_t m = Z.end - Z.start;
     int lg = 0;
     while (lg < 24 && ((int64_t)1 << lg) < m) lg++;
@@ -186,8 +186,13 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, 
         kmin = (uint32_t)keys[Z.start];
         range = (uint32_t)keys[Z.end - 1] - kmin;
     }
-    const int bits = range ? 32 - __clz(range) : 0;  // range >> shift < 2^lg
-    Z.lut_shift = (uint32_t)(bits > lg ? bits - lg : 0);
+    const int bits = range ? 32 - __clz(range) : 0;
+    // buckets no finer than the order of the sorted keys (which keep only
+    // the top bits of the RA key), then as many as range >> shift needs
+    int shift = bits > lg ? bits - lg : 0;
+    if (shift < kIndexSortBeginBit) shift = kIndexSortBeginBit;
+    lg = bits > shift ? bits - shift : 0;  // range >> shift < 2^lg
+    Z.lut_shift = (uint32_t)shift;
     Z.lut_kmin = kmin;
     Z.lut_nb = 1u << lg;
     lut_cnt[z] = (1 << lg) + 1;
@@ -458,7 +463,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
                           X->pos, X->px, X->py, X->pz, plan, err);
             }
             // the virtual key: zone offset above the RA bits that vary
-            const int max_passes = (bits_for(X->nz - 1) + 32 - kSortBeginBit + 7) / 8;
+            const int max_passes = (bits_for(X->nz - 1) + 32 - kIndexSortBeginBit + 7) / 8;
             r = index_sort(keys, vals, tk, tv, n, plan, max_passes, err, s);
             if (r != XM_OK) return r;
             const Sorted S{keys, vals, tk, tv, plan};

@@ -541,6 +541,13 @@ __device__ __forceinline__ bool sorted_in_scratch(const SortPlan* plan) { return
 // bit 8. Search windows are widened by one such quantum.
 constexpr uint32_t kRaKeyMask = 0xFFFFFF00u;
 constexpr int kSortBeginBit = 8;
+// The index is ordered by zone and the top 16 bits of the RA key (2^-16 of a
+// turn, 20 arcsec): its RA bucket tables never use finer buckets, and the
+// scan compares every record's own (24-bit) key with the search window, so
+// the order within one such bucket does not matter. A 16-bit RA field saves
+// a counting pass over an all-sky index.
+constexpr uint32_t kIndexRaMask = 0xFFFF0000u;
+constexpr int kIndexSortBeginBit = 16;
 // out[i] = sum of in[0..i) (int64); *total (device) = sum of all. One
 // launch (single-pass, decoupled look-back); a look-back that timed out sets
 // kErrTimeout in *err (device), which the caller reads at its next

@@ -24,6 +24,12 @@ constexpr int kBlock = 256;
 
 unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// Grid of a grid-stride kernel: enough blocks to fill the GPU, no more.
+unsigned grid_cap(int64_t n) {
+    const unsigned g = grid_for(n);
+    return g < 8u * 152u ? g : 8u * 152u;
+}
+
 __global__ void k_mark_b(const int64_t* __restrict__ b_row, int64_t n, uint32_t* __restrict__ bits) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,20 +39,29 @@ __global__ void k_mark_b(const int64_t* __restrict__ b_row, int64_t n, uint32_t*
 }
 
 // Rows each A source contributes, and the number of unmatched A sources.
+// (grid-stride; the unmatched A sources are summed per block, so the one
+// counter takes an atomic per block, not per warp)
 __global__ void k_rows_a(const int32_t* __restrict__ count, int64_t nA, int sel_all,
                          int with_pairs, int with_un_a, int32_t* __restrict__ rows,
                          unsigned long long* __restrict__ n_un_a) {
     pdl_wait();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nA) return;
-    int32_t c = count[i];
-    int32_t sel = sel_all ? c : (c > 0 ? 1 : 0);
-    int32_t r = with_pairs ? sel : 0;
-    if (sel == 0 && with_un_a) r = 1;
-    rows[i] = r;
-    uint32_t mask = __activemask();
-    uint32_t un = __popc(__ballot_sync(mask, c == 0));
-    if ((threadIdx.x & 31) == __ffs(mask) - 1 && un) atomicAdd(n_un_a, (unsigned long long)un);
+    __shared__ unsigned long long block_un;
+    if (threadIdx.x == 0) block_un = 0;
+    __syncthreads();
+    uint32_t un = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nA;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = count[i];
+        const int32_t sel = sel_all ? c : (c > 0 ? 1 : 0);
+        int32_t r = with_pairs ? sel : 0;
+        if (sel == 0 && with_un_a) r = 1;
+        rows[i] = r;
+        un += c == 0;
+    }
+    un = __reduce_add_sync(0xffffffffu, un);
+    if ((threadIdx.x & 31) == 0 && un) atomicAdd(&block_un, (unsigned long long)un);
+    __syncthreads();
+    if (threadIdx.x == 0 && block_un) atomicAdd(n_un_a, block_un);
 }
 
 __device__ __forceinline__ uint32_t word_valid(int64_t w, int64_t nB) {
@@ -68,8 +83,9 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
                           const int64_t* __restrict__ pb, const double* __restrict__ ps,
                           const int64_t* __restrict__ best_b, const double* __restrict__ best_s,
                           const int64_t* __restrict__ row_off, int64_t nA, int sel_all,
-                          int with_pairs, int with_un_a, int pairs_apart, int64_t* __restrict__ oa,
-                          int64_t* __restrict__ ob, double* __restrict__ os) {
+                          int with_pairs, int with_un_a, int pairs_apart, int64_t a_off,
+                          int64_t* __restrict__ oa, int64_t* __restrict__ ob,
+                          double* __restrict__ os) {
     pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
@@ -81,17 +97,17 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
             if (pairs_apart) return;
             int64_t p = pair_off[i];
             for (int32_t k = 0; k < c; k++) {
-                oa[o + k] = i;
+                oa[o + k] = i + a_off;
                 ob[o + k] = pb[p + k];
                 os[o + k] = ps[p + k];
             }
         } else {
-            oa[o] = i;
+            oa[o] = i + a_off;
             ob[o] = best_b[i];
             os[o] = best_s[i];
         }
     } else if (with_un_a) {
-        oa[o] = i;
+        oa[o] = i + a_off;
         ob[o] = -1;
         os[o] = NAN;
     }
@@ -102,7 +118,7 @@ __global__ void k_write_a(const int32_t* __restrict__ count, const int64_t* __re
 // order (coalesced).
 __global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __restrict__ pb,
                               const double* __restrict__ ps, const int64_t* __restrict__ pair_off,
-                              const int64_t* __restrict__ row_off, int64_t n_pairs,
+                              const int64_t* __restrict__ row_off, int64_t n_pairs, int64_t a_off,
                               int64_t* __restrict__ oa, int64_t* __restrict__ ob,
                               double* __restrict__ os) {
     pdl_wait();
@@ -110,7 +126,7 @@ __global__ void k_write_pairs(const int64_t* __restrict__ pa, const int64_t* __r
     if (p >= n_pairs) return;
     const int64_t a = pa[p];
     const int64_t o = row_off[a] + (p - pair_off[a]);
-    oa[o] = a;
+    oa[o] = a + a_off;
     ob[o] = pb[p];
     os[o] = ps[p];
 }
@@ -244,7 +260,7 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
         k_mark_b<<<grid_for(nA), kBlock, 0, s>>>(R->best_b, nA, S->bits);
     }
     if (nA > 0)
-        k_rows_a<<<grid_for(nA), kBlock, 0, s>>>(R->count, nA, sel_all, (int)with_pairs,
+        k_rows_a<<<grid_cap(nA), kBlock, 0, s>>>(R->count, nA, sel_all, (int)with_pairs,
                                                  (int)with_un_a, S->rows,
                                                  (unsigned long long*)&S->small[2]);
     e = cudaGetLastError();
@@ -270,8 +286,8 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
     if (nA > 0)
         k_write_a<<<grid_for(nA), kBlock, 0, s>>>(R->count, R->pair_off, R->b_row, R->sep, R->best_b,
                                                  R->best_sep, S->row_off, nA, sel_all,
-                                                 (int)with_pairs, (int)with_un_a, 0, a_row, b_row,
-                                                 sep);
+                                                 (int)with_pairs, (int)with_un_a, 0, (int64_t)0,
+                                                 a_row, b_row, sep);
     if (with_un_b && nB > 0)
         k_write_b<<<grid_for(nB), kBlock, 0, s>>>(S->bits, S->word_off, nB, &S->small[0], a_row,
                                                  b_row, sep);
@@ -309,31 +325,40 @@ static xm_status resolve_rows(xm_rows* J) {
     return XM_OK;
 }
 
-extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join_type,
-                             void* stream, xm_rows** out) {
-    if (!out) return set_error(XM_EINVAL, "xm_join: out is NULL");
+// The rows of one join type over one selection of a result. ext_bits
+// (nullable): the matched B rows of a catalogue 1 split over several results
+// (the union of their selections), which then decides the unmatched B rows
+// instead of this result's own pairs; a_off is added to every A row written;
+// with_b: write the B-only rows (else only count them).
+static xm_status join_impl(const xm_result* R, int32_t selection, int32_t join_type,
+                           const uint32_t* ext_bits, int64_t a_off, bool with_b, void* stream,
+                           xm_rows** out, const char* who) {
+    if (!out) return set_error(XM_EINVAL, "%s: out is NULL", who);
     *out = nullptr;
-    if (!R) return set_error(XM_EINVAL, "xm_join: NULL result");
+    if (!R) return set_error(XM_EINVAL, "%s: NULL result", who);
     if (selection != XM_SEL_ALL && selection != XM_SEL_BEST)
-        return set_error(XM_EINVAL, "xm_join: selection must be ALL or BEST");
+        return set_error(XM_EINVAL, "%s: selection must be ALL or BEST", who);
     if (!(R->selection & selection))
-        return set_error(XM_EINVAL, "xm_join: selection not computed by xm_match");
+        return set_error(XM_EINVAL, "%s: selection not computed by xm_match", who);
     if (join_type < XM_JOIN_AND || join_type > XM_JOIN_XOR)
-        return set_error(XM_EINVAL, "xm_join: bad join type %d", join_type);
+        return set_error(XM_EINVAL, "%s: bad join type %d", who, join_type);
+    if (a_off < 0) return set_error(XM_EINVAL, "%s: negative A row offset", who);
     const bool with_pairs = join_type == XM_JOIN_AND || join_type == XM_JOIN_OR ||
                             join_type == XM_JOIN_ALL1 || join_type == XM_JOIN_ALL2;
     const bool with_un_a = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL1 ||
                            join_type == XM_JOIN_NOT1_2 || join_type == XM_JOIN_XOR;
     const bool with_un_b = join_type == XM_JOIN_OR || join_type == XM_JOIN_ALL2 ||
                            join_type == XM_JOIN_NOT2_1 || join_type == XM_JOIN_XOR;
+    const bool write_b = with_un_b && with_b;
     const int sel_all = selection == XM_SEL_ALL;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nA = R->n_a, nB = R->n_b;
     const int64_t nwords = (nB + 31) / 32;
     xm_rows* J = new (std::nothrow) xm_rows();
-    if (!J) return set_error(XM_ENOMEM, "xm_join: host allocation");
+    if (!J) return set_error(XM_ENOMEM, "%s: host allocation", who);
 
-    uint32_t* bits = (uint32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
+    uint32_t* own_bits = ext_bits ? nullptr : (uint32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
+    const uint32_t* bits = ext_bits ? ext_bits : own_bits;
     int32_t* rows = (int32_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int32_t), s);
     int64_t* row_off = (int64_t*)dev_alloc((nA > 0 ? nA : 1) * sizeof(int64_t), s);
     int32_t* wcount = (int32_t*)dev_alloc((nwords > 0 ? nwords : 1) * sizeof(int32_t), s);
@@ -343,22 +368,25 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
     int64_t* small = (int64_t*)dev_alloc(5 * sizeof(int64_t), s);
     J->pending = small;
     J->stream = s;
-    J->with_un_b = with_un_b;
+    J->with_un_b = write_b;
     auto body = [&]() -> xm_status {
         if (!bits || !rows || !row_off || !wcount || !word_off || !small)
-            return set_error(XM_ENOMEM, "xm_join: work buffers");
-        cudaError_t e = cudaMemsetAsync(bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 5 * sizeof(int64_t), s);
+            return set_error(XM_ENOMEM, "%s: work buffers", who);
+        cudaError_t e = cudaMemsetAsync(small, 0, 5 * sizeof(int64_t), s);
+        if (e == cudaSuccess && own_bits)
+            e = cudaMemsetAsync(own_bits, 0, (nwords > 0 ? nwords : 1) * sizeof(uint32_t), s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
-        if (sel_all) {
-            if (R->n_pairs > 0)
-                XM_LAUNCH("k_mark_b", grid_for(R->n_pairs), kBlock, 0, s, k_mark_b, R->b_row,
-                          R->n_pairs, bits);
-        } else if (nA > 0) {
-            XM_LAUNCH("k_mark_b", grid_for(nA), kBlock, 0, s, k_mark_b, R->best_b, nA, bits);
+        if (own_bits) {
+            if (sel_all) {
+                if (R->n_pairs > 0)
+                    XM_LAUNCH("k_mark_b", grid_for(R->n_pairs), kBlock, 0, s, k_mark_b, R->b_row,
+                              R->n_pairs, own_bits);
+            } else if (nA > 0) {
+                XM_LAUNCH("k_mark_b", grid_for(nA), kBlock, 0, s, k_mark_b, R->best_b, nA, own_bits);
+            }
         }
         if (nA > 0)
-            XM_LAUNCH("k_rows_a", grid_for(nA), kBlock, 0, s, k_rows_a, R->count, nA, sel_all,
+            XM_LAUNCH("k_rows_a", grid_cap(nA), kBlock, 0, s, k_rows_a, R->count, nA, sel_all,
                       (int)with_pairs, (int)with_un_a, rows, (unsigned long long*)small + 2);
         int32_t* err = (int32_t*)(small + 4);
         xm_status r = exclusive_scan_i32(rows, row_off, nA, small + 0, err, s);
@@ -371,28 +399,29 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
         // rows are written at device-side offsets into room for the most
         // rows the join can have; the count is read by xm_rows_get
         const int64_t a_side = (with_pairs ? (sel_all ? R->n_pairs : nA) : 0) + (with_un_a ? nA : 0);
-        const int64_t bound = a_side + (with_un_b ? nB : 0);
+        const int64_t bound = a_side + (write_b ? nB : 0);
         int64_t nr = bound > 0 ? bound : 1;
         J->a_row = (int64_t*)dev_alloc(nr * (2 * sizeof(int64_t) + sizeof(double)), s);
-        if (!J->a_row) return set_error(XM_ENOMEM, "xm_join: %lld rows", (long long)bound);
+        if (!J->a_row) return set_error(XM_ENOMEM, "%s: %lld rows", who, (long long)bound);
         J->b_row = J->a_row + nr;
         J->sep = (double*)(J->b_row + nr);
         const int pairs_apart = sel_all && with_pairs && R->n_pairs > 0 && R->a_row;
         if (pairs_apart)
             XM_LAUNCH("k_write_pairs", grid_for(R->n_pairs), kBlock, 0, s, k_write_pairs, R->a_row,
-                      R->b_row, R->sep, R->pair_off, row_off, R->n_pairs, J->a_row, J->b_row,
-                      J->sep);
+                      R->b_row, R->sep, R->pair_off, row_off, R->n_pairs, a_off, J->a_row,
+                      J->b_row, J->sep);
         if (nA > 0 && (with_un_a || !pairs_apart))
             XM_LAUNCH("k_write_a", grid_for(nA), kBlock, 0, s, k_write_a, R->count, R->pair_off,
                       R->b_row, R->sep, R->best_b, R->best_sep, row_off, nA, sel_all,
-                      (int)with_pairs, (int)with_un_a, pairs_apart, J->a_row, J->b_row, J->sep);
-        if (with_un_b && nB > 0)
+                      (int)with_pairs, (int)with_un_a, pairs_apart, a_off, J->a_row, J->b_row,
+                      J->sep);
+        if (write_b && nB > 0)
             XM_LAUNCH("k_write_b", grid_for(nB), kBlock, 0, s, k_write_b, bits, word_off, nB,
                       small + 0, J->a_row, J->b_row, J->sep);
         return XM_OK;
     };
     xm_status st = body();
-    dev_free(bits, s);
+    dev_free(own_bits, s);
     dev_free(rows, s);
     dev_free(row_off, s);
     dev_free(wcount, s);
@@ -403,6 +432,40 @@ extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join
     }
     *out = J;
     return XM_OK;
+}
+
+extern "C" xm_status xm_join(const xm_result* R, int32_t selection, int32_t join_type,
+                             void* stream, xm_rows** out) {
+    return join_impl(R, selection, join_type, nullptr, 0, true, stream, out, "xm_join");
+}
+
+extern "C" xm_status xm_result_mark_b(const xm_result* R, int32_t selection, uint32_t* bits,
+                                      void* stream) {
+    if (!R || !bits) return set_error(XM_EINVAL, "xm_result_mark_b: NULL argument");
+    if (selection != XM_SEL_ALL && selection != XM_SEL_BEST)
+        return set_error(XM_EINVAL, "xm_result_mark_b: selection must be ALL or BEST");
+    if (!(R->selection & selection))
+        return set_error(XM_EINVAL, "xm_result_mark_b: selection not computed by xm_match");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (selection == XM_SEL_ALL) {
+        if (R->n_pairs > 0)
+            XM_LAUNCH("k_mark_b", grid_for(R->n_pairs), kBlock, 0, s, k_mark_b, R->b_row,
+                      R->n_pairs, bits);
+    } else if (R->n_a > 0) {
+        XM_LAUNCH("k_mark_b", grid_for(R->n_a), kBlock, 0, s, k_mark_b, R->best_b, R->n_a, bits);
+    }
+    return XM_OK;
+}
+
+extern "C" xm_status xm_join_shard(const xm_result* R, int32_t selection, int32_t join_type,
+                                   const uint32_t* b_matched, int64_t a_row_offset,
+                                   int32_t with_b_rows, void* stream, xm_rows** out) {
+    if (!b_matched) {
+        if (out) *out = nullptr;
+        return set_error(XM_EINVAL, "xm_join_shard: b_matched is NULL");
+    }
+    return join_impl(R, selection, join_type, b_matched, a_row_offset, with_b_rows != 0, stream,
+                     out, "xm_join_shard");
 }
 
 extern "C" xm_status xm_rows_free(xm_rows* J) {

@@ -61,10 +61,13 @@ struct LvA {
     double a, b, inv_a, inv_b;
 };
 
-__global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, LvA* __restrict__ out) {
+// (count: when the descriptions are by A row, only the rows with members
+// hold one, and only those are read later)
+__global__ void k_lvl_a64(const ACold* __restrict__ acold, int64_t n, const int32_t* count,
+                          LvA* __restrict__ out) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (count && count[i] == 0)) return;
     const ACold C = acold[i];
     LvA L;
     L.lon = C.lon;
@@ -263,7 +266,8 @@ extern "C" xm_status xm_levels_compute(const xm_index* X, const xm_result* R, co
         if (e == cudaSuccess && nw > 0) e = cudaMemsetAsync(L->n_within, 0, nw * sizeof(int32_t), s);
         if (e != cudaSuccess) return cuda_fail(e, "xm_levels_compute: memset");
         if (nA > 0)  // A descriptions are stored by slot; the slots are a permutation of the rows
-            XM_LAUNCH("k_lvl_a64", grid_of(nA), kBlock, 0, s, k_lvl_a64, R->acold, nA, a64);
+            XM_LAUNCH("k_lvl_a64", grid_of(nA), kBlock, 0, s, k_lvl_a64, R->acold, nA,
+                      R->a_slot ? (const int32_t*)nullptr : R->count, a64);
         if (n > 0) {
             const IndexGeom G = X->geom();
             XM_LAUNCH("k_lvl_pair", grid_of(n), kBlock, 0, s, k_lvl_pair, G, a64, R->a_slot,

@@ -33,7 +33,7 @@ int bits_for(int64_t v) {
     return b;
 }
 
-template <int PREC, int MODE>
+template <int PREC, int MODE, bool FUSED = false>
 xm_status launch_scan_t(const char* name, const ScanArgs& a, int64_t n_units, cudaStream_t s) {
     prepare_kernels();
     const int64_t warps = (n_units + 31) / 32;
@@ -44,11 +44,28 @@ xm_status launch_scan_t(const char* name, const ScanArgs& a, int64_t n_units, cu
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (g > 6LL * sms) g = 6LL * sms;
     }
-    XM_LAUNCH(name, (unsigned)g, kScanThreads, kScanSmem, s, (k_scan<PREC, MODE>), a);
+    XM_LAUNCH(name, (unsigned)g, kScanThreads, kScanSmem, s, (k_scan<PREC, MODE, FUSED>), a);
     return XM_OK;
 }
 
+// The scan over A rows in input order that prepares each source itself
+// (a.in): no separate preparation pass, no prepared records in memory.
+xm_status launch_scan_fused(int prec, const ScanArgs& a, int mode, int64_t n_units, cudaStream_t s) {
+    if (n_units <= 0) return XM_OK;
+    if (prec == XM_PREC_FP32_RECHECK) {
+        if (mode == kModeCount)
+            return launch_scan_t<kPrecFP32, kModeCount, true>("k_scan_fp32_count", a, n_units, s);
+        if (mode == kModeEmit)
+            return launch_scan_t<kPrecFP32, kModeEmit, true>("k_scan_fp32_emit", a, n_units, s);
+        return launch_scan_t<kPrecFP32, kModeResolve, true>("k_scan_fp32_resolve", a, n_units, s);
+    }
+    if (mode == kModeCount)
+        return launch_scan_t<kPrecFP64, kModeCount, true>("k_scan_fp64_count", a, n_units, s);
+    return launch_scan_t<kPrecFP64, kModeEmit, true>("k_scan_fp64_emit", a, n_units, s);
+}
+
 xm_status launch_scan_any(int prec, const ScanArgs& a, int mode, int64_t n_units, cudaStream_t s) {
+    if (a.A == nullptr) return launch_scan_fused(prec, a, mode, n_units, s);
     if (n_units <= 0) return XM_OK;
     if (prec == XM_PREC_FP32_RECHECK) {
         if (mode == kModeCount)
@@ -187,8 +204,6 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
         Side* pre = (!Acols->on_device && nA > 0 && !sorted_a) ? side_stream() : nullptr;
         const cudaStream_t ps = pre ? pre->st : s;
         double* a_buf = nullptr;   // A columns on the device (host input)
-        APrep* a_prep = nullptr;   // (side stream only)
-        int32_t* a_err = nullptr;  // (side stream only) preparation's error bits
         auto body = [&]() -> xm_status {
             // A columns on the device
             const double *lon = Acols->lon_deg, *lat = Acols->lat_deg;
@@ -235,26 +250,26 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             const long long arena_cap = want_all ? 12LL * nA + 65536 : 0;
             uint64_t* keys = sorted_a ? T.get<uint64_t>(2 * nn) : nullptr;
             uint32_t* vals = sorted_a ? T.get<uint32_t>(2 * nn) : nullptr;
+            // in input order the scan prepares every source itself (no
+            // prepared records); sorted order prepares them in a pass of
+            // their own, in scan order
             APrep* prep = nullptr;
-            if (pre) {
-                prep = a_prep = (APrep*)dev_alloc(nn * sizeof(APrep), ps);
-                a_err = (int32_t*)dev_alloc(sizeof(int32_t), ps);
-                if (!a_err || cudaMemsetAsync(a_err, 0, sizeof(int32_t), ps) != cudaSuccess)
-                    return set_error(XM_ENOMEM, "xm_match: preparation buffers");
-            } else {
-                prep = T.get<APrep>(nn);
-            }
-            // the float64 part stays with the result (float64 decisions after
-            // the match); in sorted order with the row -> slot map
-            R->acold = (ACold*)dev_alloc(nn * sizeof(ACold), ps);
+            if (sorted_a) prep = T.get<APrep>(nn);
+            // the float64 part stays with the result (float64 decisions on the
+            // pair list after the match); in sorted order with the row -> slot
+            // map, in input order written by the scan for the sources with
+            // members
+            const bool keep_cold = sorted_a || want_all;
+            R->acold = keep_cold ? (ACold*)dev_alloc(nn * sizeof(ACold), ps) : nullptr;
             ACold* cold = R->acold;
             int32_t* lists = T.get<int32_t>(3 * nn);
-            int32_t* small = T.get<int32_t>(8);  // [0] err, [1..3] list counts, [4] chunk queue
+            // [0] err, [1..3] list counts, [4] chunk queue, [6] largest member count
+            int32_t* small = T.get<int32_t>(8);
             int64_t* total = T.get<int64_t>(2);
             unsigned long long* stats = device_stats();
             MemberRec* arena = want_all ? T.get<MemberRec>(arena_cap) : nullptr;
-            if ((sorted_a && (!keys || !vals)) || !prep || !cold || !lists || !small || !total || !stats ||
-                (want_all && !arena))
+            if ((sorted_a && (!keys || !vals || !prep)) || (keep_cold && !cold) || !lists || !small ||
+                !total || !stats || (want_all && !arena))
                 return set_error(XM_ENOMEM, "xm_match: work buffers");
             e = cudaMemsetAsync(small, 0, 8 * sizeof(int32_t), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(total, 0, 2 * sizeof(int64_t), s);
@@ -271,19 +286,19 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                 if (!R->a_slot) return set_error(XM_ENOMEM, "xm_match: slot map");
                 XM_LAUNCH("k_slot_of_row", grid_for(nA), kBlock, 0, s, k_slot_of_row, vals, nA,
                           R->a_slot);
-            } else if (nA > 0) {
-                XM_LAUNCH("k_prep_a", grid_for(nA), kBlock, 0, ps, k_prep_a, I,
-                          (const uint32_t*)nullptr, prep, cold, pre ? a_err : err);
-                if (pre) {  // the scan waits for the preparation
-                    e = cudaEventRecord(pre->join, ps);
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pre->join, 0);
-                    if (e != cudaSuccess) return cuda_fail(e, "xm_match: preparation join");
-                }
+            } else if (pre) {  // the scan waits for the copy of the host columns
+                e = cudaEventRecord(pre->join, ps);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pre->join, 0);
+                if (e != cudaSuccess) return cuda_fail(e, "xm_match: input copy join");
             }
             ScanArgs a{};
             a.G = X->geom();
             a.A = prep;
-            a.Ac = cold;
+            a.Ac = sorted_a ? cold : nullptr;
+            a.in = I;
+            // the float64 part of the sources with members stays with the
+            // result (only the all-pairs selection's later uses read it)
+            a.acold_out = sorted_a ? nullptr : cold;
             a.nA = nA;
             a.shape = region->shape;
             a.want_best = (sel & XM_SEL_BEST) != 0;
@@ -300,7 +315,11 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             a.stats = stats;
             a.err = err;
             // the count pass runs persistent warps that take 32-source chunks
-            // from a queue, so chunks of large regions do not leave a tail
+            // from a queue, so chunks of large regions do not leave a tail; it
+            // also keeps the largest member count (the segment sorts below skip
+            // the size classes no row reaches)
+            int32_t* max_count = small + 6;
+            a.max_count = max_count;
             ScanArgs cq = a;
             cq.queue = (unsigned int*)(small + 4);
             xm_status r = launch_scan_any(prec, cq, kModeCount, nA, s);
@@ -326,15 +345,17 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
                     xm_status rr = launch_scan_any(prec, b, kModeEmit, n_ovf, s);
                     if (rr != XM_OK) return rr;
                 }
-                XM_LAUNCH("k_sort_small", grid_for(nA), kBlock, 0, s, k_sort_small, R->count,
-                          R->pair_off, nA, (long long)np, R->b_row, R->sep);
+                const unsigned gsm = grid_for(nA) < 8u * 152u ? grid_for(nA) : 8u * 152u;
+                XM_LAUNCH("k_sort_small", gsm, kBlock, 0, s, k_sort_small, R->count,
+                          R->pair_off, nA, (long long)np, R->b_row, R->sep, max_count);
                 const int64_t gw = (nA + 32 * kWarpSortWarps - 1) / (32 * kWarpSortWarps);
                 XM_LAUNCH("k_sort_warp", (unsigned)(gw < 8 * 152 ? gw : 8 * 152),
                           32 * kWarpSortWarps, 0, s, k_sort_warp, R->count, R->pair_off, nA,
-                          (long long)np, R->b_row, R->sep);
+                          (long long)np, R->b_row, R->sep, max_count);
                 const int64_t gs = (nA + 255) / 256;
                 XM_LAUNCH("k_seg_sort", (unsigned)(gs < 2 * 152 ? gs : 2 * 152), 256, 0, s,
-                          k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep);
+                          k_seg_sort, R->count, R->pair_off, nA, (long long)np, R->b_row, R->sep,
+                          max_count);
                 return XM_OK;
             };
             auto alloc_pairs = [&](int64_t np) -> bool {
@@ -353,8 +374,6 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             e = rd.add(h_small, small, sizeof(h_small));
             if (e == cudaSuccess) e = rd.add(h_total, total, sizeof(h_total));
             if (e == cudaSuccess && X->build_err) e = rd.add(&h_berr, X->build_err, sizeof(int32_t));
-            int32_t h_aerr = 0;
-            if (e == cudaSuccess && a_err) e = rd.add(&h_aerr, a_err, sizeof(int32_t));
             if (e == cudaSuccess) e = rd.mark();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match count reads");
             Side* side = ((sel & XM_SEL_BEST) && prec == XM_PREC_FP32_RECHECK) ? side_stream() : nullptr;
@@ -377,7 +396,6 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             e = rd.sync();
             if (e != cudaSuccess) return cuda_fail(e, "xm_match sync");
             if (h_berr) return index_build_status(h_berr);
-            h_small[0] |= h_aerr;
             if (h_small[0] & kErrCoord) return set_error(XM_EINVAL, "A: NaN/inf or |lat| > 90");
             if (h_small[0] & kErrSize)
                 return set_error(XM_EINVAL, "A: negative or non-finite region size or angle");
@@ -444,8 +462,6 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             else cudaGetLastError();
         }
         dev_free(a_buf, s);
-        dev_free(a_prep, s);
-        dev_free(a_err, s);
         if (st != XM_OK && pre) cudaStreamSynchronize(ps);  // (before the result is freed)
     }
     if (st != XM_OK) {

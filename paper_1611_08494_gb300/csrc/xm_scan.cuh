@@ -193,6 +193,30 @@ __device__ __forceinline__ void make_aprep(double lon, double lat, double gamma,
     *C_out = C;
 }
 
+// The prepared form of A row i from the caller's columns, its position
+// (lon0, lat0) already read. Invalid positions and sizes set the error bits
+// when err is given.
+__device__ __forceinline__ void prep_at(const AIn& I, int64_t i, double lon0, double lat0,
+                                        int32_t* err, APrep* P, ACold* C) {
+    double lon, lat, gamma;
+    bool ok;
+    a_position_of(lon0, lat0, I.rotate, I.rot, &lon, &lat, &gamma, &ok);
+    const double a = I.a_col ? I.a_col[i] : I.a;
+    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
+    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    if (err) {
+        if (!ok) atomicOr(err, kErrCoord);
+        if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
+    }
+    make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero, I.nz, I.h_f,
+               (int32_t)i, P, C);
+}
+
+__device__ __forceinline__ void prep_one(const AIn& I, int64_t i, int32_t* err, APrep* P,
+                                         ACold* C) {
+    prep_at(I, i, I.lon[i], I.lat[i], err, P, C);
+}
+
 // Prepared sources in scan order: vals[s] is the A row of position s (the
 // sorted order), or NULL for input order. Invalid positions and sizes set
 // the error bits (the sorted path found them already; setting them twice is
@@ -203,16 +227,11 @@ __global__ void k_prep_a(AIn I, const uint32_t* __restrict__ vals, APrep* __rest
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= I.n) return;
     const int64_t i = vals ? (int64_t)vals[s] : s;
-    double lon, lat, gamma;
-    bool ok;
-    a_position(I, i, &lon, &lat, &gamma, &ok);
-    const double a = I.a_col ? I.a_col[i] : I.a;
-    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
-    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
-    if (!ok) atomicOr(err, kErrCoord);
-    if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
-    make_aprep(lon, lat, gamma, ok, a, b, pa, I.shape, I.pa_dir, I.size_k, I.pa_zero, I.nz, I.h_f,
-               (int32_t)i, &out[s], &cold[s]);
+    APrep P;
+    ACold C;
+    prep_one(I, i, err, &P, &C);
+    out[s] = P;
+    cold[s] = C;
 }
 
 // One member found by the count pass: A row, its index among that row's
@@ -227,6 +246,10 @@ struct ScanArgs {
     IndexGeom G;
     const APrep* A;
     const ACold* Ac;  // float64 part of A, same order
+    // fused preparation (input order): the caller's columns, prepared by the
+    // scan itself, and where the float64 part of sources with members goes
+    AIn in;
+    ACold* acold_out;
     int64_t nA;
     int32_t shape;
     int32_t want_best;
@@ -245,6 +268,7 @@ struct ScanArgs {
     int32_t* tie_list;  // sources whose best pair is decided in float64
     int32_t* big_list;  // rows with more than kSegMax members
     int32_t* list_n;    // [0] overflow, [1] ties, [2] big
+    int32_t* max_count;  // (nullable) largest member count of any source
     // emit mode
     const int64_t* pair_off;
     int64_t* out_a;
@@ -430,10 +454,16 @@ constexpr int kScanThreads = 32 * kScanWarps;
 constexpr int kItemCap = 32;
 constexpr long long kKeyInf = 0x7FF0000000000000LL;  // above every finite key of either kind
 
+union ASlot {
+    A64 a64;
+    ACold cold;
+};
+
 struct ScanWarpSmem {
     APrep A[32];
     int32_t sidx[32];          // index of each source in P.A / P.Ac
-    A64 a64[32];               // float64 basis of sources on float64 separations
+    ASlot ac[32];              // float64 basis of sources on float64 separations; with a
+                               // fused preparation, the float64 part of the others
     long long m1[32], m2[32];  // best key, second key
     long long r1[32];          // reported separation of the best (bits)
     int32_t b1[32];
@@ -452,7 +482,11 @@ struct ScanWarpSmem {
     ItemTerms it_t[kItemCap];
 };
 
-template <int PREC, int MODE>
+// FUSED: the sources are the caller's A rows in input order (P.in), and the
+// scan prepares each one itself instead of reading a prepared record; the
+// count pass then also stores the float64 part of every source with members
+// (P.acold_out), which later float64 decisions on the result read.
+template <int PREC, int MODE, bool FUSED = false>
 __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char scan_smem[];
@@ -463,6 +497,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
     const uint32_t lt_mask = (1u << lane) - 1u;
     A64 a_own;  // float64 basis for band rechecks of float32-path sources
     int a_own_for = -1;
+    int max_cnt = 0;  // (count mode) the largest member count of this lane's sources
     uint32_t n_cand = 0, n_re = 0, n_flip = 0, n_mem = 0;
     int64_t chunk = (int64_t)blockIdx.x * kScanWarps + warp;
     // persistent mode: warps take 32-source chunks from the queue until it
@@ -483,7 +518,10 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
     int n_items = 0;
     if (lane < nloc) {
         s_me = P.list ? P.list[first + lane] : first + lane;
-        const APrep A = P.A[s_me];
+        APrep A;
+        ACold C;
+        if (FUSED) prep_one(P.in, s_me, MODE == kModeCount ? P.err : nullptr, &A, &C);
+        else A = P.A[s_me];
         W.A[lane] = A;
         W.sidx[lane] = (int32_t)s_me;
         // float32 error bounds: g (from the preparation) bounds |q32 - q|;
@@ -494,7 +532,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
         const bool s64 = PREC == kPrecFP64 || MODE == kModeResolve ||
                          W.esep[lane] * 206264.8f > 9e-5f;
         W.sep64[lane] = s64;
-        if (s64 && A.R > 0.0f) W.a64[lane] = make_a64(P.Ac[s_me]);
+        if (s64 && A.R > 0.0f) W.ac[lane].a64 = make_a64(FUSED ? C : P.Ac[s_me]);
+        else if (FUSED) W.ac[lane].cold = C;
         W.m1[lane] = kKeyInf;
         W.m2[lane] = kKeyInf;
         W.r1[lane] = 0;
@@ -629,10 +668,10 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
                 }
                 double exact = 0.0;
                 if (maybe && need64) {
-                    const A64* a64 = &W.a64[al];
+                    const A64* a64 = &W.ac[al].a64;
                     if (!s64) {  // band recheck of a float32-path source
                         if (a_own_for != al) {
-                            a_own = make_a64(P.Ac[W.sidx[al]]);
+                            a_own = make_a64(FUSED ? W.ac[al].cold : P.Ac[W.sidx[al]]);
                             a_own_for = al;
                         }
                         a64 = &a_own;
@@ -758,6 +797,15 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
                                          : (double)__int_as_float((int)W.r1[lane]) * kRadToArcsec;
         if (MODE == kModeCount) {
             P.count[A.row] = cnt;
+            max_cnt = max(max_cnt, cnt);
+            if (FUSED && P.acold_out && cnt > 0) {
+                ACold C = W.ac[lane].cold;
+                if (W.sep64[lane]) {  // (its slot holds the float64 basis)
+                    APrep Q;
+                    prep_one(P.in, s_me, nullptr, &Q, &C);
+                }
+                P.acold_out[A.row] = C;
+            }
             if (P.want_best) {
                 P.best_b[A.row] = cnt ? (int64_t)W.b1[lane] : -1;
                 P.best_sep[A.row] = best_sep;
@@ -788,6 +836,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
         warp_add(&P.stats[1], n_re);
         warp_add(&P.stats[2], n_flip);
         warp_add(&P.stats[3], n_mem);
+        const int wm = __reduce_max_sync(0xffffffffu, max_cnt);
+        if (P.max_count && lane == 0 && wm > 0) atomicMax(P.max_count, wm);
     }
 }
 
@@ -824,8 +874,10 @@ __global__ void __launch_bounds__(256) k_sort_small(const int32_t* __restrict__ 
                                                     const int64_t* __restrict__ pair_off,
                                                     int64_t nA, long long out_cap,
                                                     int64_t* __restrict__ out_b,
-                                                    double* __restrict__ out_sep) {
+                                                    double* __restrict__ out_sep,
+                                                    const int32_t* max_count) {
     pdl_wait();
+    if (max_count && *max_count < 2) return;  // no row to sort
     static_assert(kSmallSort == 16, "one row per half-warp");
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -870,8 +922,10 @@ constexpr int kWarpSortWarps = 4;
 
 __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
     const int32_t* __restrict__ count, const int64_t* __restrict__ pair_off, int64_t nA,
-    long long out_cap, int64_t* __restrict__ out_b, double* __restrict__ out_sep) {
+    long long out_cap, int64_t* __restrict__ out_b, double* __restrict__ out_sep,
+    const int32_t* max_count) {
     pdl_wait();
+    if (max_count && *max_count <= kSmallSort) return;  // no row of this size class
     __shared__ int64_t sb[kWarpSortWarps][kWarpSort];
     __shared__ double ss[kWarpSortWarps][kWarpSort];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -912,8 +966,10 @@ __global__ void __launch_bounds__(32 * kWarpSortWarps) k_sort_warp(
 __global__ void __launch_bounds__(256) k_seg_sort(const int32_t* __restrict__ count,
                                                   const int64_t* __restrict__ pair_off, int64_t nA,
                                                   long long out_cap, int64_t* __restrict__ out_b,
-                                                  double* __restrict__ out_sep) {
+                                                  double* __restrict__ out_sep,
+                                                  const int32_t* max_count) {
     pdl_wait();
+    if (max_count && *max_count <= kWarpSort) return;  // no row of this size class
     __shared__ int64_t kb[kSegMax];
     __shared__ double ks[kSegMax];
     __shared__ int32_t found[256];
@@ -1006,6 +1062,11 @@ void prepare_kernels() {
     cudaFuncSetAttribute(k_scan<kPrecFP32, kModeResolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_scan<kPrecFP64, kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_scan<kPrecFP64, kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeCount, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeEmit, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP32, kModeResolve, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeCount, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan<kPrecFP64, kModeEmit, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     radix_sort_prepare();
     done[dev] = true;
 }

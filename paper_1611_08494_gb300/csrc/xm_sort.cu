@@ -31,7 +31,7 @@ constexpr int kRadix = 256;
 // The virtual key of an index key under a plan.
 __device__ __forceinline__ uint64_t plan_key(const SortPlan& P, uint64_t key) {
     const uint32_t z = (uint32_t)(key >> 32);
-    const uint32_t ra = (uint32_t)key >> kSortBeginBit;
+    const uint32_t ra = (uint32_t)key >> kIndexSortBeginBit;
     const uint32_t rmask = P.rb >= 32 ? 0xFFFFFFFFu : ((1u << P.rb) - 1u);
     return ((uint64_t)(z - P.zmin) << P.rb) | (ra & rmask);
 }

@@ -106,6 +106,8 @@ xm_match = _sig("xm_match", _i32, _p, ctypes.POINTER(Columns), ctypes.POINTER(Re
 xm_result_free = _sig("xm_result_free", _i32, _p)
 xm_result_get = _sig("xm_result_get", _i32, _p, ctypes.POINTER(ResultView))
 xm_join = _sig("xm_join", _i32, _p, _i32, _i32, _p, ctypes.POINTER(_p))
+xm_result_mark_b = _sig("xm_result_mark_b", _i32, _p, _i32, _p, _p)
+xm_join_shard = _sig("xm_join_shard", _i32, _p, _i32, _i32, _p, _i64, _i32, _p, ctypes.POINTER(_p))
 xm_rows_free = _sig("xm_rows_free", _i32, _p)
 xm_rows_get = _sig("xm_rows_get", _i32, _p, ctypes.POINTER(RowsView))
 xm_copy_to_host = _sig("xm_copy_to_host", _i32, _p, _p, ctypes.c_size_t, _p)
@@ -314,6 +316,35 @@ class Result:
 
     def join(self, join_type: str, selection=SEL_ALL, stream=None) -> "Rows":
         return Rows(self, join_type, selection, stream)
+
+    def mark_b(self, bits, selection=SEL_ALL, stream=None) -> None:
+        """ORs the B rows of the selected pairs into ``bits`` (a device int32
+        tensor of (n_b + 31) // 32 words). ``xm_result_mark_b``."""
+        if not (bits.is_cuda and bits.dtype == torch.int32 and bits.is_contiguous()
+                and bits.numel() >= (self.n_b + 31) // 32):
+            raise ValueError("bits must be a contiguous device int32 tensor of (n_b + 31) // 32 words")
+        check(xm_result_mark_b(self.handle, int(selection), bits.data_ptr(), _stream_handle(stream)),
+              "xm_result_mark_b")
+
+    def join_shard(self, join_type: str, b_matched, a_row_offset: int, with_b_rows: bool,
+                   selection=SEL_ALL, stream=None) -> "Rows":
+        """The join rows of this result as one slice of catalogue 1: unmatched
+        B rows decided by ``b_matched`` (the OR of every slice's
+        ``mark_b``), A rows shifted by ``a_row_offset``, B-only rows written
+        only with ``with_b_rows``. ``xm_join_shard``."""
+        if not (b_matched.is_cuda and b_matched.dtype == torch.int32 and b_matched.is_contiguous()
+                and b_matched.numel() >= (self.n_b + 31) // 32):
+            raise ValueError("b_matched must be a contiguous device int32 tensor of (n_b + 31) // 32 words")
+        h = _p()
+        check(xm_join_shard(self.handle, int(selection), JOINS[join_type], b_matched.data_ptr(),
+                            int(a_row_offset), int(bool(with_b_rows)), _stream_handle(stream),
+                            ctypes.byref(h)), "xm_join_shard")
+        rows = Rows.__new__(Rows)
+        rows.handle = h.value
+        rows.result = self
+        rows._keep = b_matched
+        rows._view = None
+        return rows
 
     def levels(self, scales=(), stream=None) -> "Levels":
         """Normalised distance of every pair, the best pair per A source by
