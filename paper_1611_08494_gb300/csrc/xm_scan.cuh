@@ -301,10 +301,11 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
     W.z1 = min(z1, G.nz - 1);
     int64_t dk = 0;
     if (!full) {
-        // half-width of the RA window: asin(sin R / cos dec), widened
+        // half-width of the RA window: asin(sin R / cos dec), bounded by
+        // asin(R / cos dec) and widened
         const ZoneHot Z = load_zone_hot(G.zhot + A.z);
         const LatTerms L = lat_terms(G.h_f * A.zfrac, Z.sin_cf, Z.cos_cf);
-        const float ratio = sinf(Rm) / L.cd;
+        const float ratio = Rm / L.cd;  // (sin Rm <= Rm: a window no narrower)
         if (!(L.cd > 0.0f && ratio < 0.9999f)) full = true;
         else dk = (int64_t)(int32_t)ceilf(asinf(ratio) * (1.0f + 2e-5f) * kKey32PerRadF) + 2;  // < 2^30
     }
@@ -340,6 +341,8 @@ __device__ __forceinline__ Window a_window(const APrep& A, const IndexGeom& G) {
 // window touches (about one source per bucket), from two table reads and no
 // search; the candidates' own keys are compared with the window as they are
 // read. Keys outside the zone's key range clamp to its first or last bucket.
+// (Searching the bounds inside the buckets cut the rows read but measured
+// slower: its dependent loads cost more than the extra candidate rounds.)
 __device__ __forceinline__ void bucket_bounds(const IndexGeom& G, const ZoneHot& Z, uint32_t klo,
                                               uint32_t khi, int64_t* lo_out, int64_t* hi_out) {
     const int64_t start = Z.start;
@@ -459,8 +462,85 @@ union ASlot {
     ACold cold;
 };
 
+// The prepared sources of a chunk and the terms of its items, laid out by
+// field: lanes reading the fields of different sources or items hit
+// different banks (a record per source or item, 48 or 40 bytes apart,
+// would put several of them in one bank).
+struct ASoA {
+    uint64_t key64[32];
+    int32_t z[32], row[32], shape[32];
+    float zfrac[32], R[32], g[32];
+    float m00[32], m01[32], m10[32], m11[32];
+};
+
+__device__ __forceinline__ void put_a(ASoA& S, int l, const APrep& A) {
+    S.key64[l] = A.key64;
+    S.z[l] = A.z;
+    S.row[l] = A.row;
+    S.shape[l] = A.shape;
+    S.zfrac[l] = A.zfrac;
+    S.R[l] = A.R;
+    S.g[l] = A.g;
+    S.m00[l] = A.m00;
+    S.m01[l] = A.m01;
+    S.m10[l] = A.m10;
+    S.m11[l] = A.m11;
+}
+
+__device__ __forceinline__ APrep get_a(const ASoA& S, int l) {
+    APrep A;
+    A.key64 = S.key64[l];
+    A.z = S.z[l];
+    A.row = S.row[l];
+    A.shape = S.shape[l];
+    A.zfrac = S.zfrac[l];
+    A.R = S.R[l];
+    A.g = S.g[l];
+    A.m00 = S.m00[l];
+    A.m01 = S.m01[l];
+    A.m10 = S.m10[l];
+    A.m11 = S.m11[l];
+    return A;
+}
+
+template <int N>
+struct TSoA {
+    float sdd[N], hav_d[N], cd[N], sd[N], sinc[N], cosc[N], binw[N], ufrac[N];
+    uint32_t binA[N], nbins[N];
+};
+
+template <int N>
+__device__ __forceinline__ void put_t(TSoA<N>& S, int k, const ItemTerms& T) {
+    S.sdd[k] = T.sdd;
+    S.hav_d[k] = T.hav_d;
+    S.cd[k] = T.cd;
+    S.sd[k] = T.sd;
+    S.sinc[k] = T.sinc;
+    S.cosc[k] = T.cosc;
+    S.binw[k] = T.binw;
+    S.ufrac[k] = T.ufrac;
+    S.binA[k] = T.binA;
+    S.nbins[k] = T.nbins;
+}
+
+template <int N>
+__device__ __forceinline__ ItemTerms get_t(const TSoA<N>& S, int k) {
+    ItemTerms T;
+    T.sdd = S.sdd[k];
+    T.hav_d = S.hav_d[k];
+    T.cd = S.cd[k];
+    T.sd = S.sd[k];
+    T.sinc = S.sinc[k];
+    T.cosc = S.cosc[k];
+    T.binw = S.binw[k];
+    T.ufrac = S.ufrac[k];
+    T.binA = S.binA[k];
+    T.nbins = S.nbins[k];
+    return T;
+}
+
 struct ScanWarpSmem {
-    APrep A[32];
+    ASoA A;
     int32_t sidx[32];          // index of each source in P.A / P.Ac
     ASlot ac[32];              // float64 basis of sources on float64 separations; with a
                                // fused preparation, the float64 part of the others
@@ -479,7 +559,7 @@ struct ScanWarpSmem {
     uint32_t it_klo[kItemCap], it_khi[kItemCap];  // the item's key window
     int64_t it_lo[kItemCap];
     int32_t it_start[kItemCap + 1];  // first candidate of each item
-    ItemTerms it_t[kItemCap];
+    TSoA<kItemCap> it_t;
 };
 
 // FUSED: the sources are the caller's A rows in input order (P.in), and the
@@ -522,7 +602,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
         ACold C;
         if (FUSED) prep_one(P.in, s_me, MODE == kModeCount ? P.err : nullptr, &A, &C);
         else A = P.A[s_me];
-        W.A[lane] = A;
+        put_a(W.A, lane, A);
         W.sidx[lane] = (int32_t)s_me;
         // float32 error bounds: g (from the preparation) bounds |q32 - q|;
         // esep bounds the float32 separation error (rad)
@@ -578,7 +658,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
                 if (al + step < nloc && W.ipref[al + step] <= t) al += step;
             const int r = t - W.ipref[al];
             const int ns = W.nseg[al];
-            const int z = W.z0[al] + r / ns, sg = r % ns;
+            const int z = W.z0[al] + (ns == 2 ? r >> 1 : r), sg = ns == 2 ? r & 1 : 0;
             const ZoneHot Z = load_zone_hot(G.zhot + z);
             const uint32_t klo = W.wlo[al][sg], khi = W.whi[al][sg];
             int64_t lo, hi;
@@ -588,7 +668,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
             W.it_khi[k] = khi;
             W.it_lo[k] = lo;
             W.it_start[k] = (int32_t)(hi - lo);  // count, scanned below
-            if (PREC == kPrecFP32 && hi > lo) W.it_t[k] = item_terms(W.A[al], Z, z, G.h_f);
+            if (PREC == kPrecFP32 && hi > lo) put_t(W.it_t, k, item_terms(get_a(W.A, al), Z, z, G.h_f));
         }
         __syncwarp();
         // exclusive scan of item candidate counts (nb <= 64: 2 per lane)
@@ -623,7 +703,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
         // ---- candidates, 32 per round. The records of the next round are
         // loaded before this round is tested, so consecutive rounds' loads
         // overlap the tests. A lane's record belongs to its item's bucket
-        // range; it is a candidate when its key lies in the item's window.
+        // range; it is a candidate when its own key lies in the item's window.
         int kp = 0;  // item of the prefetched candidate; only moves forward
         int nxt_k = 0;
         BRec nxt;
@@ -646,7 +726,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
             int32_t brow = 0x7fffffff;
             bool rep32 = false;
             if (active && b.ra_key >= W.it_klo[k] && b.ra_key <= W.it_khi[k]) {
-                const APrep& A = W.A[al];
+                const APrep A = get_a(W.A, al);
                 brow = b.row;
                 n_cand++;
                 const bool s64 = W.sep64[al];
@@ -655,7 +735,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
                 bool maybe = true, band = false, in32 = false;
                 if (PREC == kPrecFP32) {
                     // q <= 1 - g: inside; q > 1 + g: outside; between: float64
-                    const float q = q32(A, A.shape, W.it_t[k], b, &x, &y);
+                    const float q = q32(A, A.shape, get_t(W.it_t, k), b, &x, &y);
                     const float g = W.g[al];
                     maybe = q <= 1.0f + g;
                     if (maybe) {
@@ -743,13 +823,13 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
             __syncwarp();
             if (is_mem) {
                 const int idx = base + rank;
-                const APrep& A = W.A[al];
+                const int32_t a_row = W.A.row[al];
                 if (MODE == kModeCount) {
                     if (P.arena) {
                         const long long slot = abase + __popc(mem_mask & lt_mask);
                         if (slot < P.arena_cap) {
                             MemberRec r;
-                            r.a_row = A.row;
+                            r.a_row = a_row;
                             r.k = idx;
                             r.b_row = brow;
                             r.f32 = rep32;
@@ -760,9 +840,9 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
                         }
                     }
                 } else if (MODE == kModeEmit) {
-                    if (idx < W.cap[al] && P.pair_off[A.row] + idx < P.out_cap) {
-                        const int64_t o = P.pair_off[A.row] + idx;
-                        P.out_a[o] = P.lrow ? P.lrow[A.row] : A.row;
+                    if (idx < W.cap[al] && P.pair_off[a_row] + idx < P.out_cap) {
+                        const int64_t o = P.pair_off[a_row] + idx;
+                        P.out_a[o] = P.lrow ? P.lrow[a_row] : a_row;
                         P.out_b[o] = brow;
                         P.out_sep[o] = rep32 ? (double)__int_as_float((int)rep) * kRadToArcsec
                                              : __longlong_as_double(rep);
@@ -789,7 +869,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
 
     // ---- per-source results (lane = source)
     if (lane < nloc) {
-        const APrep& A = W.A[lane];
+        const APrep A = get_a(W.A, lane);
         const int cnt = W.cnt[lane];
         const bool s64 = W.sep64[lane] && MODE != kModeResolve;
         const double best_sep = cnt == 0 ? NAN
