@@ -521,51 +521,81 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
         del res, rows
     v_ser = n_a * n_ser / (sum(ms_ser) / 1e3)
 
-    # pipelined as a throughput-bound user would run it: steps go to two
-    # streams in turn, and each step's index build (with its input copy) is
-    # issued before the previous step's match, whose pair count holds the
-    # host; so one step's input copy and build overlap the previous step's
-    # match, and its result copy the next step's work (each step still copies
-    # all of its inputs in and its result out; the clock covers the whole run)
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    keep = [None, None]
+    # pipelined as a throughput-bound user would run it, through the same
+    # calls with host buffers: step k's index build (which copies B in) runs
+    # on stream k % 3 and is issued two steps ahead, its match and join (the
+    # match copies A in and holds the host at its pair count) follow there,
+    # and its result copy goes to a fourth stream, so B copies in, compute and
+    # results out of neighbouring steps overlap. A step's objects live until
+    # its copy out has run (their memory is freed in their stream's order
+    # after a wait on it). Every step still copies all of its inputs in and
+    # its result out; the clock covers the whole run.
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    out_stream = torch.cuda.Stream()
+    keep = {}
+    out_bufs = {}
 
     def build(k):
-        with torch.cuda.stream(streams[k % 2]):
-            flush.zero_()
+        with torch.cuda.stream(streams[k % 3]):
             return xm.Index(host["b_lon"], host["b_lat"], frame=d["b_frame"], ids=host["b_id"],
                             zone_height_arcsec=zone_h, deferred_check=True)
 
     def finish(k, idx):
-        with torch.cuda.stream(streams[k % 2]):
-            keep[k % 2] = step(xm.PREC_FP32, False, host, True, out_slot=k % 2, idx=idx)
+        st = streams[k % 3]
+        with torch.cuda.stream(st):
+            res = xm.Result(idx, host["a_lon"], host["a_lat"], frame=d["a_frame"],
+                            precision=xm.PREC_FP32, selection=xm.SEL_ALL | xm.SEL_BEST,
+                            **d["region"])
+            rows = res.join("or")
+            srcs = [rows.a_row, rows.b_row, rows.sep, res.best_b, res.best_sep]
+            done = torch.cuda.Event()
+            done.record(st)
+        out_stream.wait_event(done)
+        slot = k % 3
+        key = tuple(t.numel() for t in srcs)
+        if out_bufs.get(slot, (None,))[0] != key:
+            out_bufs[slot] = (key, [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in srcs])
+        with torch.cuda.stream(out_stream):
+            for dst, src in zip(out_bufs[slot][1], srcs):
+                dst.copy_(src, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(out_stream)
+        keep[k] = (idx, res, rows, srcs, copied, st)
+        old = keep.pop(k - 2, None)
+        if old is not None:  # its memory is released on its stream after its copy out
+            old[5].wait_event(old[4])
+            del old
 
     def run(n):
-        nxt = build(0)
+        ahead = {0: build(0), 1: build(1) if n > 1 else None}
         for k in range(n):
-            idx, nxt = nxt, (build(k + 1) if k + 1 < n else None)
-            finish(k, idx)
+            if k + 2 < n:
+                ahead[k + 2] = build(k + 2)
+            finish(k, ahead.pop(k))
+        for k in sorted(keep):
+            keep[k][5].wait_event(keep[k][4])
+        keep.clear()
 
-    run(2)
+    run(3)
     torch.cuda.synchronize()
-    n_pipe = max(3, args.steps // 4)
+    n_pipe = max(4, args.steps // 4)
     cur = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
-    for st in streams:
+    for st in streams + [out_stream]:
         st.wait_event(e0)
     run(n_pipe)
-    for st in streams:
+    for st in streams + [out_stream]:
         cur.wait_stream(st)
     e1.record(cur)
     e1.synchronize()
-    keep[0] = keep[1] = None
     ms_pipe = e0.elapsed_time(e1)
     del host
     return {"value": n_a * n_pipe / (ms_pipe / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
-            "mode": "two streams in turn, each step's index build (and input copy) issued before "
-                    "the previous step's match: copies overlap the neighbouring steps' work",
+            "mode": "steps on three streams, each step's index build (and B copy in) issued two "
+                    "steps ahead, result copies out on a fourth stream: copies in, compute and "
+                    "copies out of neighbouring steps overlap",
             "serial_value": v_ser, "serial_mode": "one step at a time, events around each step"}
 
 

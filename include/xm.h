@@ -259,6 +259,10 @@ XM_API xm_status xm_result_get(const xm_result* result, xm_result_view* view);
  * XM_ECUDA; XM_ETIMEOUT from xm_rows_get. */
 XM_API xm_status xm_join(const xm_result* result, int32_t selection, int32_t join_type,
                          void* stream, xm_rows** out);
+/* Frees the rows' device arrays in the order of the stream they were written
+ * on (work queued there that reads them runs first; to read them on another
+ * stream, make the rows' stream wait for that work before freeing); that
+ * stream must still exist. */
 XM_API xm_status xm_rows_free(xm_rows* rows);
 
 typedef struct {

@@ -298,10 +298,12 @@ extern "C" xm_status xm_join_noalloc(const xm_result* R, int32_t selection, int3
 
 using namespace xm;
 
+// The rows' memory returns to the pool in the order of the stream they were
+// written on, after whatever the caller queued there to read them.
 static void free_rows(xm_rows* J) {
     if (!J) return;
-    dev_free(J->a_row, J->pending ? J->stream : nullptr);
-    dev_free(J->pending, J->pending ? J->stream : nullptr);
+    dev_free(J->a_row, J->stream);
+    dev_free(J->pending, J->stream);
     delete J;
 }
 

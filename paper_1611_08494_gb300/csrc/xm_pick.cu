@@ -161,6 +161,7 @@ extern "C" xm_status xm_pick_pairs(const xm_index* X, const xm_result* R, int32_
     const int64_t n = R->n_pairs, nB = R->n_b;
     xm_rows* J = new (std::nothrow) xm_rows();
     if (!J) return set_error(XM_ENOMEM, "xm_pick_pairs: host allocation");
+    J->stream = s;
     const int64_t nb1 = nB > 0 ? nB : 1, n1 = n > 0 ? n : 1;
     // per B: min reported sep, contenders, lowest contender, exact min, lowest exact
     unsigned long long* w = (unsigned long long*)dev_alloc(4 * nb1 * sizeof(unsigned long long), s);
