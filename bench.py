@@ -73,6 +73,7 @@ def parse():
     p.add_argument("--serve-b", type=int, default=300_000_000, help="resident B sources")
     p.add_argument("--serve-pool", type=int, default=256, help="distinct request payloads")
     p.add_argument("--serve-slots", type=int, default=3)
+    p.add_argument("--c1-leg", type=int, default=1, help="0 skips the small C1 leg")
     p.add_argument("--c2-leg", type=int, default=1, help="0 skips the C2 ellipse leg")
     p.add_argument("--c4-requests", type=int, default=4096, help="0 skips the batched C4 leg")
     p.add_argument("--c4-b", type=int, default=100_000_000, help="resident B of the C4 leg")
@@ -477,10 +478,12 @@ def run_ours(args):
                   "fp64_fma_tflops": measured["fp64_fma_tflops"],
                   "measured_by": "xm_measure_peak on this GPU, best of 5 launches"},
     }
+    if world == 1 and args.c1_leg:
+        line["c1"] = c1_leg(args, xm, torch)
     if world == 1 and args.c2_leg:
         line["c2"] = c2_leg(args, xm, torch, measured)
     if world == 1 and args.c4_requests > 0:
-        line["c4"] = c4_leg(args, xm, torch)
+        line["c4"] = c4_leg(args, xm, torch, measured)
     if world == 1 and args.values_scale > 0:
         line["exact_value"] = values_leg(args, xm, torch)
     if world == 1 and args.serve_seconds > 0:
@@ -636,6 +639,108 @@ def pick_leg(xm, torch, step, stream):
 
 # --------------------------------------------------------- C2 ellipse leg
 
+def c1_leg(args, xm, torch):
+    """The plain circle cross-match (A = B = 1e4 in a 1 x 1 deg box, r = 1
+    arcsec, float64 throughout): a latency-bound case whose step is a dozen
+    small launches. The step (build + match all and best + join "1 or 2")
+    from device-resident columns, the same from pinned host columns with the
+    join rows copied back (the whole call as a user makes it), and the oracle
+    on the whole workload on the host cores."""
+    from paper_1611_08494_gb300 import synth
+
+    d = synth.c1()
+    n_a = d["a_lon"].size
+    host = {k: torch.as_tensor(d[k]).pin_memory() for k in ("a_lon", "a_lat", "b_lon", "b_lat")}
+    dev = {k: v.cuda() for k, v in host.items()}
+    stream = torch.cuda.current_stream()
+
+    def step(cols, copy_out):
+        idx = xm.Index(cols["b_lon"], cols["b_lat"], frame=d["b_frame"], build_fp64=True)
+        res = xm.Result(idx, cols["a_lon"], cols["a_lat"], frame=d["a_frame"],
+                        precision=xm.PREC_FP64, selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
+        rows = res.join("or")
+        if copy_out:
+            return [t.to("cpu", non_blocking=True) for t in (rows.a_row, rows.b_row, rows.sep,
+                                                               res.best_b, res.best_sep)]
+        return rows
+
+    def timed(cols, copy_out, n):
+        for _ in range(5):
+            step(cols, copy_out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(cols, copy_out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    xm.reset_stats()
+    ms_dev = timed(dev, False, 200)
+    launches = xm.stats()["kernel_launches"] / 205
+    ms_e2e = timed(host, True, 200)
+    smp = dict(d, desc=f"the whole workload ({n_a} A x {d['b_lon'].size} B)")
+    out = {"workload": "c1 plain circle cross-match: A=10000, B=10000 (70% offset copies, "
+                       "sigma 0.3 arcsec), RA 150-151 Dec 2-3, r=1 arcsec, float64 throughout",
+           "ms_per_step": ms_dev, "a_per_s": n_a / (ms_dev / 1e3), "launches_per_step": launches,
+           "e2e_ms_per_step": ms_e2e, "e2e_a_per_s": n_a / (ms_e2e / 1e3),
+           "e2e": "pinned host columns in, join rows and best pairs copied back, per step",
+           "cpu_baseline": cpu_baseline(smp)}
+    del dev, host
+    return out
+
+
+def oracle_requests(reqs, b_lon, b_lat, b_frame, n_pick, seed, max_a):
+    """The oracle timed request by request (the cpu_baseline of a batched or
+    served workload): n_pick seeded requests of at most max_a A sources, each
+    matched alone (all pairs, best pairs) against the B sources of its cap
+    widened by its offsets and largest region, on the host cores."""
+    import torch
+
+    import oracle
+
+    h = np.random.Generator(np.random.Philox(key=seed))
+    ok = [r for r, q in enumerate(reqs) if q["lon"].numel() <= max_a]
+    pick = sorted(h.choice(ok, min(n_pick, len(ok)), replace=False).tolist())
+    nthreads = host_threads()
+    tot_a, tot_b, tot_s = 0, 0, 0.0
+    for r in pick:
+        q = reqs[r]
+        c_lon, c_lat, rad = q["cap"]
+        if q.get("frame", b_frame) != b_frame:  # the cap centre in B's frame
+            if b_frame == oracle.GAL:
+                gl, gb = oracle.from_equatorial([c_lon], [c_lat], oracle.GAL)
+            else:
+                gl, gb = oracle.to_equatorial([c_lon], [c_lat], oracle.GAL)
+            c_lon, c_lat = float(gl[0]), float(gb[0])
+        reach = rad + (8.0 * q["offset_sigma"] + 1.5 * q["max_size"]) / 3600.0
+        cl, cb = math.radians(c_lon), math.radians(c_lat)
+        lr, br = torch.deg2rad(b_lon), torch.deg2rad(b_lat)
+        dot = (torch.cos(br) * torch.cos(lr) * (math.cos(cb) * math.cos(cl)) +
+               torch.cos(br) * torch.sin(lr) * (math.cos(cb) * math.sin(cl)) +
+               torch.sin(br) * math.sin(cb))
+        rows = torch.nonzero(dot >= math.cos(math.radians(min(180.0, reach)))).flatten()
+        bl, bb = b_lon[rows].cpu().numpy(), b_lat[rows].cpu().numpy()
+        al, ab = q["lon"].cpu().numpy(), q["lat"].cpu().numpy()
+        reg = {k: (v.cpu().numpy() if hasattr(v, "numel") else v) for k, v in q["region"].items()}
+        t = time.perf_counter()
+        m = oracle.match(al, ab, bl, bb, a_frame=q.get("frame", b_frame), b_frame=b_frame,
+                         nthreads=nthreads, **reg)
+        oracle.best(m, al.size)
+        tot_s += time.perf_counter() - t
+        tot_a += al.size
+        tot_b += bl.size
+    return {"value": tot_a / tot_s if tot_s else None, "unit": UNIT, "cores": nthreads,
+            "kind": "oracle", "requests": len(pick), "a_sources": tot_a, "b_in_caps": tot_b,
+            "seconds": tot_s,
+            "sample": f"{len(pick)} seeded requests of at most {max_a} A, each alone against "
+                      f"the B of its cap ({tot_a} A, {tot_b} B), all and best pairs, "
+                      f"{tot_s:.2f} s on {nthreads} threads"}
+
+
 def c2_leg(args, xm, torch, measured):
     """The clump-vs-compact-source case: A = 2e5 per-source ellipses against
     B = 5e6 in the galactic plane. The same step (build + match all and best
@@ -761,7 +866,7 @@ def values_leg(args, xm, torch):
 
 # ------------------------------------------------------- batched C4 leg
 
-def c4_leg(args, xm, torch):
+def c4_leg(args, xm, torch, measured):
     """Batched jobs (C4): thousands of uneven requests against one resident
     B index, matched by one persistent scan launched as a CUDA graph; the
     zone height and grid come from the autotuner on a sample of the
@@ -787,6 +892,38 @@ def c4_leg(args, xm, torch):
         if k:
             ms.append(info["device_ms"])
         del b
+    # one more pass launched kernel by kernel, an event pair around each
+    # launch: the persistent count pass against HBM (per A 16 B position +
+    # 8 B per per-source region column + 16 B best pair, per candidate 12 B)
+    # and against the float32 FMA peak (12 operations per candidate)
+    xm.reset_stats()
+    xm.prof_enable(True)
+    b = xm.Batch(idx, reqs, use_graph=False, persistent_blocks=tuned["persistent_blocks"])
+    torch.cuda.synchronize()
+    prof = xm.prof_all()
+    xm.prof_enable(False)
+    st = xm.stats()
+    del b
+    scan = None
+    if "k_scan_fp32_count" in prof:
+        t_ms, nl = prof["k_scan_fp32_count"]
+        cols = sum(q["lon"].numel() * sum(1 for v in q["region"].values() if hasattr(v, "numel"))
+                   for q in reqs)
+        alg = total_a * 32 + 8 * cols + 12 * st["candidates"]
+        peaks = load_peaks()
+        fp32 = measured["fp32_fma_tflops"]
+        achieved = alg / (t_ms * 1e-3) / 1e9
+        scan = {"kernel": "k_scan_fp32_count", "launches": nl, "ms": t_ms,
+                "candidates": int(st["candidates"]), "algorithmic_bytes": alg,
+                "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": achieved / peaks.get("hbm_gbs", 6800.0),
+                "peak_source": "of measured" if peaks.get("_source") == "measured" else "of fallback",
+                "fp32_tflops": 12.0 * st["candidates"] / (t_ms * 1e-3) / 1e12,
+                "fp32_frac": 12.0 * st["candidates"] / (t_ms * 1e-3) / 1e12 / fp32,
+                "fp32_peak_source": "of measured (xm_measure_peak)",
+                "kernels_ms": {k: round(v[0], 3) for k, v in
+                               sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}}
+    base = oracle_requests(d["requests"], d["b_lon"], d["b_lat"], d["b_frame"], 12, 4141, 200_000)
     out = {"workload": f"c4 batched: {len(reqs)} requests (n_A log-uniform 1e2-1e6, caps 0.1-10 deg, "
                        f"mixed shapes/sizes/joins) against B={args.c4_b} uniform all-sky",
            "requests": len(reqs), "total_a": int(total_a), "pairs": int(info["total_pairs"]),
@@ -794,7 +931,7 @@ def c4_leg(args, xm, torch):
            "launch": "one persistent scan in one CUDA graph per batch pass",
            "zone_height_arcsec": tuned["zone_height_arcsec"],
            "persistent_blocks": tuned["persistent_blocks"], "tune_trials": tuned["trials"],
-           "setup_s": setup_s}
+           "setup_s": setup_s, "scan_roofline": scan, "cpu_baseline": base}
     del d, reqs, idx
     torch.cuda.empty_cache()
     return out
@@ -824,6 +961,7 @@ def serving_leg(args, xm, torch):
                         zone_heights=(10.0, 20.0, 40.0), blocks_per_sm=(2, 4))
     idx = xm.Index(b["b_lon"], b["b_lat"], frame=b["b_frame"], ids=b["b_id"],
                    zone_height_arcsec=tuned["zone_height_arcsec"])
+    base = oracle_requests(pool, b["b_lon"], b["b_lat"], b["b_frame"], 12, 5151, 200_000)
     del b
     pinned = lambda t: t.cpu().pin_memory()  # noqa: E731
     host_pool = []
@@ -843,6 +981,7 @@ def serving_leg(args, xm, torch):
                       "the device"}
     host = serve_window(args, xm, idx, host_pool, args.serve_seconds, 0, tuned, 0)
     out.update(host, input="pinned host columns, copied by the submitting call", **common)
+    out["cpu_baseline"] = base
     short = max(5.0, args.serve_seconds / 3.0)
     out["device_inputs"] = dict(serve_window(args, xm, idx, pool, short, 1, tuned, 0),
                                 input="device-resident columns (device-to-device copy)")
@@ -947,23 +1086,25 @@ def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, region):
     launches, so achieved = all bytes / all kernel time):
     k_onesweep   per key and pass 8 B key + 4 B row, read and written, over
                  the passes that ran (the library counts keys x passes; an
-                 index sort planned to fewer passes launches the rest empty);
+                 index sort planned to fewer passes launches the rest empty),
+                 and 8 B more each way for keys that carry a payload (the
+                 index sort carries each record's float32 offsets);
     k_scan_fp32_count  per A 16 B position + 8 B per region column given per
                  source + 16 B best pair, per candidate 12 B (offsets + RA
                  key);
     k_prep_a     per A 16 B position (+ region columns) read, 88 B of
                  prepared record written;
-    k_gather_b   per B 16 B position read + 16 B record + 16 B position
+    k_gather_b   per B 8 B key + 4 B row + 8 B offsets read, 16 B record
                  written."""
     cols = sum(1 for k in ("a_col", "b_col", "pa_col") if region.get(k) is not None)
     if kernel == "k_onesweep":
-        return 24.0 * st["sort_key_passes"] / launches
+        return (24.0 * st["sort_key_passes"] + 16.0 * st.get("sort_pay_passes", 0)) / launches
     if kernel in ("k_scan_fp32_count", "k_scan_fp64_count"):
         return (n_a * (16 + 8 * cols + 16) + st["candidates"] / steps * 12) * steps / launches
     if kernel == "k_prep_a":
         return n_a * (16 + 8 * cols + 88) * steps / launches
     if kernel == "k_gather_b":
-        return n_b * (16 + 16 + 16) * steps / launches
+        return n_b * (8 + 4 + 8 + 16) * steps / launches
     return None
 
 

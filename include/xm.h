@@ -167,6 +167,7 @@ typedef struct {
     uint64_t tie_resolved; /* A sources whose best pair was decided in FP64 */
     uint64_t kernel_launches;
     uint64_t sort_key_passes; /* keys moved by radix-sort passes (keys x passes) */
+    uint64_t sort_pay_passes; /* of those, keys that carried a 64-bit payload */
 } xm_stats;
 
 /* ---- status and configuration ------------------------------------------ */

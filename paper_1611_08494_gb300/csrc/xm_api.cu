@@ -255,8 +255,8 @@ unsigned long long* device_stats() {
     return g_dev_stats[dev];
 }
 
-static void device_stats_read(unsigned long long out[6]) {
-    for (int k = 0; k < 6; k++) out[k] = 0;
+static void device_stats_read(unsigned long long out[7]) {
+    for (int k = 0; k < 7; k++) out[k] = 0;
     std::lock_guard<std::mutex> g(g_dev_stats_mu);
     int cur = 0;
     cudaGetDevice(&cur);
@@ -265,7 +265,7 @@ static void device_stats_read(unsigned long long out[6]) {
         unsigned long long h[8];
         cudaSetDevice(d);
         if (cudaMemcpy(h, g_dev_stats[d], sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
-            for (int k = 0; k < 6; k++) out[k] += h[k];
+            for (int k = 0; k < 7; k++) out[k] += h[k];
     }
     cudaSetDevice(cur);
 }
@@ -353,7 +353,7 @@ extern "C" xm_status xm_set_allocator(void* (*alloc)(size_t, void*, void*),
 
 extern "C" xm_status xm_get_stats(xm_stats* out) {
     if (!out) return set_error(XM_EINVAL, "xm_get_stats: NULL");
-    unsigned long long d[6];
+    unsigned long long d[7];
     device_stats_read(d);  // waits for the kernels that add to them
     out->candidates = g_stats[0].load() + d[0];
     out->rechecked = g_stats[1].load() + d[1];
@@ -362,6 +362,7 @@ extern "C" xm_status xm_get_stats(xm_stats* out) {
     out->tie_resolved = g_stats[4].load() + d[4];
     out->kernel_launches = g_stats[5].load();
     out->sort_key_passes = d[5];
+    out->sort_pay_passes = d[6];
     return XM_OK;
 }
 

@@ -7,16 +7,17 @@
 //   k_zone_geom   per zone: centre, its sin/cos, number and width of RA cells
 //                 (once per device and zone count, then copied)
 //   k_ingest_b    per source, input order: validity, fixed-point position,
-//                 sort key; exact position kept by row
+//                 sort key, the float32 offsets in its cell; exact position
+//                 kept by row
 //   index sort    (xm_sort.cu) on a plan k_ingest_b narrows: the zone range
 //                 and the RA bits that vary, so a catalogue of a small sky
-//                 area sorts in fewer passes
+//                 area sorts in fewer passes; the offsets ride along
 //   k_zone_start  first sorted source of each zone (binary search)
 //   k_zone_rows   rows of each zone, size of its RA bucket table (one to two
 //                 buckets per source); prefix sum; k_zone_lut the offsets
 //   k_gather_b    the 16-byte records in (zone, RA) order (float32 offsets
-//                 in the cell's tangent frame, RA key, row), and the bucket
-//                 tables
+//                 in the cell's tangent frame, RA key, row) from the sorted
+//                 arrays, and the bucket tables
 //   k_gap_fill    the long runs of the bucket tables
 #include <math.h>
 #include <string.h>
@@ -91,9 +92,29 @@ __device__ __forceinline__ void plan_accumulate(bool has, uint32_t z, uint32_t r
     }
 }
 
+// The float32 offsets (xi, eta) of a source in the tangent frame of its cell
+// (zone centre line, RA cell centre), from its exact fixed-point position k.
+__device__ __forceinline__ void cell_offsets(const PosKey& k, float h_f, const ZoneInfo& Z,
+                                             float* xi, float* eta) {
+    const uint32_t ra_key = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
+    const uint32_t bin = bin_of(ra_key, Z.nbins);
+    const LatTerms L = lat_terms(h_f * k.zfrac, Z.sin_cf, Z.cos_cf);
+    float sa, hav_a;
+    sin_hav(Z.binw_f * cells_from_centre(k.key64, Z.nbins, bin), &sa, &hav_a);
+    *xi = L.cd * sa;
+    *eta = fmaf(L.cd * Z.sin_cf, hav_a, L.sdd);
+}
+
+// Ingest of B, one source per thread in input order: validity, longitude
+// mod 360, the exact position kept by row, the sort key (zone above the RA
+// key to 2^-24 of a turn; the sort orders on the zone and the top 16 RA
+// bits only), and the record's float32 offsets in its cell as the sort's
+// payload (x in the low word, y in the high word), so the records are
+// formed in index order without reading positions at random rows.
 __global__ void __launch_bounds__(kBlock) k_ingest_b(
     const double* __restrict__ lon, const double* __restrict__ lat, int64_t n, int32_t nz,
-    uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, double2* __restrict__ pos,
+    float h_f, const ZoneInfo* __restrict__ zones, uint64_t* __restrict__ keys,
+    uint32_t* __restrict__ vals, uint64_t* __restrict__ pay, double2* __restrict__ pos,
     double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz, SortPlan* plan,
     int32_t* err) {
     pdl_wait();
@@ -110,33 +131,17 @@ __global__ void __launch_bounds__(kBlock) k_ingest_b(
         lo = lon_mod360(lo);
         const PosKey k = pos_key(lo, la, nz);
         z = (uint32_t)k.z;
-        const uint32_t rk = (uint32_t)(k.key64 >> 32) & kIndexRaMask;
-        ra = rk >> kIndexSortBeginBit;
+        const uint32_t rk = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
+        ra = (rk & kIndexRaMask) >> kIndexSortBeginBit;
         keys[i] = ((uint64_t)z << 32) | rk;
         vals[i] = (uint32_t)i;
+        float xi, eta;
+        cell_offsets(k, h_f, zones[z], &xi, &eta);
+        pay[i] = (uint64_t)__float_as_uint(xi) | ((uint64_t)__float_as_uint(eta) << 32);
         pos[i] = make_double2(lo, la);
         if (px) unit64_deg(lo, la, &px[i], &py[i], &pz[i]);
     }
     plan_accumulate(has, z, ra, plan);
-}
-
-// The index record of a source at (lon, lat): float32 offsets in the tangent
-// frame of its cell (zone centre line, RA cell centre), from the exact
-// fixed-point position.
-__device__ __forceinline__ BRec make_brec(double lon, double lat, int32_t row, int32_t nz, float h_f,
-                                          const ZoneInfo& Z) {
-    const PosKey k = pos_key(lon, lat, nz);
-    const uint32_t ra_key = (uint32_t)(k.key64 >> 32) & kRaKeyMask;
-    const uint32_t bin = bin_of(ra_key, Z.nbins);
-    const LatTerms L = lat_terms(h_f * k.zfrac, Z.sin_cf, Z.cos_cf);
-    float sa, hav_a;
-    sin_hav(Z.binw_f * cells_from_centre(k.key64, Z.nbins, bin), &sa, &hav_a);
-    BRec r;
-    r.xi = L.cd * sa;
-    r.eta = fmaf(L.cd * Z.sin_cf, hav_a, L.sdd);
-    r.ra_key = ra_key;
-    r.row = row;
-    return r;
 }
 
 // The sorted keys and rows of an index build: where the plan's passes left
@@ -144,11 +149,14 @@ __device__ __forceinline__ BRec make_brec(double lon, double lat, int32_t row, i
 struct Sorted {
     const uint64_t* k0;
     const uint32_t* v0;
+    const uint64_t* p0;
     const uint64_t* k1;
     const uint32_t* v1;
+    const uint64_t* p1;
     const SortPlan* plan;
     __device__ __forceinline__ const uint64_t* keys() const { return sorted_in_scratch(plan) ? k1 : k0; }
     __device__ __forceinline__ const uint32_t* vals() const { return sorted_in_scratch(plan) ? v1 : v0; }
+    __device__ __forceinline__ const uint64_t* pays() const { return sorted_in_scratch(plan) ? p1 : p0; }
 };
 
 __global__ void k_zone_start(Sorted S, int64_t n, int32_t nz, int64_t* __restrict__ zone_start) {
@@ -182,9 +190,9 @@ __global__ void k_zone_rows(int32_t nz, const int64_t* __restrict__ zone_start, 
     int lg = 0;
     while (lg < 24 && ((int64_t)1 << lg) < m) lg++;
     uint32_t kmin = 0, range = 0;
-    if (m > 0) {
-        kmin = (uint32_t)keys[Z.start];
-        range = (uint32_t)keys[Z.end - 1] - kmin;
+    if (m > 0) {  // (the keys are in order of their top 16 RA bits only)
+        kmin = (uint32_t)keys[Z.start] & kIndexRaMask;
+        range = ((uint32_t)keys[Z.end - 1] & kIndexRaMask) - kmin;
     }
     const int bits = range ? 32 - __clz(range) : 0;
     // buckets no finer than the order of the sorted keys (which keep only
@@ -224,7 +232,7 @@ __global__ void k_zone_lut(int32_t nz, const int64_t* __restrict__ lut_off,
 }
 
 __device__ __forceinline__ uint32_t bucket_of(uint64_t key, const ZoneInfo& Z) {
-    return ((uint32_t)key - Z.lut_kmin) >> Z.lut_shift;
+    return (((uint32_t)key & kIndexRaMask) - Z.lut_kmin) >> Z.lut_shift;
 }
 
 // A run of bucket-table entries that take one value, too long for the
@@ -243,21 +251,23 @@ constexpr uint32_t kGapInline = 32;  // longest run written by the finding threa
 // row's bucket up to its own; the zone's last row also writes the entries
 // after its bucket (the value: the zone's row count). Runs longer than
 // kGapInline go to a list for k_gap_fill.
-__global__ void k_gather_b(Sorted S, int64_t n, const double2* __restrict__ pos, int32_t nz, float h_f,
-                           const ZoneInfo* __restrict__ zones, uint32_t* __restrict__ lut,
-                           BRec* __restrict__ rec, LutGap* __restrict__ gaps,
-                           unsigned long long* __restrict__ n_gaps, long long gap_cap,
-                           int32_t* err) {
+__global__ void k_gather_b(Sorted S, int64_t n, const ZoneInfo* __restrict__ zones,
+                           uint32_t* __restrict__ lut, BRec* __restrict__ rec,
+                           LutGap* __restrict__ gaps, unsigned long long* __restrict__ n_gaps,
+                           long long gap_cap, int32_t* err) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t* __restrict__ keys = S.keys();
-    const uint32_t* __restrict__ vals = S.vals();
     const uint64_t key = keys[i];
     const ZoneInfo& Z = zones[key >> 32];
-    const uint32_t row = vals[i];
-    const double2 p = pos[row];
-    rec[i] = make_brec(p.x, p.y, (int32_t)row, nz, h_f, Z);
+    const uint64_t off = S.pays()[i];
+    BRec r;
+    r.xi = __uint_as_float((uint32_t)off);
+    r.eta = __uint_as_float((uint32_t)(off >> 32));
+    r.ra_key = (uint32_t)key;
+    r.row = (int32_t)S.vals()[i];
+    rec[i] = r;
     const int64_t rows = Z.end - Z.start, rel = i - Z.start;
     const int64_t b = bucket_of(key, Z);
     const int64_t pb = rel == 0 ? -1 : (int64_t)bucket_of(keys[i - 1], Z);
@@ -374,7 +384,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     xm_status st = XM_OK;
     // temporaries
     double *d_lon = nullptr, *d_lat = nullptr;
-    uint64_t *keys = nullptr, *tk = nullptr;
+    uint64_t *keys = nullptr, *tk = nullptr, *pay = nullptr, *tp = nullptr;
     uint32_t *vals = nullptr, *tv = nullptr;
     int32_t* err = nullptr;
     SortPlan* plan = nullptr;
@@ -427,6 +437,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         }
         keys = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
         vals = (uint32_t*)dev_alloc(2 * nn * sizeof(uint32_t), s);
+        pay = (uint64_t*)dev_alloc(2 * nn * sizeof(uint64_t), s);
         err = (int32_t*)dev_alloc(sizeof(int32_t), s);
         plan = (SortPlan*)dev_alloc(sizeof(SortPlan), s);
         lut_cnt = (int32_t*)dev_alloc(X->nz * sizeof(int32_t), s);
@@ -439,13 +450,14 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
         gap_cap = X->lut_n / (kGapInline + 1) + 2 * (int64_t)X->nz + 16;
         gaps = (LutGap*)dev_alloc(gap_cap * sizeof(LutGap) + 16, s);
         n_gaps = gaps ? (unsigned long long*)(gaps + gap_cap) : nullptr;
-        if (!keys || !vals || !err || !plan || !lut_cnt || !lut_off || !X->lut || !gaps) {
+        if (!keys || !vals || !pay || !err || !plan || !lut_cnt || !lut_off || !X->lut || !gaps) {
             fail(set_error(XM_ENOMEM, "index build buffers"));
             break;
         }
         X->bytes += X->lut_n * sizeof(uint32_t);
         tk = keys + nn;
         tv = vals + nn;
+        tp = pay + nn;
         e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(n_gaps, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) { fail(cuda_fail(e, "memset")); break; }
@@ -459,14 +471,14 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
             if (r != XM_OK) return r;
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz, keys, vals,
-                          X->pos, X->px, X->py, X->pz, plan, err);
+                XM_LAUNCH("k_ingest_b", g, kBlock, 0, s, k_ingest_b, lon, lat, n, X->nz, G.h_f,
+                          X->zones, keys, vals, pay, X->pos, X->px, X->py, X->pz, plan, err);
             }
             // the virtual key: zone offset above the RA bits that vary
             const int max_passes = (bits_for(X->nz - 1) + 32 - kIndexSortBeginBit + 7) / 8;
-            r = index_sort(keys, vals, tk, tv, n, plan, max_passes, err, s);
+            r = index_sort(keys, vals, pay, tk, tv, tp, n, plan, max_passes, err, s);
             if (r != XM_OK) return r;
-            const Sorted S{keys, vals, tk, tv, plan};
+            const Sorted S{keys, vals, pay, tk, tv, tp, plan};
             XM_LAUNCH("k_zone_start", gz, kBlock, 0, s, k_zone_start, S, n, X->nz, X->zone_start);
             XM_LAUNCH("k_zone_rows", gz, kBlock, 0, s, k_zone_rows, X->nz, X->zone_start, S,
                       X->zones, lut_cnt);
@@ -476,8 +488,8 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
                       X->lut);
             if (n > 0) {
                 const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, S, n, X->pos, X->nz,
-                          G.h_f, X->zones, X->lut, X->rec, gaps, n_gaps, gap_cap, err);
+                XM_LAUNCH("k_gather_b", g, kBlock, 0, s, k_gather_b, S, n, X->zones, X->lut,
+                          X->rec, gaps, n_gaps, gap_cap, err);
                 XM_LAUNCH("k_gap_fill", 4 * 152, kBlock, 0, s, k_gap_fill, gaps, n_gaps, gap_cap,
                           X->lut);
             }
@@ -500,6 +512,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     dev_free(d_lon, s);
     dev_free(keys, s);
     dev_free(vals, s);
+    dev_free(pay, s);
     dev_free(err, s);
     dev_free(plan, s);
     dev_free(lut_cnt, s);

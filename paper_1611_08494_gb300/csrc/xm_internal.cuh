@@ -527,12 +527,14 @@ struct SortPlan {
 // Sets a plan to the empty ranges the key kernel narrows.
 xm_status sort_plan_init(SortPlan* plan, cudaStream_t s);
 
-// Sorts (keys, vals) of an index build by the plan's virtual key with up to
-// `max_passes` launches (each does nothing past plan->active). The sorted
-// data ends in (keys, vals) when plan->active is even, else in (tk, tv);
+// Sorts (keys, vals, pay) of an index build by the plan's virtual key with up
+// to `max_passes` launches (each does nothing past plan->active); pay (a
+// 64-bit payload per key, with scratch tp) may be NULL. The sorted data ends
+// in (keys, vals, pay) when plan->active is even, else in (tk, tv, tp);
 // sorted_in_scratch() tells which on the device.
-xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                     SortPlan* plan, int max_passes, int32_t* err, cudaStream_t s);
+xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* pay, uint64_t* tk, uint32_t* tv,
+                     uint64_t* tp, int64_t n, SortPlan* plan, int max_passes, int32_t* err,
+                     cudaStream_t s);
 
 __device__ __forceinline__ bool sorted_in_scratch(const SortPlan* plan) { return plan->active & 1; }
 

@@ -64,6 +64,34 @@ xm_status launch_scan_fused(int prec, const ScanArgs& a, int mode, int64_t n_uni
     return launch_scan_t<kPrecFP64, kModeEmit, true>("k_scan_fp64_emit", a, n_units, s);
 }
 
+// The sparse count pass (k_scan_src): persistent warps, at most the blocks
+// resident at once.
+// Whether the count pass takes the sparse form: float32 tests in input order,
+// and a region of fixed size whose bounding radius is under 0.4 zone heights,
+// so a source meets at most two zones (sources with more items are left to
+// k_scan by the pass itself).
+bool sparse_scan(int prec, bool sorted_a, const xm_region* region, const xm_index* X) {
+    if (prec != XM_PREC_FP32_RECHECK || sorted_a || region->a_col || region->b_col) return false;
+    const double k = region->size_scale * region->size_unit_arcsec * kArcsec;
+    const double a = fabs(region->a) * k, b = fabs(region->b) * k;
+    const double R = region->shape == XM_RECT     ? hypot(a, b)
+                     : region->shape == XM_CIRCLE ? a
+                                                  : fmax(a, b);
+    return R < 0.4 * X->h;
+}
+
+xm_status launch_scan_src(const ScanArgs& a, int32_t* defer, int32_t* n_defer, cudaStream_t s) {
+    prepare_kernels();
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (a.nA + 32 * kScanWarps - 1) / (32 * kScanWarps);
+    if (g > 8LL * sms) g = 8LL * sms;
+    if (g < 1) g = 1;
+    XM_LAUNCH("k_scan_src", (unsigned)g, kScanThreads, kSrcSmem, s, k_scan_src, a, defer, n_defer);
+    return XM_OK;
+}
+
 xm_status launch_scan_any(int prec, const ScanArgs& a, int mode, int64_t n_units, cudaStream_t s) {
     if (a.A == nullptr) return launch_scan_fused(prec, a, mode, n_units, s);
     if (n_units <= 0) return XM_OK;
@@ -262,8 +290,9 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             const bool keep_cold = sorted_a || want_all;
             R->acold = keep_cold ? (ACold*)dev_alloc(nn * sizeof(ACold), ps) : nullptr;
             ACold* cold = R->acold;
-            int32_t* lists = T.get<int32_t>(3 * nn);
-            // [0] err, [1..3] list counts, [4] chunk queue, [6] largest member count
+            int32_t* lists = T.get<int32_t>(4 * nn);
+            // [0] err, [1..3] list counts, [4] chunk queue, [5] sources the
+            // sparse pass leaves, [6] largest member count, [7] their queue
             int32_t* small = T.get<int32_t>(8);
             int64_t* total = T.get<int64_t>(2);
             unsigned long long* stats = device_stats();
@@ -322,7 +351,21 @@ extern "C" xm_status xm_match(const xm_index* X, const xm_columns* Acols, const 
             a.max_count = max_count;
             ScanArgs cq = a;
             cq.queue = (unsigned int*)(small + 4);
-            xm_status r = launch_scan_any(prec, cq, kModeCount, nA, s);
+            xm_status r = XM_OK;
+            if (sparse_scan(prec, sorted_a, region, X)) {
+                // one lane per source where regions are small against the
+                // zones, then the warp-cooperative scan over the sources it
+                // left (their number read on the device)
+                r = launch_scan_src(cq, lists + 3 * nn, small + 5, s);
+                if (r != XM_OK) return r;
+                ScanArgs cd = cq;
+                cd.list = lists + 3 * nn;
+                cd.nlist_dev = small + 5;
+                cd.queue = (unsigned int*)(small + 7);
+                r = launch_scan_any(prec, cd, kModeCount, nA, s);
+            } else {
+                r = launch_scan_any(prec, cq, kModeCount, nA, s);
+            }
             if (r != XM_OK) return r;
             r = exclusive_scan_i32(R->count, R->pair_off, nA, total, err, s);
             if (r != XM_OK) return r;

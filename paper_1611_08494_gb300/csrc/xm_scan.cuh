@@ -46,12 +46,16 @@ struct AIn {
     int32_t nz;
 };
 
+__device__ __noinline__ void rotate_position(double lon, double lat, const double* rot,
+                                             double* lon_o, double* lat_o, double* gamma);
+
 // Index-frame position of an A source given as (lon, lat) in its input
 // frame, in degrees (lon in [0, 360)), and the angle gamma from the index
 // frame's north to the input frame's north (east positive) at that point.
 // rot (row major) maps input-frame vectors to the index frame when rotate.
-__device__ void a_position_of(double lon, double lat, int32_t rotate, const double* rot,
-                              double* lon_o, double* lat_o, double* gamma, bool* ok) {
+__device__ __forceinline__ void a_position_of(double lon, double lat, int32_t rotate,
+                                              const double* rot, double* lon_o, double* lat_o,
+                                              double* gamma, bool* ok) {
     *ok = coord_ok(lon, lat);
     if (!*ok) { lon = 0.0; lat = 0.0; }
     lon = lon_mod360(lon);
@@ -61,6 +65,14 @@ __device__ void a_position_of(double lon, double lat, int32_t rotate, const doub
         *gamma = 0.0;
         return;
     }
+    rotate_position(lon, lat, rot, lon_o, lat_o, gamma);
+}
+
+// The rotation of a position into the index frame and the angle between the
+// two frames' north directions there (out of line: its float64 trigonometry
+// would otherwise hold registers in every kernel that prepares sources).
+__device__ __noinline__ void rotate_position(double lon, double lat, const double* rot,
+                                             double* lon_o, double* lat_o, double* gamma) {
     double sl, cl, sb, cb;
     sincos(lon * kDeg, &sl, &cl);
     sincos(lat * kDeg, &sb, &cb);
@@ -923,6 +935,268 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan(ScanArgs P) {
 
 constexpr size_t kScanSmem = sizeof(ScanWarpSmem) * kScanWarps;
 
+// ------------------------------------------------ the sparse count pass
+//
+// The count pass for regions that are small against the zone height, where a
+// source meets one or two zone items and a few records (the all-sky case):
+// one lane per source from its preparation to its results, with the running
+// state in registers instead of the flattened item and candidate rounds of
+// k_scan. A lane finds its items' bucket ranges at once; then the warp steps
+// through the lanes' records together, one record per lane and step (the next
+// one loaded while this one is tested), so the step's members can be staged
+// in shared memory and written to the record arena with one atomic per warp
+// and stage. The best-pair fold and the member indices are the count pass's
+// (sequential per source, the same minimum, second minimum and lowest-row
+// tie). Sources outside this shape -- more than two items, more than
+// kSrcMaxRec records in their ranges, or float64 separations -- are listed
+// (`defer`) and counted by k_scan over the list afterwards, in the same
+// outputs.
+
+constexpr int kSrcMaxRec = 48;  // records a lane takes on; more go to k_scan
+constexpr int kSrcStage = 64;   // member records staged per warp
+
+struct SrcWarpSmem {
+    MemberRec rec[kSrcStage];
+    ACold cold[32];  // float64 part of each lane's source
+    uint8_t who[kSrcStage];  // lane of each staged record
+    int32_t drop[32];        // a member of the lane's source did not fit the arena
+};
+
+constexpr size_t kSrcSmem = sizeof(SrcWarpSmem) * kScanWarps;
+
+// The float64 decision of a candidate in the guard band (rare), out of line
+// so its registers are not held across the record loop.
+__device__ __noinline__ bool recheck64(const ACold* C, int shape, const double2* pos,
+                                       const double* ux, const double* uy, const double* uz,
+                                       int32_t row) {
+    const A64 a64 = make_a64(*C);
+    double px, py, pz, rho;
+    if (ux) {
+        px = ux[row];
+        py = uy[row];
+        pz = uz[row];
+    } else {
+        const double2 p = pos[row];
+        unit64_deg(p.x, p.y, &px, &py, &pz);
+    }
+    return test64(a64, shape, px, py, pz, &rho);
+}
+
+__global__ void __launch_bounds__(kScanThreads, 6) k_scan_src(ScanArgs P, int32_t* defer,
+                                                              int32_t* n_defer) {
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char src_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SrcWarpSmem& W = reinterpret_cast<SrcWarpSmem*>(src_smem)[warp];
+    const IndexGeom& G = P.G;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t n_cand = 0, n_mem = 0;
+    int max_cnt = 0;
+    // The region has a fixed size: its prepared terms are the same for every
+    // source, except when a frame rotation turns a region that is not a
+    // circle (the position angle then varies with the position). They are
+    // prepared once per block; each source adds its position.
+    const AIn& I = P.in;
+    const bool same_region = !I.rotate || I.shape == XM_CIRCLE;
+    __shared__ APrep s_at;
+    __shared__ ACold s_ct;
+    if (threadIdx.x == 0) {
+        const double b = I.shape == XM_CIRCLE ? I.a : I.b;
+        APrep at;
+        ACold ct;
+        make_aprep(0.0, 0.0, 0.0, true, I.a, b, I.pa, I.shape, I.pa_dir, I.size_k, I.pa_zero, I.nz,
+                   I.h_f, 0, &at, &ct);
+        s_at = at;
+        s_ct = ct;
+        if (blockIdx.x == 0 && P.nA > 0 && !size_ok(I.a, b, I.pa)) atomicOr(P.err, kErrSize);
+    }
+    __syncthreads();
+    // chunks from the queue, the next one claimed while this one runs
+    unsigned int next = 0;
+    if (lane == 0) next = atomicAdd(P.queue, 1u);
+    for (;;) {
+        const int64_t first = (int64_t)__shfl_sync(0xffffffffu, next, 0) * 32;
+        if (first >= P.nA) break;  // whole warp
+        if (lane == 0) next = atomicAdd(P.queue, 1u);
+        W.drop[lane] = 0;
+
+        // ---- preparation, window and bucket ranges (lane = source)
+        APrep A;
+        bool mine = false;  // this lane's source is counted here
+        int n0 = 0, nrec = 0;  // records of item 0, of both items
+        int32_t lo0 = 0, lo1 = 0;  // first rows (rows fit 31 bits)
+        uint32_t klo0 = 0, khi0 = 0, klo1 = 0, khi1 = 0;
+        int32_t z0 = 0, z1 = 0;
+        if (first + lane < P.nA) {
+            const int64_t s = first + lane;
+            ACold C;
+            if (same_region) {
+                double lon, lat, gamma;
+                bool ok;
+                a_position_of(I.lon[s], I.lat[s], I.rotate, I.rot, &lon, &lat, &gamma, &ok);
+                if (!ok) atomicOr(P.err, kErrCoord);
+                const PosKey k = pos_key(lon, lat, I.nz);
+                A = s_at;
+                A.key64 = k.key64;
+                A.z = k.z;
+                A.zfrac = k.zfrac;
+                A.row = (int32_t)s;
+                if (!ok) {  // (an invalid position matches nothing)
+                    A.R = 0.0f;
+                    A.g = 0.0f;
+                    A.m00 = A.m01 = A.m10 = A.m11 = 0.0f;
+                }
+                C = s_ct;
+                C.lon = lon;
+                C.lat = lat;
+            } else {
+                prep_one(I, s, P.err, &A, &C);
+            }
+            W.cold[lane] = C;
+            mine = 16.0f * kEps32 * (A.R + 2.0f * G.h_f) * 206264.8f <= 9e-5f;  // float32 separations
+            if (mine && A.R > 0.0f) {
+                const Window w = a_window(A, G);
+                const int items = (w.z1 - w.z0 + 1) * w.nseg;
+                if (items > 2) {
+                    mine = false;
+                } else {
+                    // item 0: (z0, segment 0); item 1: the next zone, or the
+                    // second segment of the same zone
+                    z0 = w.z0;
+                    z1 = w.nseg == 2 ? w.z0 : w.z0 + 1;
+                    klo0 = w.lo[0];
+                    khi0 = w.hi[0];
+                    klo1 = w.lo[w.nseg - 1];
+                    khi1 = w.hi[w.nseg - 1];
+                    int64_t l0, h0, l1 = 0, h1 = 0;
+                    if (items == 2) bucket_bounds(G, load_zone_hot(G.zhot + z1), klo1, khi1, &l1, &h1);
+                    bucket_bounds(G, load_zone_hot(G.zhot + z0), klo0, khi0, &l0, &h0);
+                    if ((h0 - l0) + (h1 - l1) > kSrcMaxRec) {
+                        mine = false;
+                    } else {
+                        lo0 = (int32_t)l0;
+                        lo1 = (int32_t)l1;
+                        n0 = (int)(h0 - l0);
+                        nrec = n0 + (int)(h1 - l1);
+                    }
+                }
+            }
+            if (!mine) defer[atomicAdd(n_defer, 1)] = (int32_t)s;
+        }
+
+        // ---- records: the warp steps through the lanes' records together,
+        // one per lane and step, the next one loaded while this one is tested
+        // (loading more at once measured slower: the unrolled steps run
+        // whether or not their lanes have records). Keys are the bit patterns
+        // of the float32 separations (non-negative, so ordered as integers).
+        int cnt = 0;
+        int32_t m1 = 0x7F800000, m2 = 0x7F800000;  // smallest and second smallest key
+        int32_t b1 = 0x7fffffff;
+        int j = 0, cur = -1;
+        ItemTerms T;
+        BRec nb;
+        if (mine && nrec > 0) nb = load_brec(G.rec + (n0 > 0 ? lo0 : lo1));
+        int staged = 0;  // (warp-uniform)
+        auto flush = [&]() {
+            __syncwarp();
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.arena_n, (unsigned long long)staged);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int i = lane; i < staged; i += 32) {
+                if ((long long)(base + i) < P.arena_cap) P.arena[base + i] = W.rec[i];
+                else W.drop[W.who[i]] = 1;
+            }
+            staged = 0;
+            __syncwarp();
+        };
+        while (__any_sync(0xffffffffu, mine && j < nrec)) {
+            int32_t key = -1, brow = 0;  // key >= 0: the record is a member
+            if (mine && j < nrec) {
+                const BRec b = nb;
+                const int it = j < n0 ? 0 : 1;
+                j++;
+                if (j < nrec) nb = load_brec(G.rec + (j < n0 ? lo0 + j : lo1 + (j - n0)));
+                if (b.ra_key >= (it ? klo1 : klo0) && b.ra_key <= (it ? khi1 : khi0)) {
+                    if (it != cur) {
+                        cur = it;
+                        const int32_t z = it ? z1 : z0;
+                        T = item_terms(A, load_zone_hot(G.zhot + z), z, G.h_f);
+                    }
+                    n_cand++;
+                    float x, y;
+                    const float q = q32(A, A.shape, T, b, &x, &y);
+                    if (q <= 1.0f + A.g) {
+                        bool in = true;
+                        if (q >= 1.0f - A.g) {  // the guard band: decided in float64
+                            in = recheck64(&W.cold[lane], A.shape, G.pos, G.px, G.py, G.pz, b.row);
+                            atomicAdd(&P.stats[1], 1ull);
+                            if (in != (q <= 1.0f)) atomicAdd(&P.stats[2], 1ull);
+                        }
+                        if (in) {
+                            const float s2 = fmaf(x, x, y * y);
+                            const float rho32 = s2 < 1e-6f ? sqrtf(s2) * fmaf(s2, 1.0f / 6.0f, 1.0f)
+                                                           : asinf(sqrtf(s2));
+                            key = __float_as_int(rho32);
+                            brow = b.row;
+                            n_mem++;
+                            cnt++;
+                            if (key < m1 || (key == m1 && brow < b1)) {
+                                m2 = m1;
+                                m1 = key;
+                                b1 = brow;
+                            } else {
+                                m2 = min(m2, key);
+                            }
+                        }
+                    }
+                }
+            }
+            if (P.arena) {
+                const uint32_t mm = __ballot_sync(0xffffffffu, key >= 0);
+                if (mm) {
+                    if (staged + __popc(mm) > kSrcStage) flush();
+                    if (key >= 0) {
+                        const int slot = staged + __popc(mm & lt_mask);
+                        MemberRec r;
+                        r.a_row = A.row;
+                        r.k = cnt - 1;
+                        r.b_row = brow;
+                        r.f32 = 1;
+                        r.sep = __longlong_as_double((long long)key);
+                        W.rec[slot] = r;
+                        W.who[slot] = (uint8_t)lane;
+                    }
+                    staged += __popc(mm);
+                }
+            }
+        }
+        if (P.arena && staged > 0) flush();
+        __syncwarp();
+
+        // ---- results (lane = source)
+        if (mine) {
+            P.count[A.row] = cnt;
+            max_cnt = max(max_cnt, cnt);
+            if (P.acold_out && cnt > 0) P.acold_out[A.row] = W.cold[lane];
+            if (P.want_best) {
+                P.best_b[A.row] = cnt ? (int64_t)b1 : -1;
+                P.best_sep[A.row] = cnt ? (double)__int_as_float(m1) * kRadToArcsec : NAN;
+                // float32 separations within twice their error bound of the
+                // smallest: the best pair is decided in float64
+                const float esep = 16.0f * kEps32 * (A.R + 2.0f * G.h_f);
+                if (cnt > 1 && __int_as_float(m2) - __int_as_float(m1) <= 2.0f * esep)
+                    P.tie_list[atomicAdd(&P.list_n[1], 1)] = A.row;
+            }
+            if (W.drop[lane]) P.ovf_list[atomicAdd(&P.list_n[0], 1)] = A.row;
+        }
+        __syncwarp();
+    }
+    warp_add(&P.stats[0], n_cand);
+    warp_add(&P.stats[3], n_mem);
+    const int wm = __reduce_max_sync(0xffffffffu, max_cnt);
+    if (P.max_count && lane == 0 && wm > 0) atomicMax(P.max_count, wm);
+}
+
 // Pair records from the arena to their canonical slots: row a_row, member k.
 // In a batch, a_row is batch-wide and lrow maps it to the request's row.
 __global__ void k_place(const MemberRec* __restrict__ arena, const unsigned long long* n_rec,
@@ -1147,6 +1421,7 @@ void prepare_kernels() {
     cudaFuncSetAttribute(k_scan<kPrecFP32, kModeResolve, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_scan<kPrecFP64, kModeCount, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_scan<kPrecFP64, kModeEmit, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_scan_src, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrcSmem);
     radix_sort_prepare();
     done[dev] = true;
 }

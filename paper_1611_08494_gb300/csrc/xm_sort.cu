@@ -131,6 +131,8 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// A pass's shared memory; a pass that carries a 64-bit payload per key has
+// kSortTile more words of it after the struct.
 struct OnesweepSmem {
     uint64_t keys[kSortTile];
     uint32_t vals[kSortTile];
@@ -155,12 +157,17 @@ struct OnesweepSmem {
 // lowers it); silent_tile (-1 = none) is a tile that publishes nothing, so
 // the look-backs after it wait on words nobody writes -- the test form of a
 // stalled predecessor, which must end in XM_ETIMEOUT and never in a hang.
+//
+// PAY: every key also carries a 64-bit payload (pay_in -> pay_out), moved
+// with its row.
+template <bool PAY>
 __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
-    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n,
-    int shift, const unsigned long long* __restrict__ offs, uint64_t* status,
-    unsigned int* tile_counter, uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    int32_t* err, const SortPlan* plan, int pass, unsigned long long* stats, int spin_limit,
-    int silent_tile) {
+    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    const uint64_t* __restrict__ pay_in, int64_t n, int shift,
+    const unsigned long long* __restrict__ offs, uint64_t* status, unsigned int* tile_counter,
+    uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    uint64_t* __restrict__ pay_out, int32_t* err, const SortPlan* plan, int pass,
+    unsigned long long* stats, int spin_limit, int silent_tile) {
     pdl_wait();
     // with a plan: the digit of pass `pass` of the virtual key, and nothing
     // to do past the passes the plan needs (uniform over the grid)
@@ -172,11 +179,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    uint64_t* S_pay = reinterpret_cast<uint64_t*>(smem_raw + sizeof(OnesweepSmem));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ int given_up;
     if (threadIdx.x == 0) {
         S.tile = (int)atomicAdd(tile_counter, 1u);
-        if (S.tile == 0 && stats) atomicAdd(&stats[5], (unsigned long long)n);  // keys this pass
+        if (S.tile == 0 && stats) {  // keys this pass (and with a payload)
+            atomicAdd(&stats[5], (unsigned long long)n);
+            if (PAY) atomicAdd(&stats[6], (unsigned long long)n);
+        }
         given_up = (*(volatile int32_t*)err & kErrTimeout) != 0;
     }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&S.wcount[0][0])[i] = 0;
@@ -195,12 +206,16 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
     const int64_t tile_base = (int64_t)tile * kSortTile;
     const int64_t warp_base = tile_base + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
+    // the digit's first output slot (thread d), read now so the load
+    // overlaps the tile's own loads
+    const unsigned long long off_d = threadIdx.x < kRadix ? offs[threadIdx.x] : 0ull;
     uint64_t key[kSortItems];
     int32_t rank[kSortItems];
     // warp-striped: item k of lane l is element warp_base + 32 k + l, so the
     // (k, lane) order is the input order and ranks are stable. All key loads
-    // are issued before the ranking so they overlap; the row payloads are
-    // read only when placed (fewer live registers).
+    // are issued before the ranking so they overlap; the rows (and payloads)
+    // are read only when placed (fewer live registers: reading them with the
+    // keys measured slower).
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         const int64_t i = warp_base + 32 * k + lane;
@@ -291,7 +306,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
             }
             if (!silent) st_relaxed(my, kStInc | (uint64_t)(prefix + run));
         }
-        S.gstart[d] = (int64_t)offs[d] + prefix;
+        S.gstart[d] = (int64_t)off_d + prefix;
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the 256 tile counts by one warp
@@ -317,6 +332,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
             const int32_t p = S.dstart[d] + S.wcount[warp][d] + (rank[k] & 0xFFFF);
             S.keys[p] = key[k];
             S.vals[p] = vals_in[warp_base + 32 * k + lane];
+            if (PAY) S_pay[p] = pay_in[warp_base + 32 * k + lane];
             S.dig[p] = (uint8_t)d;
         }
     }
@@ -331,6 +347,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(
             if ((uint64_t)g < (uint64_t)n) {  // (always, unless a look-back gave up)
                 keys_out[g] = S.keys[p];
                 vals_out[g] = S.vals[p];
+                if (PAY) pay_out[g] = S_pay[p];
             }
         }
     }
@@ -592,6 +609,10 @@ xm_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t
     return scan_impl<int64_t>(in, out, n, total, err, s);
 }
 
+size_t onesweep_smem(bool pay) {
+    return sizeof(OnesweepSmem) + (pay ? kSortTile * sizeof(uint64_t) : 0);
+}
+
 void radix_sort_prepare() {
     static std::mutex mu;
     static bool done[64] = {};
@@ -599,8 +620,10 @@ void radix_sort_prepare() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> g(mu);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(OnesweepSmem));
+    cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)onesweep_smem(false));
+    cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)onesweep_smem(true));
     done[dev] = true;
 }
 
@@ -609,15 +632,22 @@ void radix_sort_prepare() {
 std::atomic<int> g_spin_limit{kSpinLimit};
 std::atomic<int> g_silent_tile{-1};
 
-// One pass (two tiles per SM: 64 registers, no spills; three, with spills,
-// measured slower once tiles publish their counts early).
-void onesweep_pass(int64_t ntiles, size_t smem, cudaStream_t s, const uint64_t* ki,
-                   const uint32_t* vi, int64_t n, int shift, const unsigned long long* offs,
+// One pass: two tiles of 512 threads x 8 keys per SM (64 registers, no
+// spills). Tiles of 256 x 16, 256 x 8, 384 x 12 and 512 x 12 keys, two to
+// four per SM with the rows read with the keys, measured from 3 % faster to
+// 29 % slower on the all-sky index.
+void onesweep_pass(int64_t ntiles, cudaStream_t s, const uint64_t* ki, const uint32_t* vi,
+                   const uint64_t* pi, int64_t n, int shift, const unsigned long long* offs,
                    uint64_t* status, unsigned int* counter, uint64_t* ko, uint32_t* vo,
-                   int32_t* err, const SortPlan* plan, int pass) {
-    launch_pdl(k_onesweep, dim3((unsigned)ntiles), dim3(kSortThreads), smem, s, ki, vi, n, shift,
-               offs, status, counter, ko, vo, err, plan, pass, device_stats(), g_spin_limit.load(),
-               g_silent_tile.load());
+                   uint64_t* po, int32_t* err, const SortPlan* plan, int pass) {
+    if (pi)
+        launch_pdl(k_onesweep<true>, dim3((unsigned)ntiles), dim3(kSortThreads), onesweep_smem(true),
+                   s, ki, vi, pi, n, shift, offs, status, counter, ko, vo, po, err, plan, pass,
+                   device_stats(), g_spin_limit.load(), g_silent_tile.load());
+    else
+        launch_pdl(k_onesweep<false>, dim3((unsigned)ntiles), dim3(kSortThreads), onesweep_smem(false),
+                   s, ki, vi, pi, n, shift, offs, status, counter, ko, vo, po, err, plan, pass,
+                   device_stats(), g_spin_limit.load(), g_silent_tile.load());
 }
 
 xm_status sort_guard(const int32_t* err, uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
@@ -631,8 +661,9 @@ xm_status sort_plan_init(SortPlan* plan, cudaStream_t s) {
     return XM_OK;
 }
 
-xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                     SortPlan* plan, int max_passes, int32_t* err, cudaStream_t s) {
+xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* pay, uint64_t* tk, uint32_t* tv,
+                     uint64_t* tp, int64_t n, SortPlan* plan, int max_passes, int32_t* err,
+                     cudaStream_t s) {
     if (max_passes < 1 || max_passes > 8) return set_error(XM_EINVAL, "index sort: passes");
     XM_LAUNCH("k_plan_finish", 1, 1, 0, s, k_plan_finish, plan);
     if (n <= 1) return XM_OK;  // (one key: the plan needs no pass)
@@ -646,7 +677,6 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
     unsigned long long* hist = (unsigned long long*)work;
     uint64_t* status = (uint64_t*)(hist + passes * kRadix);
     unsigned int* counters = (unsigned int*)(status + passes * st_words);
-    const size_t smem = sizeof(OnesweepSmem);
     radix_sort_prepare();
     xm_status st = XM_OK;
     cudaError_t e = cudaMemsetAsync(work, 0, bytes, s);
@@ -660,16 +690,17 @@ xm_status index_sort(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv,
         e = launch_end("k_digit_hist", s);
         if (e != cudaSuccess) st = cuda_fail(e, "k_digit_hist");
     }
-    uint64_t *ki = keys, *ko = tk;
+    uint64_t *ki = keys, *ko = tk, *pi = pay, *po = tp;
     uint32_t *vi = vals, *vo = tv;
     for (int p = 0; p < passes && st == XM_OK; p++) {
         launch_begin("k_onesweep", s);
-        onesweep_pass(ntiles, smem, s, ki, vi, n, 8 * p, hist + p * kRadix, status + p * st_words,
-                      counters + p, ko, vo, err, plan, p);
+        onesweep_pass(ntiles, s, ki, vi, pi, n, 8 * p, hist + p * kRadix, status + p * st_words,
+                      counters + p, ko, vo, po, err, plan, p);
         e = launch_end("k_onesweep", s);
         if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;
         uint32_t* u = vi; vi = vo; vo = u;
+        t = pi; pi = po; po = t;
     }
     if (st == XM_OK) st = sort_guard(err, keys, vals, tk, tv, n, s);
     dev_free(work, s);
@@ -692,7 +723,6 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     unsigned long long* hist = (unsigned long long*)work;
     uint64_t* status = (uint64_t*)(hist + passes * kRadix);
     unsigned int* counters = (unsigned int*)(status + passes * st_words);
-    const size_t smem = sizeof(OnesweepSmem);
     radix_sort_prepare();
     xm_status st = XM_OK;
     cudaError_t e = cudaMemsetAsync(work, 0, bytes, s);
@@ -709,8 +739,8 @@ xm_status radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t*
     }
     for (int p = 0; p < passes && st == XM_OK; p++) {
         launch_begin("k_onesweep", s);
-        onesweep_pass(ntiles, smem, s, ki, vi, n, begin_bit + 8 * p, hist + p * kRadix,
-                      status + p * st_words, counters + p, ko, vo, err, nullptr, p);
+        onesweep_pass(ntiles, s, ki, vi, nullptr, n, begin_bit + 8 * p, hist + p * kRadix,
+                      status + p * st_words, counters + p, ko, vo, nullptr, err, nullptr, p);
         e = launch_end("k_onesweep", s);
         if (e != cudaSuccess) { st = cuda_fail(e, "k_onesweep"); break; }
         uint64_t* t = ki; ki = ko; ko = t;

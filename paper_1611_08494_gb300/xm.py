@@ -75,7 +75,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_uint64), ("rechecked", ctypes.c_uint64),
                 ("flipped", ctypes.c_uint64), ("members", ctypes.c_uint64),
                 ("tie_resolved", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("sort_key_passes", ctypes.c_uint64)]
+                ("sort_key_passes", ctypes.c_uint64), ("sort_pay_passes", ctypes.c_uint64)]
 
 
 def _sig(name, res, *args):

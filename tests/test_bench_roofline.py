@@ -17,11 +17,13 @@ def test_dominant_kernel_and_arithmetic(monkeypatch):
     monkeypatch.setattr(bench, "traffic_record", lambda k: 1.5e7 if k == "k_onesweep" else None)
     steps, n_a, n_b = 2, 1000, 5_000_000
     # two steps, four planned passes over n_b keys each, five launches a step
-    st = {"sort_key_passes": steps * 4 * n_b, "candidates": 40_000}
+    st = {"sort_key_passes": steps * 4 * n_b, "sort_pay_passes": steps * 4 * n_b,
+          "candidates": 40_000}
     prof = {"k_onesweep": (0.5, 10), "k_scan_fp32_count": (0.3, 2), "k_gather_b": (0.1, 2)}
     r = bench.roofline(prof, st, steps, n_a, n_b, total_ms=2.0, region=REGION)
     assert r["kernel"] == "k_onesweep"
-    alg = 24.0 * steps * 4 * n_b / 10  # 8 B key + 4 B row, read and written, per key and pass
+    # 8 B key + 4 B row + 8 B offsets, read and written, per key and pass
+    alg = 40.0 * steps * 4 * n_b / 10
     assert r["algorithmic_bytes"] == pytest.approx(alg)
     assert r["ms_per_launch"] == pytest.approx(0.05)
     assert r["achieved"] == pytest.approx(alg / 0.05e-3 / 1e9)
@@ -51,10 +53,11 @@ def test_dominant_kernel_and_arithmetic(monkeypatch):
 
 def test_fallback_peak_is_named(monkeypatch):
     monkeypatch.setattr(bench, "load_peaks", lambda: {"hbm_gbs": 6800.0, "_source": "fallback"})
-    r = bench.roofline({"k_gather_b": (0.2, 2)}, {"sort_key_passes": 0, "candidates": 0}, 2,
+    r = bench.roofline({"k_gather_b": (0.2, 2)}, {"sort_key_passes": 0, "sort_pay_passes": 0,
+                                                   "candidates": 0}, 2,
                        10, 1000, 1.0, REGION)
     assert r["peak_source"] == "of fallback" and r["peak"] == 6800.0
-    assert r["algorithmic_bytes"] == 1000 * 48
+    assert r["algorithmic_bytes"] == 1000 * 36
 
 
 def test_traffic_record_follows_the_sources(tmp_path, monkeypatch):

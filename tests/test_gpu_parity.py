@@ -479,6 +479,7 @@ def test_index_sort_plan(xm, case):
                        build_fp64=prec == "fp64")
         keys = xm.stats()["sort_key_passes"]  # the index sort's alone
         assert keys % n_b == 0 and keys // n_b <= max_passes
+        assert xm.stats()["sort_pay_passes"] == keys  # each key carries its offsets
         res = xm.Result(idx, _cuda(a_lon), _cuda(a_lat), precision=_prec(xm, prec), shape=0,
                         a=2.0, selection=xm.SEL_ALL | xm.SEL_BEST)
         check_pairs(res, ref)
