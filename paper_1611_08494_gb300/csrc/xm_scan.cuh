@@ -955,9 +955,14 @@ constexpr size_t kScanSmem = sizeof(ScanWarpSmem) * kScanWarps;
 constexpr int kSrcMaxRec = 48;  // records a lane takes on; more go to k_scan
 constexpr int kSrcStage = 64;   // member records staged per warp
 
+constexpr int kSrcBuf = 128;    // records of a chunk loaded together
+
 struct SrcWarpSmem {
+    BRec buf[kSrcBuf];  // the chunk's records, lane after lane
     MemberRec rec[kSrcStage];
     ACold cold[32];  // float64 part of each lane's source
+    int32_t first[33];       // first record of each lane in buf (prefix)
+    int32_t lo0[32], lo1[32], n0[32];  // each lane's rows
     uint8_t who[kSrcStage];  // lane of each staged record
     int32_t drop[32];        // a member of the lane's source did not fit the arena
 };
@@ -1015,8 +1020,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan_src(ScanArgs P, int32_
     unsigned int next = 0;
     if (lane == 0) next = atomicAdd(P.queue, 1u);
     for (;;) {
-        const int64_t first = (int64_t)__shfl_sync(0xffffffffu, next, 0) * 32;
-        if (first >= P.nA) break;  // whole warp
+        const int64_t this_first = (int64_t)__shfl_sync(0xffffffffu, next, 0) * 32;
+        if (this_first >= P.nA) break;  // whole warp
         if (lane == 0) next = atomicAdd(P.queue, 1u);
         W.drop[lane] = 0;
 
@@ -1027,8 +1032,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan_src(ScanArgs P, int32_
         int32_t lo0 = 0, lo1 = 0;  // first rows (rows fit 31 bits)
         uint32_t klo0 = 0, khi0 = 0, klo1 = 0, khi1 = 0;
         int32_t z0 = 0, z1 = 0;
-        if (first + lane < P.nA) {
-            const int64_t s = first + lane;
+        if (this_first + lane < P.nA) {
+            const int64_t s = this_first + lane;
             ACold C;
             if (same_region) {
                 double lon, lat, gamma;
@@ -1084,18 +1089,43 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan_src(ScanArgs P, int32_
             if (!mine) defer[atomicAdd(n_defer, 1)] = (int32_t)s;
         }
 
-        // ---- records: the warp steps through the lanes' records together,
-        // one per lane and step, the next one loaded while this one is tested
-        // (loading more at once measured slower: the unrolled steps run
-        // whether or not their lanes have records). Keys are the bit patterns
-        // of the float32 separations (non-negative, so ordered as integers).
+        // ---- records: the warp loads the chunk's records together (32 per
+        // round, flattened over the lanes, so their loads are in flight at
+        // once) into shared memory, kSrcBuf at most; then every lane tests
+        // its own, a step per record (records past the buffer are read from
+        // memory). Keys are the bit patterns of the float32 separations
+        // (non-negative, so ordered as integers).
+        if (!mine) nrec = 0;
+        int incl = nrec;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int my_first = incl - nrec;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        W.first[lane] = my_first;
+        if (lane == 31) W.first[32] = total;
+        W.lo0[lane] = lo0;
+        W.lo1[lane] = lo1;
+        W.n0[lane] = n0;
+        __syncwarp();
+        const int nbuf = min(total, kSrcBuf);
+        for (int c = lane; c < nbuf; c += 32) {
+            int ol = 0;  // last lane whose first record is <= c
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (W.first[ol + step] <= c) ol += step;
+            const int jj = c - W.first[ol];
+            const int32_t row = jj < W.n0[ol] ? W.lo0[ol] + jj : W.lo1[ol] + (jj - W.n0[ol]);
+            W.buf[c] = load_brec(G.rec + row);
+        }
+        __syncwarp();
         int cnt = 0;
         int32_t m1 = 0x7F800000, m2 = 0x7F800000;  // smallest and second smallest key
         int32_t b1 = 0x7fffffff;
         int j = 0, cur = -1;
         ItemTerms T;
-        BRec nb;
-        if (mine && nrec > 0) nb = load_brec(G.rec + (n0 > 0 ? lo0 : lo1));
         int staged = 0;  // (warp-uniform)
         auto flush = [&]() {
             __syncwarp();
@@ -1109,13 +1139,13 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_scan_src(ScanArgs P, int32_
             staged = 0;
             __syncwarp();
         };
-        while (__any_sync(0xffffffffu, mine && j < nrec)) {
+        while (__any_sync(0xffffffffu, j < nrec)) {
             int32_t key = -1, brow = 0;  // key >= 0: the record is a member
-            if (mine && j < nrec) {
-                const BRec b = nb;
+            if (j < nrec) {
                 const int it = j < n0 ? 0 : 1;
+                const BRec b = my_first + j < kSrcBuf ? W.buf[my_first + j]
+                                                      : load_brec(G.rec + (it ? lo1 + (j - n0) : lo0 + j));
                 j++;
-                if (j < nrec) nb = load_brec(G.rec + (j < n0 ? lo0 + j : lo1 + (j - n0)));
                 if (b.ra_key >= (it ? klo1 : klo0) && b.ra_key <= (it ? khi1 : khi0)) {
                     if (it != cur) {
                         cur = it;
