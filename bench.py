@@ -319,6 +319,7 @@ def nvtx_pop():
 KERNEL_SOURCES = {
     "k_onesweep": ("xm_sort.cu", "xm_internal.cuh"),
     "k_scan_fp32_count": ("xm_scan.cuh", "xm_internal.cuh"),
+    "k_scan_src": ("xm_scan.cuh", "xm_internal.cuh"),
     "k_gather_b": ("xm_index.cu", "xm_internal.cuh"),
     "k_ingest_b": ("xm_index.cu", "xm_internal.cuh"),
 }
@@ -441,7 +442,8 @@ def run_ours(args):
         e2e = e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a)
 
     roof = roofline(prof, st_p, prof_steps, n_a, n_b, sum(ms_p), d["region"])
-    scan_roof = kernel_roofline("k_scan_fp32_count", prof, st_p, prof_steps, n_a, n_b, d["region"])
+    # the count pass: its sparse form (one lane per source) where it ran
+    scan_roof = kernel_roofline(count_kernel(prof), prof, st_p, prof_steps, n_a, n_b, d["region"])
     del dev, d
     torch.cuda.empty_cache()
 
@@ -799,7 +801,7 @@ def c2_leg(args, xm, torch, measured):
            "fp64_a_per_s": n_a / (statistics.median(ms64) / 1e3),
            "kernels_ms_per_step": {kk: round(v[0] / 10, 4) for kk, v in
                                    sorted(prof.items(), key=lambda kv: -kv[1][0])[:10]}}
-    scan = prof.get("k_scan_fp32_count")
+    scan = prof.get(count_kernel(prof))
     if scan:
         cand = st_p["candidates"] / 10
         t = scan[0] / scan[1] * 1e-3
@@ -810,7 +812,7 @@ def c2_leg(args, xm, torch, measured):
                                   "peak_tflops": measured["fp32_fma_tflops"],
                                   "frac": flops / t / 1e12 / measured["fp32_fma_tflops"],
                                   "peak_source": "of measured (xm_measure_peak)"}
-        out["count_pass_hbm"] = kernel_roofline("k_scan_fp32_count", prof, st_p, 10, n_a, n_b, reg)
+        out["count_pass_hbm"] = kernel_roofline(count_kernel(prof), prof, st_p, 10, n_a, n_b, reg)
     out["sort_roofline"] = kernel_roofline("k_onesweep", prof, st_p, 10, n_a, n_b, reg)
     out["picks"] = pick_leg(xm, torch, step, stream)
     del cols, reg
@@ -908,7 +910,7 @@ def c4_leg(args, xm, torch, measured):
     if "k_scan_fp32_count" in prof:
         t_ms, nl = prof["k_scan_fp32_count"]
         cols = sum(q["lon"].numel() * sum(1 for v in q["region"].values() if hasattr(v, "numel"))
-                   for q in reqs)
+                   for q in d["requests"])
         alg = total_a * 32 + 8 * cols + 12 * st["candidates"]
         peaks = load_peaks()
         fp32 = measured["fp32_fma_tflops"]
@@ -1089,7 +1091,8 @@ def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, region):
                  index sort planned to fewer passes launches the rest empty),
                  and 8 B more each way for keys that carry a payload (the
                  index sort carries each record's float32 offsets);
-    k_scan_fp32_count  per A 16 B position + 8 B per region column given per
+    k_scan_fp32_count, k_scan_src (the count pass, warp-cooperative or one
+                 lane per source)  per A 16 B position + 8 B per region column given per
                  source + 16 B best pair, per candidate 12 B (offsets + RA
                  key);
     k_prep_a     per A 16 B position (+ region columns) read, 88 B of
@@ -1099,13 +1102,19 @@ def algorithmic_bytes(kernel, st, steps, launches, n_a, n_b, region):
     cols = sum(1 for k in ("a_col", "b_col", "pa_col") if region.get(k) is not None)
     if kernel == "k_onesweep":
         return (24.0 * st["sort_key_passes"] + 16.0 * st.get("sort_pay_passes", 0)) / launches
-    if kernel in ("k_scan_fp32_count", "k_scan_fp64_count"):
+    if kernel in ("k_scan_fp32_count", "k_scan_fp64_count", "k_scan_src"):
         return (n_a * (16 + 8 * cols + 16) + st["candidates"] / steps * 12) * steps / launches
     if kernel == "k_prep_a":
         return n_a * (16 + 8 * cols + 88) * steps / launches
     if kernel == "k_gather_b":
         return n_b * (8 + 4 + 8 + 16) * steps / launches
     return None
+
+
+def count_kernel(prof):
+    """The count pass's kernel: the sparse form where the library ran it
+    (the warp-cooperative pass then only takes the sources it left)."""
+    return "k_scan_src" if "k_scan_src" in prof else "k_scan_fp32_count"
 
 
 def kernel_roofline(name, prof, st, steps, n_a, n_b, region):
