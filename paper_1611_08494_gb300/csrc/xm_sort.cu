@@ -456,24 +456,36 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
 // earlier tiles by a decoupled look-back in which one warp reads 32
 // predecessors' words per step (bounded like the sort's; a timeout sets
 // kErrTimeout in *err). The last tile writes the total.
+// Elements move between global memory and the threads through shared memory
+// (padded by one word per thread's run), so every global load and store is
+// warp-contiguous while each thread scans kScanItems consecutive elements.
+__device__ __forceinline__ int scan_pad(int e) { return e + (e >> 4); }
+
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_chained(
     const T* __restrict__ in, int64_t n, int64_t* __restrict__ out, int64_t* __restrict__ total,
     uint64_t* status, unsigned int* tile_counter, int32_t* err) {
     pdl_wait();
+    static_assert(kScanItems == 16, "one pad word per 16 elements");
+    __shared__ int64_t xs[kScanTile + kScanTile / 16];
     __shared__ int64_t warp_tot[kScanThreads / 32];
     __shared__ int64_t tile_prefix;
     __shared__ unsigned int tile_s;
     if (threadIdx.x == 0) tile_s = atomicAdd(tile_counter, 1u);
     __syncthreads();
     const int64_t tile = tile_s;
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int64_t tbase = tile * kScanTile;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const int e = k * kScanThreads + threadIdx.x;
+        xs[scan_pad(e)] = tbase + e < n ? (int64_t)in[tbase + e] : 0;
+    }
+    __syncthreads();
     int64_t v[kScanItems];
     int64_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        const int64_t i = base + k;
-        v[k] = i < n ? (int64_t)in[i] : 0;
+        v[k] = xs[scan_pad(threadIdx.x * kScanItems + k)];
         sum += v[k];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -534,9 +546,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chained(
     int64_t run = tile_prefix + woff + incl - sum;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        const int64_t i = base + k;
-        if (i < n) out[i] = run;
+        xs[scan_pad(threadIdx.x * kScanItems + k)] = run;
         run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const int e = k * kScanThreads + threadIdx.x;
+        if (tbase + e < n) out[tbase + e] = xs[scan_pad(e)];
     }
 }
 
