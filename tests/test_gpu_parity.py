@@ -236,6 +236,50 @@ def _region_points(lon0, lat0, theta_deg, xy):
     return synth.destination(np.full(len(xy), lon0), np.full(len(xy), lat0), rho, bearing)
 
 
+def _band_points(g, shape, a, b, n_ang=4):
+    """Points at q = 1 +- {1e-3, 1e-5, 1e-7} on a region of semi-axes (a, b)
+    (its frame: x along a)."""
+    ang = g.uniform(0, 2 * np.pi, n_ang)
+    pts = []
+    for eps in (1e-3, 1e-5, 1e-7):
+        for sgn in (-1, 1):
+            f = 1 + sgn * eps
+            if shape == 2:  # on the rectangle's edges
+                pts += [[a * f, b * 0.5], [a * 0.3, -b * f], [a * f, b * f]]
+            else:  # on the ellipse (q = f^2); a circle's points a hair apart in
+                # radius, so no two separations tie
+                pts += [[a * f * (1 + 1e-8 * k) * np.cos(t), b * f * (1 + 1e-8 * k) * np.sin(t)]
+                        for k, t in enumerate(ang)]
+    return np.array(pts)
+
+
+@pytest.mark.parametrize("zone_height", [5.0, 30.0, 120.0])
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_guard_band_stress_fixed_regions(xm, shape, zone_height):
+    """The same near-boundary points around fixed regions (2.5 x 1.5 arcsec)
+    at three zone heights: at 30 and 120 arcsec the regions are small
+    against the zones and the count pass takes its one-lane-per-source form,
+    whose guard band hands these cases to its float64 recheck; at 5 arcsec
+    the warp-cooperative scan does."""
+    g = synth.rng(700 + shape)
+    n = 80
+    lon0, lat0 = synth.uniform_box(g, n, 0.0, 360.0, -89.9, 89.9)
+    a_sz, b_sz = 2.5, (1.5 if shape else 2.5)
+    pa = 37.0
+    b_lon, b_lat = [], []
+    for i in range(n):
+        lo, la = _region_points(lon0[i], lat0[i], pa, _band_points(g, shape, a_sz, b_sz))
+        b_lon.append(lo); b_lat.append(la)
+    d = dict(a_lon=lon0, a_lat=lat0, b_lon=np.concatenate(b_lon), b_lat=np.concatenate(b_lat),
+             a_frame=0, b_frame=0, region=dict(shape=shape, a=a_sz, b=b_sz, pa=pa))
+    ref = oracle_ref(d)
+    xm.reset_stats()
+    _, res = run(xm, d, "fp32", zone_height=zone_height)
+    check_pairs(res, ref)
+    check_best(res, ref, n)
+    assert xm.stats()["rechecked"] > 0
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", [0, 1, 2])
 def test_guard_band_stress(xm, prec, shape):
