@@ -209,6 +209,11 @@ XM_API xm_status xm_prof_entry(int32_t i, const char** kernel, double* total_ms,
  * XM_ECUDA. */
 XM_API xm_status xm_build_index(const xm_columns* B, const xm_index_opts* opts, void* stream,
                                 xm_index** out);
+/* Frees an index. Its device memory returns to the pool in the order of the
+ * stream it was built on, which must still exist: work queued on other
+ * streams that reads the index (matches, batches, a server's slots) must be
+ * ordered before that point, e.g. by making the build stream wait on an
+ * event recorded after it. NULL is a no-op. */
 XM_API xm_status xm_index_free(xm_index* index);
 /* n sources, zones, zone height (arcsec) and device bytes held. */
 XM_API xm_status xm_index_info(const xm_index* index, int64_t* n, int64_t* zones,

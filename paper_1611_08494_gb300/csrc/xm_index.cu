@@ -372,6 +372,7 @@ extern "C" xm_status xm_build_index(const xm_columns* B, const xm_index_opts* op
     xm_index* X = new (std::nothrow) xm_index();
     if (!X) return set_error(XM_ENOMEM, "xm_build_index: host allocation");
     X->device = dev;
+    X->stream = s;
     X->frame = B->frame;
     X->n = n;
     X->nz = (int32_t)ceil(648000.0 / h_as - 1e-9);  // equal zones of height <= requested
@@ -533,9 +534,11 @@ xm_status xm::index_build_status(int32_t bits) {
     return XM_OK;
 }
 
+// The index's memory returns to the pool in the order of the stream it was
+// built on, after whatever the caller queued there.
 extern "C" xm_status xm_index_free(xm_index* X) {
     if (!X) return XM_OK;
-    cudaStream_t s = nullptr;
+    cudaStream_t s = X->stream;
     dev_free(X->rec, s);
     dev_free(X->pos, s);
     dev_free(X->px, s);

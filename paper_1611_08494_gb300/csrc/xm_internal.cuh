@@ -595,6 +595,7 @@ struct xm_index {
     int64_t lut_n;
     int64_t bytes;
     int32_t* build_err;  // error bits of a build whose check was deferred (else NULL)
+    cudaStream_t stream;  // the stream it was built on (its memory is freed in its order)
     xm::IndexGeom geom() const {
         return xm::IndexGeom{rec, pos, px, py, pz, zones, zhot, lut, nz, h, (float)h};
     }
