@@ -173,6 +173,40 @@ def oracle_time(smp, nthreads):
     return time.perf_counter() - t
 
 
+def pin_to_gpu_local_cpus(device):
+    """Restricts this process to the CPU cores the GPU is attached to (its
+    PCI device's local_cpulist), when that is known and overlaps the cores
+    the process may use, so pinned host memory allocated afterwards lies on
+    the GPU's own memory node. Returns a one-line account of what was done."""
+    import torch
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+        out = subprocess.run(["nvidia-smi", "--query-gpu=uuid,pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout
+        bus = None
+        for line in out.splitlines():
+            u, b = [x.strip() for x in line.split(",")]
+            if u.lower().endswith(uuid.lower().replace("gpu-", "")) or len(out.splitlines()) == 1:
+                bus = b
+        if not bus:
+            return "unchanged: the GPU's PCI address is unknown"
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        allowed = os.sched_getaffinity(0)
+        use = cpus & allowed
+        if not use:
+            return f"unchanged: no allowed core is local to the GPU ({path})"
+        os.sched_setaffinity(0, use)
+        return f"{len(use)} of {len(allowed)} allowed cores, local to the GPU ({bus})"
+    except Exception as e:  # (no nvidia-smi, no sysfs entry: leave the affinity)
+        return f"unchanged: {type(e).__name__}"
+
+
 def host_threads():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
@@ -343,6 +377,8 @@ def run_ours(args):
 
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    # pinned host buffers (the end-to-end legs) on the GPU's own memory node
+    affinity = pin_to_gpu_local_cpus(local)
     from paper_1611_08494_gb300 import xm
 
     measured = xm.measure_peaks()  # this GPU's float32 / float64 FMA and read rates
@@ -463,7 +499,7 @@ def run_ours(args):
                          "each step",
                    "index_check": "deferred to the match's synchronisation",
                    "pairs": n_pairs, "join_rows": n_rows},
-        "e2e": e2e,
+        "e2e": e2e and dict(e2e, host_cpus=affinity),
         "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": statistics.mean(ms64),
                       "fp32_recheck_speedup": v64 and value / world / v64},
         "gpu_launches": int(launches),
@@ -527,34 +563,46 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     v_ser = n_a * n_ser / (sum(ms_ser) / 1e3)
 
     # pipelined as a throughput-bound user would run it, through the same
-    # calls with host buffers: step k's index build (which copies B in) runs
-    # on stream k % 3 and is issued two steps ahead, its match and join (the
-    # match copies A in and holds the host at its pair count) follow there,
-    # and its result copy goes to a fourth stream, so B copies in, compute and
-    # results out of neighbouring steps overlap. A step's objects live until
-    # its copy out has run (their memory is freed in their stream's order
-    # after a wait on it). Every step still copies all of its inputs in and
-    # its result out; the clock covers the whole run.
-    streams = [torch.cuda.Stream() for _ in range(3)]
-    out_stream = torch.cuda.Stream()
+    # calls with host buffers: step k's index build (which copies B in) is
+    # issued two steps ahead on a low-priority stream, its match and join
+    # (the match copies A in and holds the host at its pair count) on a
+    # high-priority stream that waits for the build, and its result copy
+    # goes to a further stream: B copies in, results out and the builds of
+    # later steps fill the time the match and join of the current one leave,
+    # and never delay them (the GPU schedules the high-priority stream's
+    # blocks first). A step's objects live until its copy out has run (their
+    # memory is freed in their streams' order after a wait on it). Every step
+    # still copies all of its inputs in and its result out; the clock covers
+    # the whole run.
+    lo_pri, hi_pri = torch.cuda.Stream.priority_range()
+    bstreams = [torch.cuda.Stream(priority=lo_pri) for _ in range(3)]
+    mstreams = [torch.cuda.Stream(priority=hi_pri) for _ in range(3)]
+    out_stream = torch.cuda.Stream(priority=hi_pri)
+    streams = bstreams + mstreams
     keep = {}
     out_bufs = {}
 
     def build(k):
-        with torch.cuda.stream(streams[k % 3]):
-            return xm.Index(host["b_lon"], host["b_lat"], frame=d["b_frame"], ids=host["b_id"],
-                            zone_height_arcsec=zone_h, deferred_check=True)
+        bs = bstreams[k % 3]
+        with torch.cuda.stream(bs):
+            idx = xm.Index(host["b_lon"], host["b_lat"], frame=d["b_frame"], ids=host["b_id"],
+                           zone_height_arcsec=zone_h, deferred_check=True)
+            built = torch.cuda.Event()
+            built.record(bs)
+        return idx, built
 
-    def finish(k, idx):
-        st = streams[k % 3]
-        with torch.cuda.stream(st):
+    def finish(k, ahead_k):
+        idx, built = ahead_k
+        ms = mstreams[k % 3]
+        ms.wait_event(built)
+        with torch.cuda.stream(ms):
             res = xm.Result(idx, host["a_lon"], host["a_lat"], frame=d["a_frame"],
                             precision=xm.PREC_FP32, selection=xm.SEL_ALL | xm.SEL_BEST,
                             **d["region"])
             rows = res.join("or")
             srcs = [rows.a_row, rows.b_row, rows.sep, res.best_b, res.best_sep]
             done = torch.cuda.Event()
-            done.record(st)
+            done.record(ms)
         out_stream.wait_event(done)
         slot = k % 3
         key = tuple(t.numel() for t in srcs)
@@ -565,10 +613,11 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
                 dst.copy_(src, non_blocking=True)
             copied = torch.cuda.Event()
             copied.record(out_stream)
-        keep[k] = (idx, res, rows, srcs, copied, st)
+        keep[k] = (idx, res, rows, srcs, copied, (bstreams[k % 3], ms))
         old = keep.pop(k - 2, None)
-        if old is not None:  # its memory is released on its stream after its copy out
-            old[5].wait_event(old[4])
+        if old is not None:  # its memory is released in its streams after its copy out
+            for st in old[5]:
+                st.wait_event(old[4])
             del old
 
     def run(n):
@@ -578,12 +627,13 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
                 ahead[k + 2] = build(k + 2)
             finish(k, ahead.pop(k))
         for k in sorted(keep):
-            keep[k][5].wait_event(keep[k][4])
+            for st in keep[k][5]:
+                st.wait_event(keep[k][4])
         keep.clear()
 
     run(3)
     torch.cuda.synchronize()
-    n_pipe = max(4, args.steps // 4)
+    n_pipe = max(6, args.steps // 2)
     cur = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
@@ -598,9 +648,10 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     del host
     return {"value": n_a * n_pipe / (ms_pipe / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
-            "mode": "steps on three streams, each step's index build (and B copy in) issued two "
-                    "steps ahead, result copies out on a fourth stream: copies in, compute and "
-                    "copies out of neighbouring steps overlap",
+            "mode": "each step's index build (and B copy in) issued two steps ahead on a "
+                    "low-priority stream, its match and join on a high-priority stream that waits "
+                    "for it, result copies out on another stream: copies in, compute and copies "
+                    "out of neighbouring steps overlap",
             "serial_value": v_ser, "serial_mode": "one step at a time, events around each step"}
 
 
