@@ -93,40 +93,77 @@ static void keep_pool_cached() {
     done[dev] = true;
 }
 
-// Per host thread: a pinned staging area for small device -> host reads.
+// Per host thread: a pinned, mapped staging area for small device -> host
+// reads. A kernel writes the values into it instead of a device-to-host
+// copy: such copies from all streams queue in order on one copy engine, so a
+// count read would wait behind whatever large result copies the caller has
+// queued on other streams (a pipelined caller copying one step's results out
+// while the next step's match reads its pair count).
 namespace {
 constexpr size_t kStageBytes = 4096;
 struct Stage {
-    unsigned char* p = nullptr;
+    unsigned char* p = nullptr;   // host address
+    unsigned char* dp = nullptr;  // device address of the same bytes
     bool tried = false;
     ~Stage() {
         if (p) cudaFreeHost(p);
     }
 };
 thread_local Stage t_stage;
-unsigned char* stage_area() {
+Stage* stage_area() {
     if (!t_stage.tried) {
         t_stage.tried = true;
         void* p = nullptr;
-        if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocDefault) == cudaSuccess)
+        void* dp = nullptr;
+        if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
+            cudaHostGetDevicePointer(&dp, p, 0) == cudaSuccess) {
             t_stage.p = (unsigned char*)p;
-        else
-            cudaGetLastError();  // no pinned memory: plain copies below
+            t_stage.dp = (unsigned char*)dp;
+        } else {
+            if (p) cudaFreeHost(p);
+            cudaGetLastError();  // no mapped pinned memory: plain copies below
+        }
     }
-    return t_stage.p;
+    return t_stage.p ? &t_stage : nullptr;
+}
+
+// The queued small reads, copied byte by byte into the mapped staging area.
+struct StageCopies {
+    const unsigned char* src[8];
+    uint32_t off[8], bytes[8];
+    int n;
+};
+
+__global__ void k_stage_copy(StageCopies c, unsigned char* __restrict__ dst) {
+    for (int k = 0; k < c.n; k++)
+        for (uint32_t b = threadIdx.x; b < c.bytes[k]; b += blockDim.x) dst[c.off[k] + b] = c.src[k][b];
+    __threadfence_system();
 }
 }  // namespace
 
 cudaError_t HostReads::add(void* host_dst, const void* dev_src, size_t bytes) {
-    unsigned char* st = stage_area();
+    Stage* st = stage_area();
     const size_t off = (used_ + 15) & ~size_t(15);
     if (!st || n_ == 8 || off + bytes > kStageBytes)  // (blocks until the copy is done)
         return cudaMemcpyAsync(host_dst, dev_src, bytes, cudaMemcpyDeviceToHost, s_);
-    const cudaError_t e = cudaMemcpyAsync(st + off, dev_src, bytes, cudaMemcpyDeviceToHost, s_);
-    if (e != cudaSuccess) return e;
-    items_[n_++] = Item{host_dst, off, bytes};
+    items_[n_++] = Item{host_dst, dev_src, off, bytes};
     used_ = off + bytes;
+    launched_ = false;
     return cudaSuccess;
+}
+
+cudaError_t HostReads::launch() {
+    if (launched_ || n_ == 0) return cudaSuccess;
+    StageCopies c{};
+    c.n = n_;
+    for (int i = 0; i < n_; i++) {
+        c.src[i] = (const unsigned char*)items_[i].src;
+        c.off[i] = (uint32_t)items_[i].off;
+        c.bytes[i] = (uint32_t)items_[i].bytes;
+    }
+    k_stage_copy<<<1, 128, 0, s_>>>(c, stage_area()->dp);
+    launched_ = true;
+    return cudaGetLastError();
 }
 
 namespace {
@@ -134,6 +171,8 @@ thread_local cudaEvent_t t_read_ev = nullptr;
 }
 
 cudaError_t HostReads::mark() {
+    const cudaError_t el = launch();
+    if (el != cudaSuccess) return el;
     if (!t_read_ev && cudaEventCreateWithFlags(&t_read_ev, cudaEventDisableTiming) != cudaSuccess) {
         t_read_ev = nullptr;
         cudaGetLastError();
@@ -145,11 +184,13 @@ cudaError_t HostReads::mark() {
 }
 
 cudaError_t HostReads::sync() {
-    const cudaError_t e = marked_ ? cudaEventSynchronize(t_read_ev) : cudaStreamSynchronize(s_);
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return e;
+    e = marked_ ? cudaEventSynchronize(t_read_ev) : cudaStreamSynchronize(s_);
     marked_ = false;
     if (e != cudaSuccess) return e;
-    unsigned char* st = stage_area();
-    for (int i = 0; i < n_; i++) memcpy(items_[i].dst, st + items_[i].off, items_[i].bytes);
+    Stage* st = stage_area();
+    for (int i = 0; i < n_; i++) memcpy(items_[i].dst, st->p + items_[i].off, items_[i].bytes);
     n_ = 0;
     used_ = 0;
     return cudaSuccess;

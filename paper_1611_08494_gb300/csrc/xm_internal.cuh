@@ -430,27 +430,33 @@ struct Side {
 Side* side_stream();
 
 // Small device -> host reads gathered behind one synchronisation: add()
-// queues an asynchronous copy into this host thread's pinned staging area
-// (a copy into pageable memory would block the host once per copy), sync()
-// waits for the stream once and hands the values out.
+// queues a read; one small kernel on the stream writes them all into this
+// host thread's pinned, mapped staging area (not a device-to-host copy: those
+// wait in order behind every such copy queued on any stream); sync() waits
+// for the stream once and hands the values out. Without mapped memory, or
+// past the area's room, a read is a plain asynchronous copy.
 class HostReads {
   public:
     explicit HostReads(cudaStream_t s) : s_(s) {}
     cudaError_t add(void* host_dst, const void* dev_src, size_t bytes);
-    // Marks the copies queued so far: sync() then waits for them only, so
+    // Marks the reads queued so far: sync() then waits for them only, so
     // work queued on the stream after mark() keeps the GPU busy meanwhile.
     cudaError_t mark();
     cudaError_t sync();
 
   private:
+    // queues the kernel that writes the reads into the staging area (once)
+    cudaError_t launch();
     struct Item {
         void* dst;
+        const void* src;
         size_t off, bytes;
     };
     cudaStream_t s_;
     size_t used_ = 0;
     int n_ = 0;
     bool marked_ = false;
+    bool launched_ = false;
     Item items_[8];
 };
 void dev_free(void* p, cudaStream_t s);

@@ -122,3 +122,38 @@ def test_sparse_count_pass_equals_the_oracle(xm, region, selection):
     # candidates and members are counted once whichever pass took a source
     st = xm.stats()
     assert st["members"] == ref["a_row"].size
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_sparse_count_pass_rotated_frames(xm, shape):
+    """A in galactic coordinates against an equatorial index: every source
+    is rotated into the index frame, and for ellipses and rectangles the
+    position angle turns with the frame at each position, so the sparse
+    pass prepares each such source's region in full (circles keep the
+    block's shared terms). Pairs, separations, counts and best pairs equal
+    the oracle's."""
+    a_lon, a_lat, b_lon, b_lat = _mix(seed=47)
+    # A's positions in galactic coordinates (the same points on the sky)
+    ga_lon, ga_lat = oracle.from_equatorial(a_lon, a_lat, oracle.GAL)
+    region = [dict(shape=0, a=2.0), dict(shape=1, a=3.0, b=1.5, pa=30.0),
+              dict(shape=2, a=2.5, b=1.0, pa=110.0)][shape]
+    ref = oracle.match(ga_lon, ga_lat, b_lon, b_lat, a_frame=oracle.GAL, b_frame=oracle.EQ,
+                       **region)
+    assert ref["border_a"].size == 0
+    bb = oracle.best(ref, ga_lon.size)
+    assert bb["near_tie"].size == 0
+    idx = xm.Index(_cuda(b_lon), _cuda(b_lat), zone_height_arcsec=ZONE_H)
+    xm.prof_enable(True)
+    try:
+        res = xm.Result(idx, _cuda(ga_lon), _cuda(ga_lat), frame=xm.GAL, precision=xm.PREC_FP32,
+                        selection=xm.SEL_ALL | xm.SEL_BEST, **region)
+        n = res.n_pairs
+        prof = xm.prof_all()
+    finally:
+        xm.prof_enable(False)
+    assert prof["k_scan_src"][1] == 1
+    assert n == ref["a_row"].size
+    np.testing.assert_array_equal(_host(res.a_row), ref["a_row"])
+    np.testing.assert_array_equal(_host(res.b_row), ref["b_row"])
+    assert np.max(np.abs(_host(res.sep) - ref["sep"])) <= SEP_TOL
+    np.testing.assert_array_equal(_host(res.best_b), bb["best_b"])
