@@ -633,7 +633,7 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
 
     run(3)
     torch.cuda.synchronize()
-    n_pipe = max(6, args.steps // 2)
+    n_pipe = max(6, args.steps)
     cur = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
@@ -645,6 +645,7 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     e1.record(cur)
     e1.synchronize()
     ms_pipe = e0.elapsed_time(e1)
+    copies = copy_rates(torch, h2d, d2h, n_a)
     del host
     return {"value": n_a * n_pipe / (ms_pipe / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
@@ -652,7 +653,53 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
                     "low-priority stream, its match and join on a high-priority stream that waits "
                     "for it, result copies out on another stream: copies in, compute and copies "
                     "out of neighbouring steps overlap",
-            "serial_value": v_ser, "serial_mode": "one step at a time, events around each step"}
+            "serial_value": v_ser, "serial_mode": "one step at a time, events around each step",
+            "steps": n_pipe, "copies": copies}
+
+
+def copy_rates(torch, h2d_bytes, d2h_bytes, n_a):
+    """This machine's host <-> device copy rates between pinned host memory and
+    the device (1 GiB each way, best of three; each way alone and both at
+    once on two streams), and the end-to-end floor they set: a step's copies
+    in and out at the rates of both at once."""
+    nb = 1 << 30
+    dev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    dev2 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    hin = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn_in, fn_out):
+        best_in = best_out = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            evs = {}
+            for name, st, fn in (("in", s_in, fn_in), ("out", s_out, fn_out)):
+                if fn is None:
+                    continue
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(st):
+                    a.record(st)
+                    fn()
+                    b.record(st)
+                evs[name] = (a, b)
+            torch.cuda.synchronize()
+            if "in" in evs:
+                best_in = max(best_in, nb / (evs["in"][0].elapsed_time(evs["in"][1]) * 1e-3) / 1e9)
+            if "out" in evs:
+                best_out = max(best_out, nb / (evs["out"][0].elapsed_time(evs["out"][1]) * 1e-3) / 1e9)
+        return best_in, best_out
+
+    cin = lambda: dev.copy_(hin, non_blocking=True)  # noqa: E731
+    cout = lambda: hout.copy_(dev2, non_blocking=True)  # noqa: E731
+    h2d_alone, _ = timed(cin, None)
+    _, d2h_alone = timed(None, cout)
+    h2d_both, d2h_both = timed(cin, cout)
+    floor_s = max(h2d_bytes / (h2d_both * 1e9), d2h_bytes / (d2h_both * 1e9))
+    del dev, dev2, hin, hout
+    return {"h2d_gbs": h2d_alone, "d2h_gbs": d2h_alone, "both_gbs": [h2d_both, d2h_both],
+            "floor_value": n_a / floor_s,
+            "floor": "a step's copies in and out at the rates of both at once, all compute hidden"}
 
 
 def pick_leg(xm, torch, step, stream):
