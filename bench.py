@@ -563,17 +563,18 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     v_ser = n_a * n_ser / (sum(ms_ser) / 1e3)
 
     # pipelined as a throughput-bound user would run it, through the same
-    # calls with host buffers: step k's index build (which copies B in) is
-    # issued two steps ahead on a low-priority stream, its match and join
-    # (the match copies A in and holds the host at its pair count) on a
-    # high-priority stream that waits for the build, and its result copy
-    # goes to a further stream: B copies in, results out and the builds of
-    # later steps fill the time the match and join of the current one leave,
-    # and never delay them (the GPU schedules the high-priority stream's
-    # blocks first). A step's objects live until its copy out has run (their
-    # memory is freed in their streams' order after a wait on it). Every step
-    # still copies all of its inputs in and its result out; the clock covers
-    # the whole run.
+    # calls with host buffers: step k's match is queued first (xm_match_async:
+    # its copy of A goes ahead on the copy queue, which runs host copies of
+    # all streams in the order they were queued), then the index build of
+    # step k + 2 (which copies B in) on a low-priority stream, then step k's
+    # wait for its pair count and its join on a high-priority stream that
+    # waited for step k's build, and its result copy on a further stream: B
+    # copies in, results out and the builds of later steps fill the time the
+    # match and join of the current one leave, and never delay them (the GPU
+    # schedules the high-priority stream's blocks first). A step's objects
+    # live until its copy out has run (their memory is released in their
+    # streams' order after a wait on it). Every step still copies all of its
+    # inputs in and its result out; the clock covers the whole run.
     lo_pri, hi_pri = torch.cuda.Stream.priority_range()
     bstreams = [torch.cuda.Stream(priority=lo_pri) for _ in range(3)]
     mstreams = [torch.cuda.Stream(priority=hi_pri) for _ in range(3)]
@@ -591,14 +592,20 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
             built.record(bs)
         return idx, built
 
-    def finish(k, ahead_k):
+    def start(k, ahead_k):
         idx, built = ahead_k
         ms = mstreams[k % 3]
         ms.wait_event(built)
         with torch.cuda.stream(ms):
-            res = xm.Result(idx, host["a_lon"], host["a_lat"], frame=d["a_frame"],
-                            precision=xm.PREC_FP32, selection=xm.SEL_ALL | xm.SEL_BEST,
-                            **d["region"])
+            return xm.Pending(idx, host["a_lon"], host["a_lat"], frame=d["a_frame"],
+                              precision=xm.PREC_FP32, selection=xm.SEL_ALL | xm.SEL_BEST,
+                              **d["region"])
+
+    def finish(k, pending):
+        ms = mstreams[k % 3]
+        with torch.cuda.stream(ms):
+            res = pending.wait()
+            idx = pending.index
             rows = res.join("or")
             srcs = [rows.a_row, rows.b_row, rows.sep, res.best_b, res.best_sep]
             done = torch.cuda.Event()
@@ -623,9 +630,10 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     def run(n):
         ahead = {0: build(0), 1: build(1) if n > 1 else None}
         for k in range(n):
+            pending = start(k, ahead.pop(k))
             if k + 2 < n:
                 ahead[k + 2] = build(k + 2)
-            finish(k, ahead.pop(k))
+            finish(k, pending)
         for k in sorted(keep):
             for st in keep[k][5]:
                 st.wait_event(keep[k][4])
@@ -650,9 +658,10 @@ def e2e_legs(args, xm, torch, d, step, flush, zone_h, n_a):
     return {"value": n_a * n_pipe / (ms_pipe / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
             "mode": "each step's index build (and B copy in) issued two steps ahead on a "
-                    "low-priority stream, its match and join on a high-priority stream that waits "
-                    "for it, result copies out on another stream: copies in, compute and copies "
-                    "out of neighbouring steps overlap",
+                    "low-priority stream, after the current step's match is queued "
+                    "(xm_match_async, so A's copy goes first); its wait and join on a "
+                    "high-priority stream that waits for the build, result copies out on another "
+                    "stream: copies in, compute and copies out of neighbouring steps overlap",
             "serial_value": v_ser, "serial_mode": "one step at a time, events around each step",
             "steps": n_pipe, "copies": copies}
 

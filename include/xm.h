@@ -26,7 +26,8 @@
  *  - Outputs are opaque handles owned by the library and released with the
  *    matching xm_*_free. Their device arrays stay valid until then.
  *  - Device memory comes from the allocator installed with xm_set_allocator,
- *    else from cudaMallocAsync on the call's stream.
+ *    else from the library's block cache in front of cudaMallocAsync on the
+ *    call's stream (xm_set_cache_limit).
  *  - Angles: longitudes/latitudes and position angles in degrees; region sizes
  *    in `size_unit_arcsec` arcseconds times `size_scale`; separations are
  *    returned in arcseconds (float64).
@@ -157,6 +158,7 @@ typedef struct {
 typedef struct xm_index xm_index;
 typedef struct xm_result xm_result;
 typedef struct xm_rows xm_rows;
+typedef struct xm_pending xm_pending;
 
 /* Per-call counters (cumulative over calls on the handle's device). */
 typedef struct {
@@ -183,6 +185,25 @@ XM_API const char* xm_version(void);
  * call's stream and ctx. */
 XM_API xm_status xm_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
                                   void (*release)(void* ptr, void* stream, void* ctx), void* ctx);
+
+/* Without an installed allocator, device blocks the library frees are kept
+ * per device for reuse by later calls instead of going back to the CUDA
+ * stream-ordered pool (taking a large block from the pool can hold the
+ * calling thread for tens of milliseconds while copies run). A kept block
+ * carries an event recorded on the freeing stream; a later allocation reuses
+ * it once that event has completed, or at once on the same stream. When the
+ * pool runs out, kept blocks go back to it and the allocation is retried.
+ *
+ * xm_set_cache_limit: at most `bytes` are kept per device (blocks past it go
+ * back to the pool, oldest first, at the next free); 0 keeps nothing; a
+ * negative value restores the default, half the device's memory.
+ * xm_free_cached: every block kept for the current device goes back to the
+ * pool, ordered on `stream` after its free point (no host wait).
+ * xm_mem_info: bytes of the current device the library holds in live
+ * objects and temporaries, and bytes kept for reuse (either may be NULL). */
+XM_API xm_status xm_set_cache_limit(int64_t bytes);
+XM_API xm_status xm_free_cached(void* stream);
+XM_API xm_status xm_mem_info(int64_t* live_bytes, int64_t* kept_bytes);
 
 /* Counters accumulated since the last reset. */
 XM_API xm_status xm_get_stats(xm_stats* out);
@@ -231,6 +252,22 @@ XM_API xm_status xm_index_info(const xm_index* index, int64_t* n, int64_t* zones
  * Errors: XM_EINVAL (bad region/opts/coordinates), XM_ENOMEM, XM_ECUDA. */
 XM_API xm_status xm_match(const xm_index* index, const xm_columns* A, const xm_region* region,
                           const xm_match_opts* opts, void* stream, xm_result** out);
+/* xm_match in two calls, for a caller with more work to queue before the
+ * match's synchronisation. xm_match_async checks the arguments and queues
+ * everything of the match up to its pair count on `stream` (for host A, the
+ * copy of A's columns comes first), then returns without waiting;
+ * xm_match_wait takes the one synchronisation and queues the rest, giving
+ * the result of xm_match. Copies of host memory queued on any stream run in
+ * the order they were queued, so an input copy queued after xm_match_async
+ * (an index build's, say) does not hold up this match's. Every pending match
+ * must be waited for exactly once, by any host thread; until then the A and
+ * region columns it was given must stay valid and unchanged, and `index`
+ * alive. An error from either call leaves nothing behind (after a failed
+ * xm_match_wait the pending match is gone). Errors: those of xm_match. */
+XM_API xm_status xm_match_async(const xm_index* index, const xm_columns* A,
+                                const xm_region* region, const xm_match_opts* opts, void* stream,
+                                xm_pending** out);
+XM_API xm_status xm_match_wait(xm_pending* pending, xm_result** out);
 /* Frees the result's device arrays in the order of the stream it was computed
  * on (work queued there that reads them runs first); that stream must still
  * exist. */

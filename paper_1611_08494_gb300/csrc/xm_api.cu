@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "xm_internal.cuh"
@@ -78,53 +79,200 @@ xm_status cuda_fail(cudaError_t e, const char* what) {
     return set_error(XM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// The default stream-ordered pool keeps freed memory cached instead of
-// returning it to the driver at every synchronisation (release threshold
-// raised once per device), so per-call temporaries cost no driver call.
-static void keep_pool_cached() {
-    static bool done[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+// ---- device memory
+//
+// Blocks the library frees are kept per device for reuse instead of going
+// back to the stream-ordered pool at once: taking a block of gigabytes from
+// the pool was measured to hold the calling thread for 10-60 ms while copies
+// ran on the copy engines (whether the pool reused freed memory or grew), and
+// a pipelined caller allocates and frees blocks of the same sizes every step.
+// A kept block carries an event recorded on the freeing stream at the free
+// point. An allocation takes the smallest kept block of at least its size
+// (and at most about twice it) that is already free on the GPU: its event has
+// completed, or it was freed on the allocating stream (stream order covers
+// it). The allocating stream waits on that event (a no-op then, and still
+// correct if a destroyed stream's handle was handed out again). Failing that
+// the block comes from the pool; when the pool has no memory left, kept
+// blocks still in use on other streams are taken (the allocating stream
+// waits for them on the GPU), and then every kept block goes back to the pool
+// before one more try. The kept total is capped (half the device's memory
+// unless xm_set_cache_limit says otherwise); past it the oldest blocks go
+// back first. While a stream is being captured into a graph its allocations
+// and frees go to the pool directly.
+namespace {
+
+struct Kept {
+    void* p;
+    size_t bytes;
+    cudaStream_t s;
+    cudaEvent_t ev;
+    bool done;  // ev known to have completed
+    uint64_t age;
+};
+
+struct DevMem {
+    std::mutex mu;
+    bool ready = false;
+    std::unordered_map<void*, size_t> live;  // blocks handed out -> size
+    std::vector<Kept> kept;
+    std::vector<cudaEvent_t> spare;
+    size_t live_bytes = 0, kept_bytes = 0, total = 0;
+    uint64_t tick = 0;
+};
+
+DevMem g_mem[64];
+std::atomic<long long> g_cache_limit{-1};  // bytes; < 0: half the device's memory
+
+size_t round_block(size_t b) {
+    if (b == 0) b = 1;
+    const size_t g = b <= (size_t(1) << 20) ? 512 : (size_t(2) << 20);
+    return (b + g - 1) / g * g;
+}
+
+size_t cache_limit(const DevMem& d) {
+    const long long l = g_cache_limit.load();
+    return l < 0 ? d.total / 2 : (size_t)l;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// First use on a device: the pool keeps what goes back to it (release
+// threshold raised) and the device's size sets the default cap.
+void mem_init(DevMem& d, int dev) {
+    if (d.ready) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t keep = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    done[dev] = true;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) cudaGetLastError();
+    d.total = tot;
+    d.ready = true;
 }
 
-// Per host thread: a pinned, mapped staging area for small device -> host
-// reads. A kernel writes the values into it instead of a device-to-host
+// Kept block i goes back to the pool, ordered after its free point on `s`.
+void give_back(DevMem& d, size_t i, cudaStream_t s) {
+    const Kept k = d.kept[i];
+    d.kept[i] = d.kept.back();
+    d.kept.pop_back();
+    d.kept_bytes -= k.bytes;
+    bool done = k.done;
+    if (!done) {
+        const cudaError_t q = cudaEventQuery(k.ev);
+        if (q == cudaSuccess) done = true;
+        else if (q != cudaErrorNotReady) cudaGetLastError();
+    }
+    if (!done && cudaStreamWaitEvent(s, k.ev, 0) != cudaSuccess) cudaGetLastError();
+    if (cudaFreeAsync(k.p, s) != cudaSuccess) cudaGetLastError();
+    d.spare.push_back(k.ev);
+}
+
+// A kept block of `need` bytes or a little more for stream `s`; with
+// `pending`, also one still in use on another stream.
+void* take(DevMem& d, size_t need, cudaStream_t s, bool pending) {
+    const size_t most = 2 * need + (size_t(1) << 20);
+    long best = -1;
+    for (size_t i = 0; i < d.kept.size(); i++) {
+        Kept& k = d.kept[i];
+        if (k.bytes < need || k.bytes > most) continue;
+        if (best >= 0 && k.bytes >= d.kept[best].bytes) continue;
+        if (!k.done && k.s != s && !pending) {
+            const cudaError_t q = cudaEventQuery(k.ev);
+            if (q == cudaSuccess) {
+                k.done = true;
+            } else {
+                if (q != cudaErrorNotReady) cudaGetLastError();
+                continue;
+            }
+        }
+        best = (long)i;
+    }
+    if (best < 0) return nullptr;
+    const Kept k = d.kept[best];
+    if (!k.done && cudaStreamWaitEvent(s, k.ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    d.kept[best] = d.kept.back();
+    d.kept.pop_back();
+    d.kept_bytes -= k.bytes;
+    d.spare.push_back(k.ev);
+    d.live[k.p] = k.bytes;
+    d.live_bytes += k.bytes;
+    return k.p;
+}
+
+void* pool_alloc(DevMem& d, size_t need, cudaStream_t s) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, need, s) != cudaSuccess) {
+        cudaGetLastError();  // clear the error state of a failed allocation
+        return nullptr;
+    }
+    d.live[p] = need;
+    d.live_bytes += need;
+    return p;
+}
+
+}  // namespace
+
+// Pinned, mapped staging areas for small device -> host reads, one per
+// HostReads object while it lives (taken from a pool, each with an event).
+// A kernel writes the values into the area instead of a device-to-host
 // copy: such copies from all streams queue in order on one copy engine, so a
 // count read would wait behind whatever large result copies the caller has
 // queued on other streams (a pipelined caller copying one step's results out
-// while the next step's match reads its pair count).
+// while the next step's match reads its pair count). An area goes back to
+// the pool with its event recorded after its last kernel, and is handed out
+// again only once that event has completed.
 namespace {
 constexpr size_t kStageBytes = 4096;
-struct Stage {
-    unsigned char* p = nullptr;   // host address
-    unsigned char* dp = nullptr;  // device address of the same bytes
-    bool tried = false;
-    ~Stage() {
-        if (p) cudaFreeHost(p);
+std::mutex g_stage_mu;
+std::vector<HostReads::Area> g_stage_free;
+
+bool take_area(HostReads::Area* out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-};
-thread_local Stage t_stage;
-Stage* stage_area() {
-    if (!t_stage.tried) {
-        t_stage.tried = true;
-        void* p = nullptr;
-        void* dp = nullptr;
-        if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
-            cudaHostGetDevicePointer(&dp, p, 0) == cudaSuccess) {
-            t_stage.p = (unsigned char*)p;
-            t_stage.dp = (unsigned char*)dp;
-        } else {
-            if (p) cudaFreeHost(p);
-            cudaGetLastError();  // no mapped pinned memory: plain copies below
+    {
+        std::lock_guard<std::mutex> g(g_stage_mu);
+        for (size_t i = 0; i < g_stage_free.size(); i++) {
+            if (g_stage_free[i].dev != dev) continue;
+            const cudaError_t q = cudaEventQuery(g_stage_free[i].ev);
+            if (q != cudaSuccess) {
+                if (q != cudaErrorNotReady) cudaGetLastError();
+                continue;
+            }
+            *out = g_stage_free[i];
+            g_stage_free[i] = g_stage_free.back();
+            g_stage_free.pop_back();
+            return true;
         }
     }
-    return t_stage.p ? &t_stage : nullptr;
+    HostReads::Area A{};
+    A.dev = dev;
+    void* p = nullptr;
+    void* dp = nullptr;
+    if (cudaHostAlloc(&p, kStageBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dp, p, 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (p) cudaFreeHost(p);
+        cudaGetLastError();  // no mapped pinned memory: plain copies instead
+        return false;
+    }
+    A.p = (unsigned char*)p;
+    A.dp = (unsigned char*)dp;
+    *out = A;
+    return true;
 }
 
 // The queued small reads, copied byte by byte into the mapped staging area.
@@ -141,14 +289,29 @@ __global__ void k_stage_copy(StageCopies c, unsigned char* __restrict__ dst) {
 }
 }  // namespace
 
+HostReads::~HostReads() {
+    if (!have_) return;
+    // a kernel still to run writes into the area: its event marks the end
+    if (launched_ && !synced_ && cudaEventRecord(area_.ev, s_) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(s_);
+    }
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    g_stage_free.push_back(area_);
+}
+
 cudaError_t HostReads::add(void* host_dst, const void* dev_src, size_t bytes) {
-    Stage* st = stage_area();
+    if (!tried_) {
+        tried_ = true;
+        have_ = take_area(&area_);
+    }
     const size_t off = (used_ + 15) & ~size_t(15);
-    if (!st || n_ == 8 || off + bytes > kStageBytes)  // (blocks until the copy is done)
+    if (!have_ || n_ == 8 || off + bytes > kStageBytes)  // (blocks until the copy is done)
         return cudaMemcpyAsync(host_dst, dev_src, bytes, cudaMemcpyDeviceToHost, s_);
     items_[n_++] = Item{host_dst, dev_src, off, bytes};
     used_ = off + bytes;
     launched_ = false;
+    synced_ = false;
     return cudaSuccess;
 }
 
@@ -161,24 +324,16 @@ cudaError_t HostReads::launch() {
         c.off[i] = (uint32_t)items_[i].off;
         c.bytes[i] = (uint32_t)items_[i].bytes;
     }
-    k_stage_copy<<<1, 128, 0, s_>>>(c, stage_area()->dp);
+    k_stage_copy<<<1, 128, 0, s_>>>(c, area_.dp);
     launched_ = true;
     return cudaGetLastError();
-}
-
-namespace {
-thread_local cudaEvent_t t_read_ev = nullptr;
 }
 
 cudaError_t HostReads::mark() {
     const cudaError_t el = launch();
     if (el != cudaSuccess) return el;
-    if (!t_read_ev && cudaEventCreateWithFlags(&t_read_ev, cudaEventDisableTiming) != cudaSuccess) {
-        t_read_ev = nullptr;
-        cudaGetLastError();
-        return cudaSuccess;  // sync() waits for the whole stream instead
-    }
-    const cudaError_t e = cudaEventRecord(t_read_ev, s_);
+    if (!have_) return cudaSuccess;  // sync() waits for the whole stream
+    const cudaError_t e = cudaEventRecord(area_.ev, s_);
     marked_ = e == cudaSuccess;
     return e;
 }
@@ -186,11 +341,11 @@ cudaError_t HostReads::mark() {
 cudaError_t HostReads::sync() {
     cudaError_t e = launch();
     if (e != cudaSuccess) return e;
-    e = marked_ ? cudaEventSynchronize(t_read_ev) : cudaStreamSynchronize(s_);
+    e = marked_ ? cudaEventSynchronize(area_.ev) : cudaStreamSynchronize(s_);
     marked_ = false;
     if (e != cudaSuccess) return e;
-    Stage* st = stage_area();
-    for (int i = 0; i < n_; i++) memcpy(items_[i].dst, st->p + items_[i].off, items_[i].bytes);
+    synced_ = true;
+    for (int i = 0; i < n_; i++) memcpy(items_[i].dst, area_.p + items_[i].off, items_[i].bytes);
     n_ = 0;
     used_ = 0;
     return cudaSuccess;
@@ -222,17 +377,79 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
         h = g_hook;
     }
     if (h.alloc) return h.alloc(bytes, (void*)s, h.ctx);
-    keep_pool_cached();
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
-        cudaGetLastError();  // clear the sticky-free error state of a failed allocation
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
         return nullptr;
+    }
+    DevMem& d = g_mem[dev];
+    std::lock_guard<std::mutex> g(d.mu);
+    mem_init(d, dev);
+    if (capturing(s)) {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;  // not recorded: its free goes to the pool as well
+    }
+    const size_t need = round_block(bytes);
+    void* p = take(d, need, s, false);
+    if (!p) p = pool_alloc(d, need, s);
+    if (!p) p = take(d, need, s, true);
+    if (!p) {
+        while (!d.kept.empty()) give_back(d, d.kept.size() - 1, s);
+        p = pool_alloc(d, need, s);
     }
     return p;
 }
 
 void dev_free(void* p, cudaStream_t s) {
     if (!p) return;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        cur = 0;
+    }
+    // the device whose cache handed the block out (the current one, as a rule)
+    for (int k = 0; k < 64; k++) {
+        const int dev = k == 0 ? cur : (k <= cur ? k - 1 : k);
+        if (dev < 0 || dev >= 64) continue;
+        DevMem& d = g_mem[dev];
+        std::lock_guard<std::mutex> g(d.mu);
+        if (!d.ready) continue;
+        auto it = d.live.find(p);
+        if (it == d.live.end()) continue;
+        const size_t bytes = it->second;
+        d.live.erase(it);
+        d.live_bytes -= bytes;
+        if (dev != cur) cudaSetDevice(dev);
+        cudaEvent_t ev = nullptr;
+        if (!d.spare.empty()) {
+            ev = d.spare.back();
+            d.spare.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ev = nullptr;
+        }
+        const size_t limit = cache_limit(d);
+        if (!ev || bytes > limit || capturing(s) || cudaEventRecord(ev, s) != cudaSuccess) {
+            cudaGetLastError();
+            if (ev) d.spare.push_back(ev);
+            if (cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
+        } else {
+            d.kept.push_back(Kept{p, bytes, s, ev, false, ++d.tick});
+            d.kept_bytes += bytes;
+            while (d.kept_bytes > limit && !d.kept.empty()) {
+                size_t old = 0;
+                for (size_t i = 1; i < d.kept.size(); i++)
+                    if (d.kept[i].age < d.kept[old].age) old = i;
+                give_back(d, old, s);
+            }
+        }
+        if (dev != cur) cudaSetDevice(cur);
+        return;
+    }
     AllocHook h;
     {
         std::lock_guard<std::mutex> g(g_hook_mu);
@@ -389,6 +606,35 @@ extern "C" xm_status xm_set_allocator(void* (*alloc)(size_t, void*, void*),
     g_hook.alloc = alloc;
     g_hook.release = release;
     g_hook.ctx = ctx;
+    return XM_OK;
+}
+
+extern "C" xm_status xm_set_cache_limit(int64_t bytes) {
+    g_cache_limit.store(bytes < 0 ? -1 : (long long)bytes);
+    return XM_OK;
+}
+
+extern "C" xm_status xm_free_cached(void* stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(XM_EINVAL, "xm_free_cached: device %d", dev);
+    DevMem& d = g_mem[dev];
+    std::lock_guard<std::mutex> g(d.mu);
+    while (!d.kept.empty()) give_back(d, d.kept.size() - 1, (cudaStream_t)stream);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? XM_OK : cuda_fail(e, "xm_free_cached");
+}
+
+extern "C" xm_status xm_mem_info(int64_t* live_bytes, int64_t* kept_bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(XM_EINVAL, "xm_mem_info: device %d", dev);
+    DevMem& d = g_mem[dev];
+    std::lock_guard<std::mutex> g(d.mu);
+    if (live_bytes) *live_bytes = (int64_t)d.live_bytes;
+    if (kept_bytes) *kept_bytes = (int64_t)d.kept_bytes;
     return XM_OK;
 }
 

@@ -430,19 +430,30 @@ struct Side {
 Side* side_stream();
 
 // Small device -> host reads gathered behind one synchronisation: add()
-// queues a read; one small kernel on the stream writes them all into this
-// host thread's pinned, mapped staging area (not a device-to-host copy: those
-// wait in order behind every such copy queued on any stream); sync() waits
-// for the stream once and hands the values out. Without mapped memory, or
-// past the area's room, a read is a plain asynchronous copy.
+// queues a read; one small kernel on the stream writes them all into a
+// pinned, mapped staging area this object holds while it lives (not a
+// device-to-host copy: those wait in order behind every such copy queued on
+// any stream); sync() waits for the stream once and hands the values out.
+// Without mapped memory, or past the area's room, a read is a plain
+// asynchronous copy.
 class HostReads {
   public:
     explicit HostReads(cudaStream_t s) : s_(s) {}
+    ~HostReads();
+    HostReads(const HostReads&) = delete;
+    HostReads& operator=(const HostReads&) = delete;
     cudaError_t add(void* host_dst, const void* dev_src, size_t bytes);
     // Marks the reads queued so far: sync() then waits for them only, so
     // work queued on the stream after mark() keeps the GPU busy meanwhile.
     cudaError_t mark();
     cudaError_t sync();
+
+    struct Area {
+        unsigned char* p = nullptr;   // host address
+        unsigned char* dp = nullptr;  // device address of the same bytes
+        cudaEvent_t ev = nullptr;     // recorded after the kernel writing it
+        int dev = 0;
+    };
 
   private:
     // queues the kernel that writes the reads into the staging area (once)
@@ -453,10 +464,13 @@ class HostReads {
         size_t off, bytes;
     };
     cudaStream_t s_;
+    Area area_;
+    bool tried_ = false, have_ = false;
     size_t used_ = 0;
     int n_ = 0;
     bool marked_ = false;
     bool launched_ = false;
+    bool synced_ = false;
     Item items_[8];
 };
 void dev_free(void* p, cudaStream_t s);

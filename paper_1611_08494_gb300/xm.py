@@ -89,6 +89,9 @@ xm_status_str = _sig("xm_status_str", ctypes.c_char_p, _i32)
 xm_last_error = _sig("xm_last_error", ctypes.c_char_p)
 xm_version = _sig("xm_version", ctypes.c_char_p)
 xm_set_allocator = _sig("xm_set_allocator", _i32, _p, _p, _p)
+xm_set_cache_limit = _sig("xm_set_cache_limit", _i32, _i64)
+xm_free_cached = _sig("xm_free_cached", _i32, _p)
+xm_mem_info = _sig("xm_mem_info", _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64))
 xm_get_stats = _sig("xm_get_stats", _i32, ctypes.POINTER(Stats))
 xm_reset_stats = _sig("xm_reset_stats", _i32)
 xm_prof_enable = _sig("xm_prof_enable", _i32, _i32)
@@ -103,6 +106,9 @@ xm_index_info = _sig("xm_index_info", _i32, _p, ctypes.POINTER(_i64), ctypes.POI
                      ctypes.POINTER(_f64), ctypes.POINTER(_i64))
 xm_match = _sig("xm_match", _i32, _p, ctypes.POINTER(Columns), ctypes.POINTER(Region),
                 ctypes.POINTER(MatchOpts), _p, ctypes.POINTER(_p))
+xm_match_async = _sig("xm_match_async", _i32, _p, ctypes.POINTER(Columns), ctypes.POINTER(Region),
+                      ctypes.POINTER(MatchOpts), _p, ctypes.POINTER(_p))
+xm_match_wait = _sig("xm_match_wait", _i32, _p, ctypes.POINTER(_p))
 xm_result_free = _sig("xm_result_free", _i32, _p)
 xm_result_get = _sig("xm_result_get", _i32, _p, ctypes.POINTER(ResultView))
 xm_join = _sig("xm_join", _i32, _p, _i32, _i32, _p, ctypes.POINTER(_p))
@@ -157,6 +163,25 @@ def _stream_handle(stream) -> Optional[int]:
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream
     return int(stream)
+
+
+def set_cache_limit(nbytes: int) -> None:
+    """Most bytes of freed device blocks the library keeps per device for
+    reuse (0: none; negative: the default, half the device's memory)."""
+    check(xm_set_cache_limit(int(nbytes)), "xm_set_cache_limit")
+
+
+def free_cached(stream=None) -> None:
+    """Returns the kept blocks of the current device to the CUDA pool,
+    ordered on ``stream``."""
+    check(xm_free_cached(_stream_handle(stream)), "xm_free_cached")
+
+
+def mem_info() -> dict:
+    """Device bytes the library holds in live objects and keeps for reuse."""
+    live, kept = _i64(), _i64()
+    check(xm_mem_info(ctypes.byref(live), ctypes.byref(kept)), "xm_mem_info")
+    return {"live_bytes": live.value, "kept_bytes": kept.value}
 
 
 def _f64_buffer(x, keep: list, on_device: Optional[bool]):
@@ -256,6 +281,46 @@ def region(shape=CIRCLE, a=1.0, b=None, pa=0.0, a_col=None, b_col=None, pa_col=N
                   ap, bp, pp, float(size_scale), float(size_unit_arcsec), float(pa_zero_deg)), keep
 
 
+class Pending:
+    """A match queued up to its pair count, ``xm_match_async``: the copy of
+    host A comes first on the stream's copy queue, so input copies queued
+    after it (an index build's) do not hold it up. ``wait()`` takes the
+    match's one synchronisation and returns its Result (``xm_match_wait``).
+    The A and region columns and the index stay referenced until then."""
+
+    def __init__(self, index: Index, lon, lat, frame=EQ, selection=SEL_ALL | SEL_BEST,
+                 precision=PREC_FP32, block=0, a_order=A_ORDER_DEFAULT, stream=None, **region_kw):
+        cols, keep = columns(lon, lat, frame)
+        reg, keep = region(keep=keep, **region_kw)
+        opts = MatchOpts(int(selection), int(precision), int(block), int(a_order))
+        h = _p()
+        check(xm_match_async(index.handle, ctypes.byref(cols), ctypes.byref(reg),
+                             ctypes.byref(opts), _stream_handle(stream), ctypes.byref(h)),
+              "xm_match_async")
+        self.handle = h.value
+        self.index = index
+        self._keep = keep
+
+    def wait(self) -> "Result":
+        h, self.handle = self.handle, None
+        if not h:
+            raise ValueError("this match was already waited for")
+        r = _p()
+        try:
+            check(xm_match_wait(h, ctypes.byref(r)), "xm_match_wait")
+        finally:
+            self._keep = None
+        return Result._from_handle(r.value, self.index)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:  # never waited for: the match completes and its result is dropped
+            self.handle = None
+            r = _p()
+            if xm_match_wait(h, ctypes.byref(r)) == 0 and r.value:
+                xm_result_free(r.value)
+
+
 class Result:
     """Members of every A source. ``xm_match``."""
 
@@ -267,7 +332,16 @@ class Result:
         h = _p()
         check(xm_match(index.handle, ctypes.byref(cols), ctypes.byref(reg), ctypes.byref(opts),
                        _stream_handle(stream), ctypes.byref(h)), "xm_match")
-        self.handle = h.value
+        self._adopt(h.value, index)
+
+    @classmethod
+    def _from_handle(cls, handle, index):
+        self = cls.__new__(cls)
+        self._adopt(handle, index)
+        return self
+
+    def _adopt(self, handle, index):
+        self.handle = handle
         self.index = index
         v = ResultView()
         check(xm_result_get(self.handle, ctypes.byref(v)), "xm_result_get")
