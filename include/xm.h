@@ -329,13 +329,13 @@ XM_API xm_status xm_rows_get(const xm_rows* rows, xm_rows_view* view);
  * results of at most 2^20 A rows and 2^23 B rows (about 16 MB, held on every
  * GPU that loads the library until the process exits); larger results are
  * XM_EOVERFLOW, as is a row count above `capacity` (*n_rows still reports
- * it, nothing is written). The first call on a device looks up that array's
- * device address (a runtime query that is not allowed while a stream is
- * being captured), so make the first call on each device before any stream
- * capture begins. The current device must be the one the result was
- * computed on (else XM_EINVAL). All calls share the array: calls whose work
- * overlaps on the GPU (on different streams without ordering) race and must
- * not be made. Synchronises `stream` once, to read the row count. */
+ * it, nothing is written). The current device must be the one the result
+ * was computed on (else XM_EINVAL). All calls share the array: calls whose
+ * work overlaps on the GPU (on different streams without ordering) race and
+ * must not be made. Synchronises `stream` once, to read the row count, so it
+ * must not be called while `stream` is being captured into a graph; its
+ * first call on a device also looks up the array's device address, a query
+ * that fails while any stream is being captured in global mode. */
 XM_API xm_status xm_join_noalloc(const xm_result* result, int32_t selection, int32_t join_type,
                                  int64_t* a_row, int64_t* b_row, double* sep, int64_t capacity,
                                  int64_t* n_rows, void* stream);
