@@ -482,6 +482,7 @@ def run_ours(args):
     scan_roof = kernel_roofline(count_kernel(prof), prof, st_p, prof_steps, n_a, n_b, d["region"])
     del dev, d
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
 
     if rank != 0:
         return
@@ -924,6 +925,7 @@ def c2_leg(args, xm, torch, measured):
     out["picks"] = pick_leg(xm, torch, step, stream)
     del cols, reg
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
     return out
 
 
@@ -970,6 +972,7 @@ def values_leg(args, xm, torch):
                            "unit": "GB/s", "frac": ach / peak, "peak_source": "of measured"}
     del d
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
     return out
 
 
@@ -1043,6 +1046,7 @@ def c4_leg(args, xm, torch, measured):
            "setup_s": setup_s, "scan_roofline": scan, "cpu_baseline": base}
     del d, reqs, idx
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
     return out
 
 
@@ -1079,6 +1083,7 @@ def serving_leg(args, xm, torch):
         host_pool.append(dict(q, lon=pinned(q["lon"]), lat=pinned(q["lat"]), region=reg))
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
     setup_s = time.perf_counter() - t_setup
     common = dict(slots=args.serve_slots, pool=len(pool),
                   zone_height_arcsec=tuned["zone_height_arcsec"],
@@ -1099,6 +1104,7 @@ def serving_leg(args, xm, torch):
                                   input="pinned host columns", mem_budget_bytes=budget)
     del pool, host_pool, idx
     torch.cuda.empty_cache()
+    xm.free_cached()  # and the blocks the library kept for reuse
     return out
 
 

@@ -560,7 +560,8 @@ typedef struct {
     int32_t slots;               /* batches in flight at once (0 -> 2) */
     int32_t max_batch_requests;  /* requests per batch (0 -> 256) */
     int64_t max_batch_a;         /* A sources per batch (0 -> 2^26) */
-    int64_t mem_budget_bytes;    /* device memory for requests in flight (0 -> 60 % of free) */
+    int64_t mem_budget_bytes;    /* device memory for requests in flight (0 -> 60 % of free,
+                                    counting blocks the library keeps for reuse as free) */
     int32_t precision;           /* xm_precision */
     int32_t use_graph;           /* run each batch as a CUDA graph */
     int32_t persistent_blocks;   /* 0 -> 4 */

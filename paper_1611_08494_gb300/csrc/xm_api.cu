@@ -462,6 +462,17 @@ void dev_free(void* p, cudaStream_t s) {
     cudaFreeAsync(p, s);
 }
 
+size_t kept_device_bytes() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    DevMem& d = g_mem[dev];
+    std::lock_guard<std::mutex> g(d.mu);
+    return d.kept_bytes;
+}
+
 void launch_begin(const char* name, cudaStream_t s) {
     (void)name;
     g_stats[5].fetch_add(1, std::memory_order_relaxed);

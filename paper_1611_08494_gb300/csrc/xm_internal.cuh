@@ -474,6 +474,8 @@ class HostReads {
     Item items_[8];
 };
 void dev_free(void* p, cudaStream_t s);
+// Bytes of freed blocks kept for reuse on the current device.
+size_t kept_device_bytes();
 
 // Kernel launch bookkeeping: counts launches and, while profiling is on,
 // brackets each launch with events on its stream.

@@ -187,7 +187,10 @@ extern "C" xm_status xm_serve_open(const xm_index* index, const xm_serve_opts* o
         delete S;
         return cuda_fail(e, "xm_serve_open: cudaMemGetInfo");
     }
-    S->mem_budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)(0.6 * (double)free_b);
+    // blocks the library keeps for reuse are free to the server's own
+    // allocations (and go back to the pool when it runs short)
+    const double avail = (double)free_b + (double)kept_device_bytes();
+    S->mem_budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)(0.6 * avail);
     for (int k = 0; k <= o.slots; k++) {
         cudaStream_t st = nullptr;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
