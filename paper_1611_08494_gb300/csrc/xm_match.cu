@@ -215,6 +215,9 @@ struct xm_pending {
     Temps T;
     int64_t nA, nn;
     bool sorted_a = false, want_all = false;
+    // the side streams' handles, copied: the per-thread records they come
+    // from end with their thread, and the wait may run on another one
+    Side pre_side{}, tie_side{};
     Side* pre = nullptr;  // side stream of the host A copy
     cudaStream_t ps = nullptr;
     double* a_buf = nullptr;  // A columns on the device (host input)
@@ -228,14 +231,14 @@ struct xm_pending {
     int32_t h_small[8] = {};
     int64_t h_total[2] = {0, 0};
     int32_t h_berr = 0;  // a deferred index build's error bits
-    Side* side = nullptr;  // float64 near-tie resolve beside the placement
+    Side* side = nullptr;  // float64 near-tie resolve beside the placement (tie_side)
     cudaEvent_t fork = nullptr;
     int64_t np_spec = 0;
 
     xm_pending(const xm_index* X_, const xm_columns* A_, const xm_region* r_,
                const xm_match_opts* o, cudaStream_t s_)
         : X(X_), A(*A_), region(*r_), sel(o->selection), prec(o->precision), s(s_), T(s_),
-          nA(A_->n), nn(A_->n > 0 ? A_->n : 1), rd(s_) {  // (declaration order)
+          nA(A_->n), nn(A_->n > 0 ? A_->n : 1), rd(s_) {
         sorted_a = o->a_order == XM_A_ORDER_SORTED ||
                    (o->a_order == XM_A_ORDER_DEFAULT && kDefaultSortedA);
         want_all = (sel & XM_SEL_ALL) != 0;
@@ -290,7 +293,12 @@ xm_status xm_pending::begin() {
     // host A in input order is copied and prepared on the side stream,
     // alongside what the caller's stream is still running (an index build
     // launched just before, say); its buffers are freed on `s` after it
-    pre = (!A.on_device && nA > 0 && !sorted_a) ? side_stream() : nullptr;
+    if (!A.on_device && nA > 0 && !sorted_a) {
+        if (Side* p = side_stream()) {
+            pre_side = *p;
+            pre = &pre_side;
+        }
+    }
     ps = pre ? pre->st : s;
     // A columns on the device
     const double *lon = A.lon_deg, *lat = A.lat_deg;
@@ -433,7 +441,12 @@ xm_status xm_pending::begin() {
     if (e == cudaSuccess && X->build_err) e = rd.add(&h_berr, X->build_err, sizeof(int32_t));
     if (e == cudaSuccess) e = rd.mark();
     if (e != cudaSuccess) return cuda_fail(e, "xm_match count reads");
-    side = ((sel & XM_SEL_BEST) && prec == XM_PREC_FP32_RECHECK) ? side_stream() : nullptr;
+    if ((sel & XM_SEL_BEST) && prec == XM_PREC_FP32_RECHECK) {
+        if (Side* p = side_stream()) {
+            tie_side = *p;
+            side = &tie_side;
+        }
+    }
     if (side && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
                  cudaEventRecord(fork, s) != cudaSuccess)) {
         cudaGetLastError();

@@ -4,11 +4,13 @@ The two-call form must give exactly xm_match's result: with host A and with
 device A, in both A orders. It must stay exact with several matches pending at
 once on one host thread, each with its own staging of the count reads and its
 own fork to the near-tie resolve, waited for in any order, with index builds
-queued between them. A pending match that is never waited for must leave
-nothing behind. An error found on the device (A coordinates out of range) must
-surface at the wait and leave nothing either."""
+queued between them; and when it is waited for on another thread than the one
+that queued it, after that thread has ended. A pending match that is never
+waited for must leave nothing behind. An error found on the device (A
+coordinates out of range) must surface at the wait and leave nothing either."""
 
 import gc
+import threading
 
 import numpy as np
 import pytest
@@ -114,3 +116,21 @@ def test_error_surfaces_at_wait(env):
     assert ex.value.status == "XM_EINVAL"
     del p
     assert _live(xm, torch) == base
+
+
+def test_waited_on_another_thread(env):
+    xm, torch, d, host, idx = env
+    kw = dict(frame=d["a_frame"], selection=xm.SEL_ALL | xm.SEL_BEST, **d["region"])
+    ref = _arrays(xm.Result(idx, host["a_lon"], host["a_lat"], **kw))
+    st = torch.cuda.Stream()
+    held = []
+
+    def queue():
+        held.append(xm.Pending(idx, host["a_lon"], host["a_lat"], stream=st, **kw))
+
+    t = threading.Thread(target=queue)
+    t.start()
+    t.join()  # the queuing thread has ended (its side streams' records with it)
+    res = held.pop().wait()
+    st.synchronize()
+    _same(_arrays(res), ref, "waited on another thread")
