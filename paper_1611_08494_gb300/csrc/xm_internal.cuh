@@ -72,10 +72,13 @@ struct __align__(16) ZoneInfo {
     double sin_c, cos_c;   // of dec_c, float64
     double binw;           // RA cell width (rad)
     int64_t start, end;    // index rows of the zone
-    int64_t lut_base;      // first bucket entry of the zone
+    // the four fields the B ingest reads for every source, in one 32-byte
+    // sector (across two sectors its pass took 2.62 ms instead of 2.00 on
+    // the all-sky index)
     float sin_cf, cos_cf;  // of dec_c, float32
     float binw_f;          // RA cell width (rad), float32
     uint32_t nbins;        // RA cells
+    int64_t lut_base;      // first bucket entry of the zone
     uint32_t lut_shift;    // key bits per bucket
     uint32_t lut_kmin;     // smallest ra_key of the zone
     uint32_t lut_nb;       // buckets (a power of two)
