@@ -231,6 +231,7 @@ __global__ void k_batch_matched_b(BatchConst C, const int32_t* __restrict__ coun
     const bool all = R.join_sel == XM_SEL_ALL;
     const int64_t p = pair_off[g];
     if (all && p + c > pair_cap) return;
+    uint32_t fresh = 0;  // this source's first insertions
     for (int32_t k = 0; k < (all ? c : 1); k++) {
         const int64_t b = all ? pb[p + k] : best_b[g];
         const uint64_t key = ((uint64_t)(uint32_t)r << 32) | (uint64_t)(uint32_t)b;
@@ -243,13 +244,20 @@ __global__ void k_batch_matched_b(BatchConst C, const int32_t* __restrict__ coun
             const unsigned long long prev =
                 atomicCAS((unsigned long long*)&table[h], ~0ull, (unsigned long long)key);
             if (prev == ~0ull) {
-                atomicAdd(&req_mb[r], 1ull);
+                fresh++;
                 break;
             }
             if (prev == key) break;
             h = (h + 1) & mask;
         }
     }
+    // counted once per request and warp (a warp's sources almost always
+    // belong to one request, whose counter would otherwise take one atomic
+    // per distinct B row)
+    const uint32_t peers = __match_any_sync(__activemask(), fresh ? r : -1);
+    const uint32_t sum = __reduce_add_sync(peers, fresh);
+    const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+    if (fresh && (peers & lt) == 0) atomicAdd(&req_mb[r], (unsigned long long)sum);
 }
 
 // Per-request bounds in the pair and row arenas.
