@@ -495,6 +495,9 @@ typedef struct xm_batch xm_batch;
  * names the request. */
 XM_API xm_status xm_match_batch(const xm_index* index, const xm_request* requests, int64_t n,
                                 const xm_batch_opts* opts, void* stream, xm_batch** out);
+/* Frees a batch. Its device memory is released in the order of the stream it
+ * was computed on, which must still exist: work queued on other streams that
+ * reads the batch's arrays must be ordered before that point. */
 XM_API xm_status xm_batch_free(xm_batch* batch);
 
 /* Device arrays of one request of a batch (valid until xm_batch_free). A rows

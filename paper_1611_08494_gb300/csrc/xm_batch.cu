@@ -347,6 +347,9 @@ using namespace xm;
 
 struct xm_batch {
     int device;
+    // the stream the batch was computed on: its arrays are released in that
+    // stream's order, after the work the caller queued there to read them
+    cudaStream_t stream = nullptr;
     int64_t n_req, total_a, total_pairs, total_rows, n_b;
     int32_t precision;
     std::vector<int64_t> off;          // [n_req + 1]
@@ -365,7 +368,7 @@ static void free_batch_bufs(BatchBufs& B, cudaStream_t s) {
 
 extern "C" xm_status xm_batch_free(xm_batch* X) {
     if (!X) return XM_OK;
-    free_batch_bufs(X->B, nullptr);
+    free_batch_bufs(X->B, X->stream);
     delete X;
     return XM_OK;
 }
@@ -738,6 +741,7 @@ extern "C" xm_status xm_match_batch(const xm_index* X, const xm_request* reqs, i
     xm_batch* X2 = new (std::nothrow) xm_batch();
     if (!X2) return set_error(XM_ENOMEM, "xm_match_batch: host allocation");
     cudaGetDevice(&X2->device);
+    X2->stream = s;
     X2->n_req = n;
     X2->n_b = X->n;
     X2->precision = prec;
