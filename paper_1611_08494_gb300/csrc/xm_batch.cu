@@ -93,9 +93,9 @@ __global__ void k_batch_ingest(BatchConst C, uint64_t* __restrict__ keys,
     double lon, lat, gamma;
     bool ok;
     batch_position(C, R, i, &lon, &lat, &gamma, &ok);
-    const double a = R.a_col ? R.a_col[i] : R.a;
-    const double b = R.shape == XM_CIRCLE ? a : (R.b_col ? R.b_col[i] : R.b);
-    const double pa = R.pa_col ? R.pa_col[i] : R.pa;
+    const double a = col_or(R.a_col, i, R.a);
+    const double b = R.shape == XM_CIRCLE ? a : col_or(R.b_col, i, R.b);
+    const double pa = col_or(R.pa_col, i, R.pa);
     if (!ok) {
         atomicOr(err, kErrCoord);
         atomicMin(bad_req, r);
@@ -123,9 +123,9 @@ __global__ void k_batch_prep(BatchConst C, const uint32_t* __restrict__ vals,
     double lon, lat, gamma;
     bool ok;
     batch_position(C, R, i, &lon, &lat, &gamma, &ok);
-    const double a = R.a_col ? R.a_col[i] : R.a;
-    const double b = R.shape == XM_CIRCLE ? a : (R.b_col ? R.b_col[i] : R.b);
-    const double pa = R.pa_col ? R.pa_col[i] : R.pa;
+    const double a = col_or(R.a_col, i, R.a);
+    const double b = R.shape == XM_CIRCLE ? a : col_or(R.b_col, i, R.b);
+    const double pa = col_or(R.pa_col, i, R.pa);
     make_aprep(lon, lat, gamma, ok, a, b, pa, R.shape, R.pa_dir, R.size_k, R.pa_zero, C.nz, C.h_f,
                (int32_t)g, &out[s], &cold[s]);
     lrow[g] = (int32_t)i;

@@ -123,11 +123,10 @@ __global__ void __launch_bounds__(kBlock) k_ingest_b(
     uint32_t z = 0, ra = 0;
     if (has) {
         double lo = lon[i], la = lat[i];
-        if (!coord_ok(lo, la)) {
-            atomicOr(err, kErrCoord);
-            lo = 0.0;
-            la = 0.0;
-        }
+        const bool ok = coord_ok(lo, la);
+        if (!ok) atomicOr(err, kErrCoord);
+        lo = keep_or_zero(lo, ok);
+        la = keep_or_zero(la, ok);
         lo = lon_mod360(lo);
         const PosKey k = pos_key(lo, la, nz);
         z = (uint32_t)k.z;

@@ -188,6 +188,20 @@ __host__ __device__ inline double lon_mod360(double lon) {
     return lon_reduce360(lon);
 }
 
+// Selects of float64 values made on their bit patterns: a select between two
+// float64 registers issues on the float64 pipe, which this GPU runs at 1/64
+// of the float32 rate (two such selects per source, zeroing an invalid
+// position, kept that pipe a quarter busy in the B ingest).
+__device__ __forceinline__ double keep_or_zero(double x, bool keep) {
+    return __longlong_as_double(keep ? __double_as_longlong(x) : 0ll);
+}
+// p[i] when a column is given, else the constant v.
+__device__ __forceinline__ double col_or(const double* __restrict__ p, int64_t i, double v) {
+    long long b = __double_as_longlong(v);
+    if (p) b = __ldg(reinterpret_cast<const long long*>(p) + i);
+    return __longlong_as_double(b);
+}
+
 // Finite longitude and |lat| <= 90 (NaN fails), decided on the bit patterns.
 __device__ __forceinline__ bool coord_ok(double lon, double lat) {
     const uint64_t bl = (uint64_t)__double_as_longlong(lon) & 0x7FFFFFFFFFFFFFFFull;

@@ -57,7 +57,8 @@ __device__ __forceinline__ void a_position_of(double lon, double lat, int32_t ro
                                               const double* rot, double* lon_o, double* lat_o,
                                               double* gamma, bool* ok) {
     *ok = coord_ok(lon, lat);
-    if (!*ok) { lon = 0.0; lat = 0.0; }
+    lon = keep_or_zero(lon, *ok);  // (an invalid position becomes (0, 0))
+    lat = keep_or_zero(lat, *ok);
     lon = lon_mod360(lon);
     if (!rotate) {
         *lon_o = lon;
@@ -127,9 +128,9 @@ __global__ void k_ingest_a(AIn I, uint64_t* __restrict__ keys, uint32_t* __restr
     bool ok;
     a_position(I, i, &lon, &lat, &gamma, &ok);
     if (!ok) atomicOr(err, kErrCoord);
-    const double a = I.a_col ? I.a_col[i] : I.a;
-    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
-    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    const double a = col_or(I.a_col, i, I.a);
+    const double b = I.shape == XM_CIRCLE ? a : col_or(I.b_col, i, I.b);
+    const double pa = col_or(I.pa_col, i, I.pa);
     if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
     const PosKey k = pos_key(lon, lat, I.nz);
     keys[i] = ((uint64_t)k.z << 32) | ((uint32_t)(k.key64 >> 32) & kRaKeyMask);
@@ -213,9 +214,9 @@ __device__ __forceinline__ void prep_at(const AIn& I, int64_t i, double lon0, do
     double lon, lat, gamma;
     bool ok;
     a_position_of(lon0, lat0, I.rotate, I.rot, &lon, &lat, &gamma, &ok);
-    const double a = I.a_col ? I.a_col[i] : I.a;
-    const double b = I.shape == XM_CIRCLE ? a : (I.b_col ? I.b_col[i] : I.b);
-    const double pa = I.pa_col ? I.pa_col[i] : I.pa;
+    const double a = col_or(I.a_col, i, I.a);
+    const double b = I.shape == XM_CIRCLE ? a : col_or(I.b_col, i, I.b);
+    const double pa = col_or(I.pa_col, i, I.pa);
     if (err) {
         if (!ok) atomicOr(err, kErrCoord);
         if (!size_ok(a, b, pa)) atomicOr(err, kErrSize);
