@@ -388,7 +388,7 @@ def run_ours(args):
     smp = cap_sample(d, args.cpu_sample or 1_500_000) if (rank == 0 and world == 1
                                                           and not args.no_cpu_baseline) else None
     dev = {k: d[k] for k in ("a_lon", "a_lat", "b_lon", "b_lat", "b_id")}
-    zone_h = args.zone_height or 12.0
+    zone_h = args.zone_height or 24.0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     host_out = {}
