@@ -8,8 +8,9 @@ streams that wait for them, results copied out on a further stream, each
 step's objects released in their streams' order after a wait on its copy out)
 must give every step exactly the rows, separations and best pairs of a serial
 run with nothing kept. Kept bytes must shrink while live objects reuse them,
-nothing may stay live once every object is gone, a limit of 0 keeps nothing,
-and xm_free_cached hands everything back."""
+nothing may stay live once every object is gone, a limit of 0 keeps nothing, a
+small limit caps what is kept (results unchanged), and xm_free_cached hands
+everything back."""
 
 import gc
 
@@ -167,3 +168,22 @@ def test_kept_blocks_are_reused_and_handed_back(env):
     xm.free_cached()
     torch.cuda.synchronize()
     assert xm.mem_info()["kept_bytes"] == 0
+
+
+def test_cache_limit_caps_kept_bytes(env):
+    xm, torch, d, host = env
+    base = _live_after_gc(xm, torch)["live_bytes"]
+    ref = _serial(xm, torch, d, host)
+    cap = 64 << 20
+    xm.free_cached()
+    xm.set_cache_limit(cap)
+    try:
+        for _ in range(3):  # blocks past the cap go back to the pool, oldest first
+            got = _serial(xm, torch, d, host)
+            info = _live_after_gc(xm, torch)
+            assert info["kept_bytes"] <= cap
+            assert info["live_bytes"] == base
+            for a, b in zip(got, ref):
+                np.testing.assert_array_equal(a, b)
+    finally:
+        xm.set_cache_limit(-1)
